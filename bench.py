@@ -1,0 +1,324 @@
+"""Benchmark of the Horseshoe-probit Gibbs sweep on GB300.
+
+Workload (default): N = 1,000,000 rows, p = 1000, X iid N(0,1) stored FP32
+(4 GB), 10 nonzero coefficients U[1,3] with random sign, y = 1{x beta + eps > 0},
+seed 0 -- the paper's N = 1e6, p = 1000 synthetic problem (Sect. 6.1, Eq. 13)
+with random sparse beta.  One step = one full Gibbs sweep (X-stream, reduce,
+lambda/tau, Cholesky + inverse, beta tail, nu/xi, commit).  X (4 GB) is far
+larger than L2 (129 MB), so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (rank 0 only).  Under torchrun each rank runs an
+independent chain (distinct Philox chain id) on its own GPU: weak scaling,
+no collective on the data path; the barrier and max-over-ranks timing use
+torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gibbs sweeps/sec at N=1e6,p=1000 (1 chain); % HBM roofline"
+WORKLOADS = {
+    "c1s": dict(N=200_000, p=1000, nz=10, dt="f32",
+                name="horseshoe-probit sweep, N=2e5, p=1000, X iid N(0,1) fp32 (profiling case, 800 MB)"),
+    "c1": dict(N=1_000_000, p=1000, nz=10, dt="f32",
+               name="horseshoe-probit sweep, N=1e6, p=1000, X iid N(0,1) fp32, 10 nonzeros U[1,3], 1 chain"),
+    "c0": dict(N=10_000, p=100, nz=5, dt="f64",
+               name="horseshoe-probit sweep, N=1e4, p=100, X iid N(0,1) fp64, 5 nonzeros U[1,3], 1 chain"),
+}
+XSTREAM_SOURCES = ["paper_1608_04329_gb300/csrc/xstream.cu", "paper_1608_04329_gb300/csrc/hs_common.cuh"]
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend=backend)
+    return dist, rank, ws, local
+
+
+def max_over_ranks(dist, value: float) -> float:
+    """Max of a float over ranks (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _traffic(workload: str):
+    """DRAM bytes per X-stream launch from the committed ncu summary, or None
+    when the kernel sources changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "xstream_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for s in XSTREAM_SOURCES:
+        with open(os.path.join(ROOT, s), "rb") as f:
+            h.update(f.read())
+    if rec.get("sources_sha256") != h.hexdigest() or rec.get("workload") != workload:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def make_data(wl):
+    import hs_synth
+    return hs_synth.make_problem(wl["N"], wl["p"], wl["nz"], wl["dt"], seed=0)
+
+
+def cpu_oracle_rate(d, wl, n_sweeps: int, budget_s: float = 30.0):
+    """Oracle sweeps/s on the host (full workload, first n_sweeps sweeps)."""
+    import oracle
+    X = oracle.fmt.stored_to_f64(d["X"], d["x_dtype"], d["scales"])
+    t0 = time.perf_counter()
+    G = oracle.gram(X)
+    t_gram = time.perf_counter() - t0
+    st = oracle.init_state(wl["p"])
+    st = oracle.sweep_once(st, X, d["y"], G, 0)  # warm-up
+    done, t = 0, 0.0
+    while done < n_sweeps and t < budget_s:
+        t1 = time.perf_counter()
+        st = oracle.sweep_once(st, X, d["y"], G, 0)
+        t += time.perf_counter() - t1
+        done += 1
+    return done / t, done, t, t_gram
+
+
+def run_reference(args, wl, dist, rank):
+    if rank != 0:
+        return 0
+    d = make_data(wl)
+    n = args.steps
+    rate, done, t, t_gram = cpu_oracle_rate(d, wl, n_sweeps=n, budget_s=args.ref_budget)
+    cores = os.cpu_count()
+    sample = (f"{done} oracle sweeps of the full workload (of {n} requested; capped at "
+              f"{args.ref_budget:.0f} s), after an untimed Gram ({t_gram:.1f} s) and one warm-up sweep")
+    line = {"metric": METRIC, "value": rate, "unit": "sweeps/s", "n_gpus": 0, "steps": done,
+            "warmup": 1, "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "N": wl["N"], "p": wl["p"], "x_dtype": wl["dt"]},
+            "impl": "reference",
+            "cpu_baseline": {"value": rate, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS))
+    ap.add_argument("--graph", type=int, default=1)
+    ap.add_argument("--chol", default="df32", choices=["f64", "df32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sweeps", type=int, default=3)
+    ap.add_argument("--profile", type=int, default=1,
+                    help="1: CUDA events around each kernel group in the timed region (eager launches)")
+    ap.add_argument("--ref-budget", type=float, default=120.0)
+    args = ap.parse_args(argv)
+    wl = WORKLOADS[args.workload]
+    dist, rank, ws, local = _dist()
+    if args.impl == "reference":
+        rc = run_reference(args, wl, dist, rank)
+        if dist is not None:
+            dist.destroy_process_group()
+        return rc
+
+    import torch
+    import paper_1608_04329_gb300 as pkg
+    pkg.load_library()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    torch.cuda.set_device(local)
+    d = make_data(wl)
+    chol = pkg.CHOL_F64 if args.chol == "f64" else pkg.CHOL_DF32
+    s = pkg.HSProbit(d["X"], d["y"], seed=0, chain=rank, device=local, use_graph=bool(args.graph),
+                     chol_arith=chol, ring_size=max(args.steps + args.warmup, 16))
+    stream = torch.cuda.ExternalStream(s.stream(), device=local)
+    s.sweep(args.warmup)
+
+    # ---- device-timed region: K sweeps, inputs resident in HBM ----
+    s.set_profiling(bool(args.profile))
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        s.sweep(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms_local = e0.elapsed_time(e1)
+    ms = max_over_ranks(dist, ms_local)
+    value = ws * args.steps / (ms / 1e3)
+    xs_ms, xs_n = s.kernel_time("xstream")
+    groups = {g: s.kernel_time(g) for g in ("xstream", "reduce", "shrink", "cholesky", "tail")}
+    launches = s.launches_per_sweep() * args.steps
+    s.set_profiling(False)
+    s.close()
+
+    # ---- roofline of the X-stream kernel ----
+    bytes_per_launch = wl["N"] * (wl["p"] * {"f64": 8, "f32": 4, "bf16": 2, "fp8": 1}[wl["dt"]] + 1)
+    peak, peak_kind = _peaks()
+    if xs_n > 0:
+        avg_ms = xs_ms / xs_n
+        achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": _traffic(args.workload), "peak_source": peak_kind,
+                    "kernel": "xstream", "avg_launch_ms": avg_ms}
+    else:
+        roofline = None
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        Xp = torch.from_numpy(d["X"]).pin_memory()
+        yp = torch.from_numpy(d["y"]).pin_memory()
+        Xh, yh = Xp.numpy(), yp.numpy()
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = pkg.HSProbit(Xh, yh, seed=1, chain=rank, device=local, use_graph=bool(args.graph), chol_arith=chol)
+        d2h = 0
+        for _ in range(args.steps):
+            s2.sweep(1)
+            dr = s2.draws()
+            d2h += sum(v.nbytes for v in dr.values())
+        s2.close()
+        t_e2e = max_over_ranks(dist, time.perf_counter() - t0)
+        e2e = {"value": ws * args.steps / t_e2e, "unit": "sweeps/s",
+               "h2d_bytes_per_step": int((d["X"].nbytes + d["y"].nbytes) / args.steps),
+               "d2h_bytes_per_step": int(d2h / args.steps),
+               "includes": "init from pinned host X and y (H2D copy + FP64 Gram) amortised over the steps, "
+                           "then per step one sweep and the D2H of its draw (beta, lambda^-2, tau^-2)"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, done, t, t_gram = cpu_oracle_rate(d, wl, n_sweeps=args.cpu_sweeps)
+        cpu = {"value": rate, "unit": "sweeps/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{done} FP64 oracle sweeps of the full workload after one warm-up sweep "
+                         f"(Gram {t_gram:.1f} s untimed), numpy/scipy with all host cores"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if wl["dt"] != "f64" else "f64",
+                "data": "synthetic",
+                "config": {"workload": wl["name"], "N": wl["N"], "p": wl["p"], "x_dtype": wl["dt"],
+                           "chains_per_gpu": 1, "cholesky": args.chol, "graph": bool(args.graph),
+                           "l2": "inputs larger than L2 (X 4 GB), no flush",
+                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches,
+                "clocks": clk.summary(),
+                "kernel_ms_per_sweep": {g: (v[0] / max(v[1], 1)) for g, v in groups.items()},
+                "hbm_roofline_frac_whole_sweep": (bytes_per_launch / (ms / args.steps / 1e3) / 1e9) / 8000.0}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

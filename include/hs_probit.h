@@ -1,0 +1,182 @@
+/*
+ * hs_probit.h -- C ABI of the GB300 (sm_103a) Gibbs sweep for Horseshoe
+ * probit regression.
+ *
+ * Model and sampler: Terenin, Dong & Draper, "GPU-accelerated Gibbs sampling:
+ * a case study of the Horseshoe Probit model", Sect. 5.
+ *   likelihood  y_i = round[Phi(z_i)], z_i | x_i, beta ~ N(x_i beta, 1)   (Eq. 9)
+ *   prior       beta_j ~ N(0, lambda_j^2 tau^2), lambda_j, tau ~ C+(0, 1)  (Eq. 10)
+ *   conditionals of z, lambda^{-2}, nu^{-1}, beta, tau^{-2}, xi^{-1}       (Eq. 12)
+ *   schedule    (i) z and lambda^{-2} in parallel, then tau^{-2};
+ *               (ii) beta, nu^{-1} and xi^{-1} in parallel.
+ * One call of hs_probit_sweep(h, n) runs n such sweeps on the GPU.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "host" are ordinary host memory owned by the caller;
+ *     pointers marked "device" are CUDA device memory on the handle's device,
+ *     also owned by the caller.  The library never frees caller memory.
+ *   - The handle owns all device memory it allocates; hs_probit_free
+ *     releases it.
+ *   - Matrices are row-major.  X is N x p with rows contiguous (row stride p).
+ *   - Status codes are the HS_* values below: 0 on success, < 0 on error.
+ *   - A handle may be used from one host thread at a time.
+ *
+ * Random numbers: every uniform is Philox4x32-10 (Salmon et al., SC'11, the
+ * generator the paper recommends in Sect. 5) of the counter
+ *     (index, k, purpose | chain << 8, problem)  with key (seed lo, seed hi),
+ * where k is the 1-based sweep number; purposes are z = 1, lambda = 2,
+ * tau = 3, beta noise = 4, nu = 5, xi = 6.  Two 32-bit words (hi, lo) give
+ * u = (2m + 1) 2^-53 with m = (hi << 20) | (lo >> 12).  Runs are therefore
+ * bit-reproducible and resumable from a saved state.
+ */
+#ifndef HS_PROBIT_H
+#define HS_PROBIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define HS_OK            0
+#define HS_EINVAL       -1  /* bad argument (sizes, y not in {0,1}, NULL) */
+#define HS_ENOMEM       -2  /* device or pinned host allocation failed */
+#define HS_ECUDA        -3  /* a CUDA runtime call failed */
+#define HS_ENOTPD       -4  /* X^T X + tau^{-2} Lambda^{-2} not positive definite */
+#define HS_ENONFINITE   -5  /* a non-finite value appeared in X beta, z or beta */
+#define HS_ETIMEOUT     -6  /* a bounded device wait ran out */
+#define HS_ESTATE       -7  /* handle is in an error state; call set_state */
+#define HS_EUNSUPPORTED -8  /* option not supported by this build */
+
+/* ---- storage type of X -------------------------------------------------- */
+#define HS_X_F64      0  /* double; the sweep computes X beta and X^T z in FP64 */
+#define HS_X_F32      1  /* float; FP32 arithmetic and accumulation */
+#define HS_X_BF16     2  /* bfloat16 bit patterns (uint16); FP32 arithmetic */
+#define HS_X_FP8E4M3  3  /* e4m3 codes (uint8) times a per-column FP32 scale */
+
+/* ---- arithmetic of the p x p Cholesky and inverse factor ----------------- */
+#define HS_CHOL_F64   0  /* native FP64 (GB300 runs FP64 at ~1/64 of the FP32 rate) */
+#define HS_CHOL_DF32  1  /* FP32 pairs (~48-bit significand) on the FP32 pipe; default */
+
+typedef struct hs_probit hs_probit;  /* opaque handle */
+
+typedef struct hs_probit_config {
+  int32_t x_dtype;     /* HS_X_*; hs_probit_init uses HS_X_F32 */
+  int32_t x_is_device; /* 1: X, y and x_scales are device pointers (copied) */
+  int32_t thin;        /* keep every thin-th sweep in the draw ring (>= 1) */
+  int32_t ring_size;   /* number of draws the device ring holds (>= 1) */
+  int32_t debug;       /* 1: keep z and X^T z of the last sweep for debug_* */
+  int32_t use_graph;   /* 1: replay each sweep as a captured CUDA graph */
+  int32_t chol_arith;  /* HS_CHOL_* */
+  int32_t device;      /* CUDA device ordinal */
+  uint32_t chain;      /* chain id in the counter (0..2^24-1) */
+  uint32_t problem;    /* problem id in the counter */
+  void* stream;        /* cudaStream_t for the sweep; NULL: library-owned stream */
+  const float* x_scales; /* HS_X_FP8E4M3 only: p column scales (host or device) */
+  int32_t reserved[8];
+} hs_probit_config;
+
+/* Values of one sampler state (Eq. 12 variables).  Arrays are host memory of
+ * length p owned by the caller. */
+typedef struct hs_probit_state_view {
+  double* beta;        /* beta_j */
+  double* lambda_inv2; /* lambda_j^{-2} */
+  double* nu_inv;      /* nu_j^{-1} */
+  double tau_inv2;     /* tau^{-2} */
+  double xi_inv;       /* xi^{-1} */
+  int64_t k;           /* sweeps done; the next sweep uses counter k + 1 */
+} hs_probit_state_view;
+
+/* Fill *cfg with defaults: F32 host X, thin 1, ring 1024, no debug, no graph,
+ * HS_CHOL_DF32, device 0, chain 0, problem 0, library stream. */
+void hs_probit_config_default(hs_probit_config* cfg);
+
+/* Create a sampler for host X (float32, N x p row-major) and host y (N bytes in
+ * {0,1}) with the cold start of Sect. 6.1 (beta = 0; lambda = nu = tau = xi = 1).
+ * N >= 2 (Sect. 4, Eq. 1) and 1 <= p <= 8192.  X and y are copied; the
+ * one-time Gram matrix X^T X (Sect. 5, beta update, step i) is formed in FP64
+ * on the GPU.  Returns NULL on error; hs_probit_last_error() gives the status. */
+hs_probit* hs_probit_init(const float* X, const uint8_t* y, int64_t N, int64_t p,
+                          uint64_t seed);
+
+/* As hs_probit_init with a configuration.  X is of type cfg->x_dtype (double,
+ * float, uint16 bf16 bits or uint8 e4m3 codes), host or device per
+ * cfg->x_is_device; X is copied, never adopted.  For HS_X_FP8E4M3 the value of
+ * X[i][j] is x_scales[j] * e4m3(X[i][j]).  cfg may be NULL (defaults). */
+hs_probit* hs_probit_init_ex(const hs_probit_config* cfg, const void* X, const uint8_t* y,
+                             int64_t N, int64_t p, uint64_t seed);
+
+/* Status of the last failed hs_probit_init / hs_probit_init_ex in this thread. */
+int hs_probit_last_error(void);
+
+/* Static text for a status code. */
+const char* hs_probit_status_string(int status);
+
+/* Run n_iter >= 0 Gibbs sweeps (Sect. 5, schedule (i)-(ii)) on the handle's
+ * stream and wait for them.  Returns HS_OK, or the first device error seen
+ * (HS_ENOTPD, HS_ENONFINITE, HS_ETIMEOUT).  After an error the state stays at
+ * the last good sweep and further sweeps return HS_ESTATE until
+ * hs_probit_set_state. */
+int hs_probit_sweep(hs_probit* h, int64_t n_iter);
+
+/* Copy the oldest undrained recorded draws into caller host arrays:
+ * beta[d * p + j], lambda_inv2[d * p + j], tau_inv2[d] for d < returned count.
+ * Any of the three pointers may be NULL.  At most max_draws are copied; draws
+ * older than the last ring_size recorded ones are lost.  Returns the count
+ * (>= 0) or a status < 0. */
+int64_t hs_probit_draws(hs_probit* h, double* beta, double* lambda_inv2, double* tau_inv2,
+                        int64_t max_draws);
+
+/* Number of recorded, undrained draws (capped at the ring size), or < 0. */
+int64_t hs_probit_draws_available(const hs_probit* h);
+
+/* Copy the current state into caller host arrays (out->beta, out->lambda_inv2,
+ * out->nu_inv must each hold p doubles; NULL arrays are skipped). */
+int hs_probit_get_state(const hs_probit* h, hs_probit_state_view* out);
+
+/* Replace the state (all three arrays required) and clear a sticky error.
+ * The next sweep is number in->k + 1.  Values are not validated beyond
+ * finiteness of the scalars; a state that makes the precision matrix
+ * indefinite is reported by the next sweep as HS_ENOTPD. */
+int hs_probit_set_state(hs_probit* h, const hs_probit_state_view* in);
+
+/* z of the last sweep (N doubles, host), if the handle was made with debug = 1. */
+int hs_probit_debug_z(hs_probit* h, double* z_out);
+
+/* X^T z of the last sweep (p doubles, host), if made with debug = 1. */
+int hs_probit_debug_xtz(hs_probit* h, double* xtz_out);
+
+/* The Gram matrix X^T X in FP64 (p x p row-major, host). */
+int hs_probit_gram(hs_probit* h, double* G_out);
+
+/* Sizes of the handle: N, p and the CUDA stream the sweep runs on
+ * (cudaStream_t as void*).  Any out pointer may be NULL. */
+int hs_probit_info(const hs_probit* h, int64_t* N, int64_t* p, void** stream);
+
+/* Profiling.  While on, sweeps launch eagerly (no graph) and CUDA events on
+ * the launching stream bracket each kernel group; hs_probit_kernel_time
+ * returns the summed milliseconds and the number of launches timed since
+ * profiling was switched on.  which: 0 X-stream kernel, 1 X^T z reduce,
+ * 2 lambda/tau kernel, 3 Cholesky+inverse branch (all its launches),
+ * 4 beta/nu/xi tail, 5 Gram (setup). */
+int hs_probit_set_profiling(hs_probit* h, int on);
+int hs_probit_kernel_time(hs_probit* h, int which, double* total_ms, int64_t* launches);
+
+/* Number of kernel launches one sweep makes (for launch accounting). */
+int64_t hs_probit_launches_per_sweep(const hs_probit* h);
+
+/* Failure-path test hook: run a kernel that waits, at most max_spins polls,
+ * on a device flag that nothing sets.  Returns HS_ETIMEOUT (the wait ran out
+ * and the kernel returned normally) or HS_ECUDA.  Does not touch the state. */
+int hs_probit_debug_wait_timeout(hs_probit* h, int64_t max_spins);
+
+/* Release the handle and everything it owns.  NULL is allowed. */
+void hs_probit_free(hs_probit* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HS_PROBIT_H */

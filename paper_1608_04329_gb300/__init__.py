@@ -1,0 +1,283 @@
+"""GB300 (sm_103a) Gibbs sampler for Horseshoe probit regression.
+
+Python binding of ``lib/libhs_probit.so``, whose C ABI is declared in
+``include/hs_probit.h``.  The binding only marshals arguments: every step of a
+sweep runs in the library's CUDA kernels.  If the library is missing or cannot
+be loaded, every entry point raises; there is no CPU fallback.
+
+Model (Terenin, Dong & Draper, Sect. 5): probit likelihood through latent z
+(Eq. 9), horseshoe prior (Eq. 10), full conditionals of Eq. 12, sampled in the
+order (i) z and lambda^{-2}, then tau^{-2}; (ii) beta, nu^{-1}, xi^{-1}.
+
+    import numpy as np, paper_1608_04329_gb300 as hs
+    s = hs.HSProbit(X.astype(np.float32), y, seed=0)
+    s.sweep(1000)
+    d = s.draws()            # {"beta": (n, p), "lambda_inv2": (n, p), "tau_inv2": (n,)}
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["HSProbit", "HSProbitError", "load_library", "library_path", "STATUS",
+           "X_F64", "X_F32", "X_BF16", "X_FP8E4M3", "CHOL_F64", "CHOL_DF32"]
+
+X_F64, X_F32, X_BF16, X_FP8E4M3 = 0, 1, 2, 3
+CHOL_F64, CHOL_DF32 = 0, 1
+STATUS = {0: "HS_OK", -1: "HS_EINVAL", -2: "HS_ENOMEM", -3: "HS_ECUDA", -4: "HS_ENOTPD",
+          -5: "HS_ENONFINITE", -6: "HS_ETIMEOUT", -7: "HS_ESTATE", -8: "HS_EUNSUPPORTED"}
+KERNEL_GROUPS = {"xstream": 0, "reduce": 1, "shrink": 2, "cholesky": 3, "tail": 4, "gram": 5}
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+
+
+def library_path() -> str:
+    return os.path.join(_PKG, "lib", "libhs_probit.so")
+
+
+class HSProbitError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {STATUS.get(int(status), status)} ({int(status)})")
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("x_dtype", ctypes.c_int32), ("x_is_device", ctypes.c_int32), ("thin", ctypes.c_int32),
+                ("ring_size", ctypes.c_int32), ("debug", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("chol_arith", ctypes.c_int32), ("device", ctypes.c_int32), ("chain", ctypes.c_uint32),
+                ("problem", ctypes.c_uint32), ("stream", ctypes.c_void_p), ("x_scales", ctypes.c_void_p),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class _StateView(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_void_p), ("lambda_inv2", ctypes.c_void_p), ("nu_inv", ctypes.c_void_p),
+                ("tau_inv2", ctypes.c_double), ("xi_inv", ctypes.c_double), ("k", ctypes.c_int64)]
+
+
+_LIB = None
+
+# name -> (restype, argtypes)
+_PROTOS = {
+    "hs_probit_config_default": (None, [ctypes.POINTER(_Config)]),
+    "hs_probit_init": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_uint64]),
+    "hs_probit_init_ex": (ctypes.c_void_p, [ctypes.POINTER(_Config), ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64]),
+    "hs_probit_last_error": (ctypes.c_int, []),
+    "hs_probit_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "hs_probit_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "hs_probit_draws": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int64]),
+    "hs_probit_draws_available": (ctypes.c_int64, [ctypes.c_void_p]),
+    "hs_probit_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_StateView)]),
+    "hs_probit_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_StateView)]),
+    "hs_probit_debug_z": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hs_probit_debug_xtz": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hs_probit_gram": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hs_probit_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_void_p)]),
+    "hs_probit_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hs_probit_kernel_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_int64)]),
+    "hs_probit_launches_per_sweep": (ctypes.c_int64, [ctypes.c_void_p]),
+    "hs_probit_debug_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "hs_probit_free": (None, [ctypes.c_void_p]),
+}
+
+
+def load_library(path: str | None = None):
+    """Load libhs_probit.so (raises if it is missing: there is no fallback)."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                           "g.build()'` (needs nvcc); this package has no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _PROTOS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path == library_path():
+        _LIB = lib
+    return lib
+
+
+def _ptr(a: np.ndarray) -> ctypes.c_void_p:
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _infer_dtype(X) -> int:
+    name = str(getattr(X, "dtype", ""))
+    if name.endswith("float64"):
+        return X_F64
+    if name.endswith("float32"):
+        return X_F32
+    if name.endswith("bfloat16") or name.endswith("uint16"):
+        return X_BF16
+    if "float8_e4m3" in name or name.endswith("uint8"):
+        return X_FP8E4M3
+    raise ValueError(f"unsupported X dtype {name}")
+
+
+class HSProbit:
+    """One Horseshoe-probit Gibbs chain on one GPU.
+
+    X: N x p row-major.  A numpy array (host) or a torch tensor (host or CUDA
+    device memory; device tensors are copied by the library on the device).
+    Element type: float64, float32, bfloat16 (torch) / uint16 bit patterns, or
+    e4m3 (torch float8_e4m3fn / uint8 codes) with ``scales`` (p float32).
+    y: N values in {0, 1} (uint8), on the same side (host/device) as X.
+    """
+
+    def __init__(self, X, y, seed: int = 0, *, scales=None, thin: int = 1, ring_size: int = 1024,
+                 debug: bool = False, use_graph: bool = False, chol_arith: int = CHOL_DF32, chain: int = 0,
+                 problem: int = 0, stream=None, device: int = 0, x_dtype: int | None = None):
+        self._lib = load_library()
+        self._h = None
+        is_dev = hasattr(X, "is_cuda") and bool(X.is_cuda)
+        dt = _infer_dtype(X) if x_dtype is None else int(x_dtype)
+        self._keep = []
+        if hasattr(X, "data_ptr"):
+            Xc = X.contiguous()
+            yc = y.contiguous()
+            self._keep += [Xc, yc]
+            xptr, yptr = ctypes.c_void_p(Xc.data_ptr()), ctypes.c_void_p(yc.data_ptr())
+            N, p = int(Xc.shape[0]), int(Xc.shape[1])
+        else:
+            Xc = np.ascontiguousarray(X)
+            yc = np.ascontiguousarray(y, dtype=np.uint8)
+            self._keep += [Xc, yc]
+            xptr, yptr = _ptr(Xc), _ptr(yc)
+            N, p = Xc.shape
+        cfg = _Config()
+        self._lib.hs_probit_config_default(ctypes.byref(cfg))
+        cfg.x_dtype = dt
+        cfg.x_is_device = 1 if is_dev else 0
+        cfg.thin = thin
+        cfg.ring_size = ring_size
+        cfg.debug = 1 if debug else 0
+        cfg.use_graph = 1 if use_graph else 0
+        cfg.chol_arith = chol_arith
+        cfg.device = device
+        cfg.chain = chain
+        cfg.problem = problem
+        cfg.stream = ctypes.c_void_p(int(stream)) if stream is not None else None
+        if scales is not None:
+            if hasattr(scales, "data_ptr"):
+                sc = scales.contiguous()
+                cfg.x_scales = ctypes.c_void_p(sc.data_ptr())
+            else:
+                sc = np.ascontiguousarray(scales, dtype=np.float32)
+                cfg.x_scales = ctypes.c_void_p(sc.ctypes.data)
+            self._keep.append(sc)
+        h = self._lib.hs_probit_init_ex(ctypes.byref(cfg), xptr, yptr, N, p, ctypes.c_uint64(seed & (2**64 - 1)))
+        if not h:
+            raise HSProbitError(self._lib.hs_probit_last_error(), "hs_probit_init_ex")
+        self._h = ctypes.c_void_p(h)
+        self._keep = []
+        self.N, self.p, self.seed, self.x_dtype = int(N), int(p), int(seed), dt
+
+    # ---- core ----
+    def sweep(self, n: int = 1) -> None:
+        st = self._lib.hs_probit_sweep(self._h, int(n))
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_sweep")
+
+    def sweep_status(self, n: int = 1) -> int:
+        return int(self._lib.hs_probit_sweep(self._h, int(n)))
+
+    def draws(self, max_draws: int | None = None) -> dict:
+        avail = int(self._lib.hs_probit_draws_available(self._h))
+        n = avail if max_draws is None else min(avail, int(max_draws))
+        beta = np.empty((n, self.p))
+        lam = np.empty((n, self.p))
+        tau = np.empty(n)
+        got = self._lib.hs_probit_draws(self._h, _ptr(beta), _ptr(lam), _ptr(tau), n)
+        if got < 0:
+            raise HSProbitError(got, "hs_probit_draws")
+        return {"beta": beta[:got], "lambda_inv2": lam[:got], "tau_inv2": tau[:got]}
+
+    def get_state(self) -> dict:
+        beta, lam, nu = np.empty(self.p), np.empty(self.p), np.empty(self.p)
+        v = _StateView(_ptr(beta).value, _ptr(lam).value, _ptr(nu).value, 0.0, 0.0, 0)
+        st = self._lib.hs_probit_get_state(self._h, ctypes.byref(v))
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_get_state")
+        return {"beta": beta, "lambda_inv2": lam, "nu_inv": nu, "tau_inv2": v.tau_inv2, "xi_inv": v.xi_inv,
+                "k": int(v.k)}
+
+    def set_state(self, beta, lambda_inv2, nu_inv, tau_inv2, xi_inv, k) -> None:
+        b = np.ascontiguousarray(beta, dtype=np.float64)
+        l_ = np.ascontiguousarray(lambda_inv2, dtype=np.float64)
+        n_ = np.ascontiguousarray(nu_inv, dtype=np.float64)
+        if b.shape != (self.p,) or l_.shape != (self.p,) or n_.shape != (self.p,):
+            raise ValueError("state arrays must have length p")
+        v = _StateView(_ptr(b).value, _ptr(l_).value, _ptr(n_).value, float(tau_inv2), float(xi_inv), int(k))
+        st = self._lib.hs_probit_set_state(self._h, ctypes.byref(v))
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_set_state")
+
+    # ---- debug / inspection ----
+    def debug_z(self) -> np.ndarray:
+        z = np.empty(self.N)
+        st = self._lib.hs_probit_debug_z(self._h, _ptr(z))
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_debug_z")
+        return z
+
+    def debug_xtz(self) -> np.ndarray:
+        v = np.empty(self.p)
+        st = self._lib.hs_probit_debug_xtz(self._h, _ptr(v))
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_debug_xtz")
+        return v
+
+    def gram(self) -> np.ndarray:
+        G = np.empty((self.p, self.p))
+        st = self._lib.hs_probit_gram(self._h, _ptr(G))
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_gram")
+        return G
+
+    def stream(self) -> int:
+        s = ctypes.c_void_p()
+        self._lib.hs_probit_info(self._h, None, None, ctypes.byref(s))
+        return int(s.value or 0)
+
+    def set_profiling(self, on: bool) -> None:
+        self._lib.hs_probit_set_profiling(self._h, 1 if on else 0)
+
+    def kernel_time(self, group: str):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        st = self._lib.hs_probit_kernel_time(self._h, KERNEL_GROUPS[group], ctypes.byref(ms), ctypes.byref(n))
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_kernel_time")
+        return float(ms.value), int(n.value)
+
+    def launches_per_sweep(self) -> int:
+        return int(self._lib.hs_probit_launches_per_sweep(self._h))
+
+    def debug_wait_timeout(self, max_spins: int) -> int:
+        return int(self._lib.hs_probit_debug_wait_timeout(self._h, int(max_spins)))
+
+    def close(self) -> None:
+        if self._h is not None and self._lib is not None:
+            self._lib.hs_probit_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

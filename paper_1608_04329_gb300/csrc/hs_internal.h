@@ -1,0 +1,138 @@
+// Host-side declarations shared by the translation units of the library
+// (kernel launchers and their parameter blocks).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hs {
+
+// ---- device error word bits (atomicOr into one int) -----------------------
+enum : int {
+  kErrNonFinite = 1,   // non-finite eta, z or beta
+  kErrNotPD = 2,       // non-positive pivot in the Cholesky factor
+  kErrTimeout = 4,     // a bounded wait ran out
+  kErrGamma = 8,       // Cheng's sampler found no acceptance in its round cap
+  kErrBadY = 16,       // a y value outside {0, 1}
+};
+
+// Philox key and the fixed parts of the counter.
+struct RngKey {
+  uint32_t k0, k1, chain, problem;
+};
+
+// ---- X-stream: eta = X beta, z ~ TN, per-CTA partial sums of X^T z ---------
+struct XStreamArgs {
+  const void* X;         // N x ld storage type, rows 16-byte aligned, pads zero
+  const uint8_t* y;      // N
+  int64_t N;
+  int ld;                // row stride in elements (multiple of 16 bytes)
+  int p;
+  const void* beta_c;    // ld values of the compute type (double or float)
+  void* partials;        // grid x ld compute-type partial sums (written)
+  double* z_out;         // N, or nullptr
+  const int64_t* k_dev;  // sweeps done; this sweep is *k_dev + 1
+  RngKey rng;
+  int* err;
+};
+
+// Per-process kernel attributes (shared-memory carveout); call before launching.
+cudaError_t xstream_prepare();
+cudaError_t linalg_prepare();
+
+// Persistent grid size (CTAs) the X-stream kernel uses for this shape.
+int xstream_grid(int x_dtype, int p, int ld, int64_t N, int num_sms);
+// Launch; returns cudaSuccess or the launch error.
+cudaError_t xstream_launch(int x_dtype, const XStreamArgs& a, int grid, cudaStream_t s);
+// Size in bytes of one partials row element (8 for F64 X, 4 otherwise).
+int partial_elem_bytes(int x_dtype);
+
+// X^T z = sum over CTAs of the partials (fixed order, FP64), times the column scale.
+cudaError_t reduce_partials_launch(int x_dtype, const void* partials, int grid, int ld, int p,
+                                   const float* colscale, double* xtz, cudaStream_t s);
+
+// G = X^T X (p x p, FP64, row-major, full), X as stored (scaled for FP8).
+cudaError_t gram_launch(int x_dtype, const void* X, int64_t N, int ld, int p,
+                        const float* colscale, double* G, cudaStream_t s);
+
+// y must be 0/1: sets kErrBadY in err otherwise.
+cudaError_t check_y_launch(const uint8_t* y, int64_t N, int* err, cudaStream_t s);
+
+// ---- shrinkage: lambda^{-2} (Exp), tau^{-2} (Cheng GB) and the scaling -------
+struct ShrinkArgs {
+  int p, P;
+  RngKey rng;
+  const int64_t* k_dev;
+  const double* beta;     // current beta
+  const double* lam;      // current lambda^{-2} (read only)
+  const double* nu;       // current nu^{-1}
+  const double* scal;     // [0] tau^{-2}, [1] xi^{-1} (current)
+  double* lam_new;        // written
+  double* tau_new;        // written (one value)
+  const double* G;        // p x p (diagonal read)
+  double* S;              // P: 1/sqrt(A_jj) rounded to FP32 (1 for padded j)
+  double* part;           // ceil(p / 128) block partial sums (scratch)
+  unsigned int* ticket;   // zero between sweeps (scratch)
+  int* err;
+};
+cudaError_t shrink_launch(const ShrinkArgs& a, cudaStream_t s);
+
+// ---- Cholesky of A = G + tau^{-2} Lambda^{-2} (scaled) and its inverse ------
+struct CholArgs {
+  int p, P;               // P = number of tiles * tile size
+  const double* G;        // p x p
+  const double* S;        // P
+  const double* lam_new;  // p
+  const double* tau_new;  // 1
+  void* A;                // P x P workspace (double, or FP32 pairs); lower part becomes L~
+  void* Linv;             // P x P; lower part becomes L~^{-1}
+  void* LinvT;            // P x P; upper part becomes L~^{-T}
+  int* err;
+  int arith;              // HS_CHOL_*
+};
+// Enqueues the whole factorization (several launches); returns the count.
+cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches);
+int chol_launch_count(int P, int arith);
+
+// ---- beta tail, nu/xi, commit ----------------------------------------------
+struct TailArgs {
+  int p, P, ld;
+  RngKey rng;
+  const int64_t* k_dev;
+  const double* xtz;       // p
+  const double* S;         // P
+  const void* Linv;        // P x P lower (double, or FP32 pairs when df32)
+  const void* LinvT;       // P x P upper (same storage)
+  int df32;
+  double* v;               // P scratch: L^{-1} X^T z + s
+  double* beta_new;        // p
+  double* nu_new;          // p
+  const double* lam_new;   // p
+  const double* tau_new;   // 1
+  // state committed when the error word is clear
+  double* beta;            // p
+  double* lam;             // p
+  double* nu;              // p
+  double* scal;            // [0] tau^{-2}, [1] xi^{-1}
+  int64_t* k_dev_rw;       // incremented on commit
+  void* beta_c;            // ld compute-type copy of beta (times column scale)
+  int beta_c_is_double;
+  const float* colscale;   // p or nullptr
+  double* ring_beta;       // ring x p
+  double* ring_lam;        // ring x p
+  double* ring_tau;        // ring
+  int ring_size, thin;
+  int* err;
+};
+cudaError_t tail_enqueue(const TailArgs& a, cudaStream_t s, int* launches);
+constexpr int kTailLaunches = 3;
+
+// beta_c = (compute type)(beta * colscale), pads zero.
+cudaError_t beta_c_launch(const double* beta, const float* colscale, int p, int ld, void* beta_c,
+                          int is_double, cudaStream_t s);
+
+// Test hook: wait on a device flag nothing sets, at most max_spins polls.
+cudaError_t wait_timeout_launch(int* flag, int64_t max_spins, int* err, cudaStream_t s);
+
+
+}  // namespace hs

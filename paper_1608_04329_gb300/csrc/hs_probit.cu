@@ -1,0 +1,754 @@
+// Host runtime and C ABI of the Horseshoe-probit Gibbs sweep.
+//
+// One handle holds the data (X in its storage type with 16-byte aligned rows,
+// y, optional column scales), the one-time Gram matrix, the sampler state
+// (beta, lambda^{-2}, nu^{-1}, tau^{-2}, xi^{-1}, sweep count k) and the work
+// buffers, all in device memory it owns.  A sweep is a fork/join DAG on two
+// streams: the X-stream (and the reduce of its partial sums) on the main
+// stream runs concurrently with the lambda/tau kernel and the Cholesky branch
+// on a side stream, which depend only on the previous state (Sect. 5,
+// schedule (i)-(ii): z and lambda first, tau next, then beta, nu, xi).  The
+// beta tail joins both.  The DAG can be captured once as a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hs_internal.h"
+#include "hs_probit.h"
+
+namespace {
+
+thread_local int g_last_error = HS_OK;
+
+constexpr int kMaxP = 8192;
+constexpr int kProfGroups = 6;
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = (cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int elem_bytes_of(int dt) {
+  switch (dt) {
+    case HS_X_F64: return 8;
+    case HS_X_F32: return 4;
+    case HS_X_BF16: return 2;
+    case HS_X_FP8E4M3: return 1;
+  }
+  return 0;
+}
+
+}  // namespace
+
+struct hs_probit {
+  hs_probit_config cfg{};
+  int device = 0;
+  int x_dtype = HS_X_F32;
+  int64_t N = 0;
+  int p = 0, ld = 0, P = 0, T = 0;
+  int elem = 4;
+  hs::RngKey rng{};
+  cudaStream_t s0 = nullptr, s1 = nullptr;
+  bool own_s0 = false;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::vector<void*> allocs;
+
+  void* X = nullptr;
+  uint8_t* y = nullptr;
+  float* colscale = nullptr;
+  double *beta = nullptr, *lam = nullptr, *nu = nullptr, *scal = nullptr;
+  int64_t* k_dev = nullptr;
+  double *lam_new = nullptr, *tau_new = nullptr, *beta_new = nullptr, *nu_new = nullptr;
+  void* beta_c = nullptr;
+  double *G = nullptr, *S = nullptr, *A = nullptr, *Linv = nullptr, *LinvT = nullptr;
+  double *xtz = nullptr, *v = nullptr;
+  double* shrink_part = nullptr;
+  unsigned int* shrink_ticket = nullptr;
+  void* partials = nullptr;
+  int grid = 1;
+  double* z = nullptr;
+  double *ring_beta = nullptr, *ring_lam = nullptr, *ring_tau = nullptr;
+  int ring_size = 1, thin = 1;
+  int* err = nullptr;
+  int* hook_err = nullptr;
+  int* hook_flag = nullptr;
+  int* h_err = nullptr;      // pinned
+  int64_t* h_k = nullptr;    // pinned
+
+  int sticky = HS_OK;
+  int64_t k_host = 0;
+  int64_t drained = 0;       // draws (index k/thin) already handed out
+  int64_t launches = 0;
+
+  bool graph_ready = false;
+  cudaGraphExec_t gexec = nullptr;
+
+  int profiling = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  double prof_ms[kProfGroups] = {0};
+  int64_t prof_n[kProfGroups] = {0};
+
+  template <typename T>
+  cudaError_t alloc(T** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
+    if (e == cudaSuccess) {
+      allocs.push_back(q);
+      *p = static_cast<T*>(q);
+    }
+    return e;
+  }
+  cudaEvent_t take_event() {
+    if (!ev_pool.empty()) {
+      cudaEvent_t e = ev_pool.back();
+      ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+
+namespace {
+
+int fail(int status) {
+  g_last_error = status;
+  return status;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return HS_OK;
+  if (e == cudaErrorMemoryAllocation) return HS_ENOMEM;
+  return HS_ECUDA;
+}
+
+int status_from_err_bits(int bits) {
+  if (bits & hs::kErrNonFinite) return HS_ENONFINITE;
+  if (bits & hs::kErrNotPD) return HS_ENOTPD;
+  if (bits & hs::kErrTimeout) return HS_ETIMEOUT;
+  if (bits & hs::kErrGamma) return HS_ENONFINITE;
+  if (bits & hs::kErrBadY) return HS_EINVAL;
+  return HS_ECUDA;
+}
+
+hs::XStreamArgs xstream_args(hs_probit* h) {
+  hs::XStreamArgs a{};
+  a.X = h->X;
+  a.y = h->y;
+  a.N = h->N;
+  a.ld = h->ld;
+  a.p = h->p;
+  a.beta_c = h->beta_c;
+  a.partials = h->partials;
+  a.z_out = h->cfg.debug ? h->z : nullptr;
+  a.k_dev = h->k_dev;
+  a.rng = h->rng;
+  a.err = h->err;
+  return a;
+}
+
+hs::ShrinkArgs shrink_args(hs_probit* h) {
+  hs::ShrinkArgs a{};
+  a.p = h->p;
+  a.P = h->P;
+  a.rng = h->rng;
+  a.k_dev = h->k_dev;
+  a.beta = h->beta;
+  a.lam = h->lam;
+  a.nu = h->nu;
+  a.scal = h->scal;
+  a.lam_new = h->lam_new;
+  a.tau_new = h->tau_new;
+  a.G = h->G;
+  a.S = h->S;
+  a.part = h->shrink_part;
+  a.ticket = h->shrink_ticket;
+  a.err = h->err;
+  return a;
+}
+
+hs::CholArgs chol_args(hs_probit* h) {
+  hs::CholArgs a{};
+  a.p = h->p;
+  a.P = h->P;
+  a.G = h->G;
+  a.S = h->S;
+  a.lam_new = h->lam_new;
+  a.tau_new = h->tau_new;
+  a.A = h->A;
+  a.Linv = h->Linv;
+  a.LinvT = h->LinvT;
+  a.err = h->err;
+  a.arith = h->cfg.chol_arith;
+  return a;
+}
+
+hs::TailArgs tail_args(hs_probit* h) {
+  hs::TailArgs a{};
+  a.p = h->p;
+  a.P = h->P;
+  a.ld = h->ld;
+  a.rng = h->rng;
+  a.k_dev = h->k_dev;
+  a.xtz = h->xtz;
+  a.S = h->S;
+  a.Linv = h->Linv;
+  a.LinvT = h->LinvT;
+  a.df32 = (h->cfg.chol_arith == HS_CHOL_DF32);
+  a.v = h->v;
+  a.beta_new = h->beta_new;
+  a.nu_new = h->nu_new;
+  a.lam_new = h->lam_new;
+  a.tau_new = h->tau_new;
+  a.beta = h->beta;
+  a.lam = h->lam;
+  a.nu = h->nu;
+  a.scal = h->scal;
+  a.k_dev_rw = h->k_dev;
+  a.beta_c = h->beta_c;
+  a.beta_c_is_double = (h->x_dtype == HS_X_F64);
+  a.colscale = h->colscale;
+  a.ring_beta = h->ring_beta;
+  a.ring_lam = h->ring_lam;
+  a.ring_tau = h->ring_tau;
+  a.ring_size = h->ring_size;
+  a.thin = h->thin;
+  a.err = h->err;
+  return a;
+}
+
+// Record a profiling event pair around a group on a stream.
+struct ProfSpan {
+  hs_probit* h;
+  int group;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr;
+  ProfSpan(hs_probit* hh, int g, cudaStream_t ss) : h(hh), group(g), s(ss) {
+    if (h->profiling) {
+      e0 = h->take_event();
+      cudaEventRecord(e0, s);
+    }
+  }
+  ~ProfSpan() {
+    if (h->profiling && e0) {
+      cudaEvent_t e1 = h->take_event();
+      cudaEventRecord(e1, s);
+      h->pending.push_back({group, {e0, e1}});
+    }
+  }
+};
+
+// Enqueue one sweep (eager launches).  Returns a CUDA error or success.
+cudaError_t enqueue_sweep(hs_probit* h) {
+  cudaError_t e;
+  int n = 0;
+  if ((e = cudaEventRecord(h->ev_fork, h->s0)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(h->s1, h->ev_fork, 0)) != cudaSuccess) return e;
+  {
+    ProfSpan sp(h, 2, h->s1);
+    if ((e = hs::shrink_launch(shrink_args(h), h->s1)) != cudaSuccess) return e;
+  }
+  {
+    ProfSpan sp(h, 3, h->s1);
+    int nl = 0;
+    if ((e = hs::chol_enqueue(chol_args(h), h->s1, &nl)) != cudaSuccess) return e;
+    n += nl;
+  }
+  if ((e = cudaEventRecord(h->ev_join, h->s1)) != cudaSuccess) return e;
+  {
+    ProfSpan sp(h, 0, h->s0);
+    if ((e = hs::xstream_launch(h->x_dtype, xstream_args(h), h->grid, h->s0)) != cudaSuccess) return e;
+  }
+  {
+    ProfSpan sp(h, 1, h->s0);
+    if ((e = hs::reduce_partials_launch(h->x_dtype, h->partials, h->grid, h->ld, h->p, h->colscale, h->xtz,
+                                        h->s0)) != cudaSuccess)
+      return e;
+  }
+  if ((e = cudaStreamWaitEvent(h->s0, h->ev_join, 0)) != cudaSuccess) return e;
+  {
+    ProfSpan sp(h, 4, h->s0);
+    int nl = 0;
+    if ((e = hs::tail_enqueue(tail_args(h), h->s0, &nl)) != cudaSuccess) return e;
+    n += nl;
+  }
+  (void)n;
+  return cudaSuccess;
+}
+
+cudaError_t build_graph(hs_probit* h) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->s0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const int saved = h->profiling;
+  h->profiling = 0;
+  cudaError_t e2 = enqueue_sweep(h);
+  h->profiling = saved;
+  e = cudaStreamEndCapture(h->s0, &g);
+  if (e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return e2;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(&h->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e == cudaSuccess) h->graph_ready = true;
+  return e;
+}
+
+void collect_profile(hs_probit* h) {
+  for (auto& pe : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
+      h->prof_ms[pe.first] += ms;
+      h->prof_n[pe.first] += 1;
+    }
+    h->ev_pool.push_back(pe.second.first);
+    h->ev_pool.push_back(pe.second.second);
+  }
+  h->pending.clear();
+  (void)cudaGetLastError();
+}
+
+void destroy(hs_probit* h) {
+  if (!h) return;
+  if (h->s0) cudaStreamSynchronize(h->s0);
+  if (h->s1) cudaStreamSynchronize(h->s1);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (auto& pe : h->pending) {
+    h->ev_pool.push_back(pe.second.first);
+    h->ev_pool.push_back(pe.second.second);
+  }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->h_k) cudaFreeHost(h->h_k);
+  if (h->s1) cudaStreamDestroy(h->s1);
+  if (h->own_s0 && h->s0) cudaStreamDestroy(h->s0);
+  (void)cudaGetLastError();
+  delete h;
+}
+
+int sync_and_check(hs_probit* h) {
+  cudaError_t e = cudaMemcpyAsync(h->h_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->s0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_k, h->k_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, h->s0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s0);
+  if (e != cudaSuccess) return cuda_status(e);
+  h->k_host = *h->h_k;
+  if (*h->h_err) return status_from_err_bits(*h->h_err);
+  return HS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hs_probit_config_default(hs_probit_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->x_dtype = HS_X_F32;
+  cfg->x_is_device = 0;
+  cfg->thin = 1;
+  cfg->ring_size = 1024;
+  cfg->debug = 0;
+  cfg->use_graph = 0;
+  cfg->chol_arith = HS_CHOL_DF32;
+  cfg->device = 0;
+}
+
+int hs_probit_last_error(void) { return g_last_error; }
+
+const char* hs_probit_status_string(int status) {
+  switch (status) {
+    case HS_OK: return "ok";
+    case HS_EINVAL: return "invalid argument";
+    case HS_ENOMEM: return "out of memory";
+    case HS_ECUDA: return "CUDA runtime error";
+    case HS_ENOTPD: return "precision matrix not positive definite";
+    case HS_ENONFINITE: return "non-finite value in the sweep";
+    case HS_ETIMEOUT: return "bounded device wait ran out";
+    case HS_ESTATE: return "handle in error state (call hs_probit_set_state)";
+    case HS_EUNSUPPORTED: return "unsupported option";
+  }
+  return "unknown status";
+}
+
+hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, const uint8_t* y, int64_t N,
+                             int64_t p, uint64_t seed) {
+  g_last_error = HS_OK;
+  hs_probit_config cfg;
+  if (cfg_in)
+    cfg = *cfg_in;
+  else
+    hs_probit_config_default(&cfg);
+  // ---- argument checks (host only, before any CUDA call) ----
+  if (!X || !y || N < 2 || p < 1 || p > kMaxP || cfg.thin < 1 || cfg.ring_size < 1 ||
+      cfg.chain >= (1u << 24) || (cfg.x_dtype < HS_X_F64 || cfg.x_dtype > HS_X_FP8E4M3) ||
+      (cfg.chol_arith != HS_CHOL_F64 && cfg.chol_arith != HS_CHOL_DF32) || N > (int64_t)0xFFFFFFFF) {
+    fail(HS_EINVAL);
+    return nullptr;
+  }
+  if (cfg.x_dtype == HS_X_FP8E4M3 && !cfg.x_scales) {
+    fail(HS_EINVAL);
+    return nullptr;
+  }
+  if (!cfg.x_is_device) {
+    for (int64_t i = 0; i < N; ++i)
+      if (y[i] > 1) {
+        fail(HS_EINVAL);
+        return nullptr;
+      }
+    if (cfg.x_dtype == HS_X_FP8E4M3)
+      for (int64_t j = 0; j < p; ++j)
+        if (!(std::isfinite(cfg.x_scales[j]) && cfg.x_scales[j] > 0.f)) {
+          fail(HS_EINVAL);
+          return nullptr;
+        }
+  }
+  DeviceGuard dg(cfg.device);
+  if (!dg.ok) {
+    fail(HS_ECUDA);
+    return nullptr;
+  }
+  hs_probit* h = new (std::nothrow) hs_probit();
+  if (!h) {
+    fail(HS_ENOMEM);
+    return nullptr;
+  }
+  h->cfg = cfg;
+  h->device = cfg.device;
+  h->x_dtype = cfg.x_dtype;
+  h->N = N;
+  h->p = (int)p;
+  h->elem = elem_bytes_of(cfg.x_dtype);
+  const int ve = 16 / h->elem;
+  h->ld = (int)((p + ve - 1) / ve * ve);
+  h->T = (int)((p + 31) / 32);
+  h->P = h->T * 32;
+  h->rng = hs::RngKey{(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), cfg.chain, cfg.problem};
+  h->ring_size = cfg.ring_size;
+  h->thin = cfg.thin;
+
+  cudaError_t e = cudaSuccess;
+  auto check = [&](cudaError_t ee) {
+    if (e == cudaSuccess && ee != cudaSuccess) e = ee;
+    return e == cudaSuccess;
+  };
+  int num_sms = 0;
+  check(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  check(hs::xstream_prepare());
+  check(hs::linalg_prepare());
+  if (cfg.stream) {
+    h->s0 = static_cast<cudaStream_t>(cfg.stream);
+  } else {
+    check(cudaStreamCreateWithFlags(&h->s0, cudaStreamNonBlocking));
+    h->own_s0 = true;
+  }
+  check(cudaStreamCreateWithFlags(&h->s1, cudaStreamNonBlocking));
+  check(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  check(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  const size_t P2 = (size_t)h->P * h->P;
+  const size_t pd = (size_t)p * sizeof(double);
+  h->grid = hs::xstream_grid(h->x_dtype, h->p, h->ld, N, num_sms > 0 ? num_sms : 1);
+  check(h->alloc(&h->X, (size_t)N * h->ld * h->elem));
+  check(h->alloc(&h->y, (size_t)N));
+  if (cfg.x_dtype == HS_X_FP8E4M3) check(h->alloc(&h->colscale, (size_t)p * sizeof(float)));
+  check(h->alloc(&h->beta, pd));
+  check(h->alloc(&h->lam, pd));
+  check(h->alloc(&h->nu, pd));
+  check(h->alloc(&h->scal, 2 * sizeof(double)));
+  check(h->alloc(&h->k_dev, sizeof(int64_t)));
+  check(h->alloc(&h->lam_new, pd));
+  check(h->alloc(&h->tau_new, sizeof(double)));
+  check(h->alloc(&h->beta_new, pd));
+  check(h->alloc(&h->nu_new, pd));
+  check(h->alloc(&h->beta_c, (size_t)h->ld * (h->x_dtype == HS_X_F64 ? 8 : 4)));
+  check(h->alloc(&h->G, (size_t)p * p * sizeof(double)));
+  check(h->alloc(&h->S, (size_t)h->P * sizeof(double)));
+  check(h->alloc(&h->A, P2 * sizeof(double)));
+  check(h->alloc(&h->Linv, P2 * sizeof(double)));
+  check(h->alloc(&h->LinvT, P2 * sizeof(double)));
+  check(h->alloc(&h->xtz, pd));
+  check(h->alloc(&h->v, (size_t)h->P * sizeof(double)));
+  check(h->alloc(&h->shrink_part, (size_t)((p + 127) / 128) * sizeof(double)));
+  check(h->alloc(&h->shrink_ticket, sizeof(unsigned int)));
+  check(h->alloc(&h->partials, (size_t)h->grid * h->ld * hs::partial_elem_bytes(h->x_dtype)));
+  if (cfg.debug) check(h->alloc(&h->z, (size_t)N * sizeof(double)));
+  check(h->alloc(&h->ring_beta, (size_t)h->ring_size * pd));
+  check(h->alloc(&h->ring_lam, (size_t)h->ring_size * pd));
+  check(h->alloc(&h->ring_tau, (size_t)h->ring_size * sizeof(double)));
+  check(h->alloc(&h->err, sizeof(int)));
+  check(h->alloc(&h->hook_err, sizeof(int)));
+  check(h->alloc(&h->hook_flag, sizeof(int)));
+  if (e == cudaSuccess) check(cudaMallocHost(&h->h_err, sizeof(int)));
+  if (e == cudaSuccess) check(cudaMallocHost(&h->h_k, sizeof(int64_t)));
+  if (e != cudaSuccess) {
+    int st = cuda_status(e);
+    destroy(h);
+    fail(st);
+    return nullptr;
+  }
+  // ---- data ----
+  const cudaMemcpyKind kind = cfg.x_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  check(cudaMemsetAsync(h->X, 0, (size_t)N * h->ld * h->elem, h->s0));
+  check(cudaMemcpy2DAsync(h->X, (size_t)h->ld * h->elem, X, (size_t)p * h->elem, (size_t)p * h->elem, (size_t)N,
+                          kind, h->s0));
+  check(cudaMemcpyAsync(h->y, y, (size_t)N, kind, h->s0));
+  if (h->colscale) check(cudaMemcpyAsync(h->colscale, cfg.x_scales, (size_t)p * sizeof(float), kind, h->s0));
+  check(cudaMemsetAsync(h->err, 0, sizeof(int), h->s0));
+  check(cudaMemsetAsync(h->hook_err, 0, sizeof(int), h->s0));
+  check(cudaMemsetAsync(h->shrink_ticket, 0, sizeof(unsigned int), h->s0));
+  if (cfg.x_is_device) check(hs::check_y_launch(h->y, N, h->err, h->s0));
+  // ---- cold start (Sect. 6.1): beta = 0, lambda = nu = tau = xi = 1, k = 0 ----
+  {
+    std::vector<double> ones((size_t)p, 1.0);
+    const double sc[2] = {1.0, 1.0};
+    const int64_t k0 = 0;
+    check(cudaMemsetAsync(h->beta, 0, pd, h->s0));
+    check(cudaMemcpyAsync(h->lam, ones.data(), pd, cudaMemcpyHostToDevice, h->s0));
+    check(cudaMemcpyAsync(h->nu, ones.data(), pd, cudaMemcpyHostToDevice, h->s0));
+    check(cudaMemcpyAsync(h->scal, sc, sizeof(sc), cudaMemcpyHostToDevice, h->s0));
+    check(cudaMemcpyAsync(h->k_dev, &k0, sizeof(k0), cudaMemcpyHostToDevice, h->s0));
+    check(cudaMemsetAsync(h->beta_c, 0, (size_t)h->ld * (h->x_dtype == HS_X_F64 ? 8 : 4), h->s0));
+    check(cudaStreamSynchronize(h->s0));  // host staging buffers go out of scope
+  }
+  // ---- one-time Gram matrix (Sect. 5, beta update, step i) ----
+  {
+    ProfSpan sp(h, 5, h->s0);
+    check(hs::gram_launch(h->x_dtype, h->X, N, h->ld, h->p, h->colscale, h->G, h->s0));
+  }
+  if (e == cudaSuccess) {
+    const int st = sync_and_check(h);
+    if (st != HS_OK) {
+      destroy(h);
+      fail(st);
+      return nullptr;
+    }
+  }
+  if (e != cudaSuccess) {
+    int st = cuda_status(e);
+    destroy(h);
+    fail(st);
+    return nullptr;
+  }
+  h->launches = 1 + hs::chol_launch_count(h->P, h->cfg.chol_arith) + 2 + hs::kTailLaunches;
+  return h;
+}
+
+hs_probit* hs_probit_init(const float* X, const uint8_t* y, int64_t N, int64_t p, uint64_t seed) {
+  hs_probit_config cfg;
+  hs_probit_config_default(&cfg);
+  return hs_probit_init_ex(&cfg, X, y, N, p, seed);
+}
+
+int hs_probit_sweep(hs_probit* h, int64_t n_iter) {
+  if (!h || n_iter < 0) return HS_EINVAL;
+  if (h->sticky != HS_OK) return HS_ESTATE;
+  if (n_iter == 0) return HS_OK;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return HS_ECUDA;
+  cudaError_t e = cudaSuccess;
+  const bool graph = h->cfg.use_graph && !h->profiling;
+  if (graph && !h->graph_ready) {
+    e = build_graph(h);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
+    if (graph)
+      e = cudaGraphLaunch(h->gexec, h->s0);
+    else
+      e = enqueue_sweep(h);
+  }
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(h->s0);
+    return cuda_status(e);
+  }
+  const int st = sync_and_check(h);
+  if (h->profiling) {
+    cudaStreamSynchronize(h->s1);
+    collect_profile(h);
+  }
+  if (st != HS_OK) h->sticky = st;
+  return st;
+}
+
+int64_t hs_probit_draws_available(const hs_probit* h) {
+  if (!h) return HS_EINVAL;
+  const int64_t newest = h->k_host / h->thin;
+  int64_t first = h->drained + 1;
+  if (newest - first + 1 > h->ring_size) first = newest - h->ring_size + 1;
+  return newest >= first ? newest - first + 1 : 0;
+}
+
+int64_t hs_probit_draws(hs_probit* h, double* beta, double* lambda_inv2, double* tau_inv2, int64_t max_draws) {
+  if (!h || max_draws < 0) return HS_EINVAL;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return HS_ECUDA;
+  if (cudaStreamSynchronize(h->s0) != cudaSuccess) return HS_ECUDA;
+  const int64_t newest = h->k_host / h->thin;
+  int64_t first = h->drained + 1;
+  if (newest - first + 1 > h->ring_size) first = newest - h->ring_size + 1;
+  int64_t count = newest >= first ? newest - first + 1 : 0;
+  if (count > max_draws) count = max_draws;
+  const size_t p = (size_t)h->p;
+  for (int64_t d = 0; d < count;) {
+    const int64_t slot = (first + d - 1) % h->ring_size;
+    int64_t run = h->ring_size - slot;
+    if (run > count - d) run = count - d;
+    cudaError_t e = cudaSuccess;
+    if (beta)
+      e = cudaMemcpy(beta + d * p, h->ring_beta + slot * p, run * p * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && lambda_inv2)
+      e = cudaMemcpy(lambda_inv2 + d * p, h->ring_lam + slot * p, run * p * sizeof(double),
+                     cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && tau_inv2)
+      e = cudaMemcpy(tau_inv2 + d, h->ring_tau + slot, run * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return HS_ECUDA;
+    d += run;
+  }
+  h->drained = first + count - 1;
+  return count;
+}
+
+int hs_probit_get_state(const hs_probit* hc, hs_probit_state_view* out) {
+  hs_probit* h = const_cast<hs_probit*>(hc);
+  if (!h || !out) return HS_EINVAL;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return HS_ECUDA;
+  if (cudaStreamSynchronize(h->s0) != cudaSuccess) return HS_ECUDA;
+  const size_t pd = (size_t)h->p * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (out->beta) e = cudaMemcpy(out->beta, h->beta, pd, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && out->lambda_inv2) e = cudaMemcpy(out->lambda_inv2, h->lam, pd, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && out->nu_inv) e = cudaMemcpy(out->nu_inv, h->nu, pd, cudaMemcpyDeviceToHost);
+  double sc[2] = {0, 0};
+  int64_t k = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(sc, h->scal, sizeof(sc), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&k, h->k_dev, sizeof(k), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return HS_ECUDA;
+  out->tau_inv2 = sc[0];
+  out->xi_inv = sc[1];
+  out->k = k;
+  return HS_OK;
+}
+
+int hs_probit_set_state(hs_probit* h, const hs_probit_state_view* in) {
+  if (!h || !in || !in->beta || !in->lambda_inv2 || !in->nu_inv || in->k < 0 || !std::isfinite(in->tau_inv2) ||
+      !std::isfinite(in->xi_inv) || in->k >= (int64_t)0xFFFFFFFF)
+    return HS_EINVAL;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return HS_ECUDA;
+  if (cudaStreamSynchronize(h->s0) != cudaSuccess) return HS_ECUDA;
+  if (cudaStreamSynchronize(h->s1) != cudaSuccess) return HS_ECUDA;
+  const size_t pd = (size_t)h->p * sizeof(double);
+  const double sc[2] = {in->tau_inv2, in->xi_inv};
+  const int64_t k = in->k;
+  cudaError_t e = cudaMemcpy(h->beta, in->beta, pd, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->lam, in->lambda_inv2, pd, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->nu, in->nu_inv, pd, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->scal, sc, sizeof(sc), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->k_dev, &k, sizeof(k), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int));
+  if (e == cudaSuccess)
+    e = hs::beta_c_launch(h->beta, h->colscale, h->p, h->ld, h->beta_c, h->x_dtype == HS_X_F64 ? 1 : 0, h->s0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s0);
+  if (e != cudaSuccess) return HS_ECUDA;
+  h->sticky = HS_OK;
+  h->k_host = k;
+  h->drained = k / h->thin;
+  return HS_OK;
+}
+
+int hs_probit_debug_z(hs_probit* h, double* z_out) {
+  if (!h || !z_out) return HS_EINVAL;
+  if (!h->cfg.debug) return HS_EUNSUPPORTED;
+  DeviceGuard dg(h->device);
+  if (cudaStreamSynchronize(h->s0) != cudaSuccess) return HS_ECUDA;
+  return cuda_status(cudaMemcpy(z_out, h->z, (size_t)h->N * sizeof(double), cudaMemcpyDeviceToHost));
+}
+
+int hs_probit_debug_xtz(hs_probit* h, double* xtz_out) {
+  if (!h || !xtz_out) return HS_EINVAL;
+  if (!h->cfg.debug) return HS_EUNSUPPORTED;
+  DeviceGuard dg(h->device);
+  if (cudaStreamSynchronize(h->s0) != cudaSuccess) return HS_ECUDA;
+  return cuda_status(cudaMemcpy(xtz_out, h->xtz, (size_t)h->p * sizeof(double), cudaMemcpyDeviceToHost));
+}
+
+int hs_probit_gram(hs_probit* h, double* G_out) {
+  if (!h || !G_out) return HS_EINVAL;
+  DeviceGuard dg(h->device);
+  if (cudaStreamSynchronize(h->s0) != cudaSuccess) return HS_ECUDA;
+  return cuda_status(
+      cudaMemcpy(G_out, h->G, (size_t)h->p * h->p * sizeof(double), cudaMemcpyDeviceToHost));
+}
+
+int hs_probit_info(const hs_probit* h, int64_t* N, int64_t* p, void** stream) {
+  if (!h) return HS_EINVAL;
+  if (N) *N = h->N;
+  if (p) *p = h->p;
+  if (stream) *stream = (void*)h->s0;
+  return HS_OK;
+}
+
+int hs_probit_set_profiling(hs_probit* h, int on) {
+  if (!h) return HS_EINVAL;
+  h->profiling = on ? 1 : 0;
+  for (int i = 0; i < kProfGroups; ++i) {
+    if (on) {
+      h->prof_ms[i] = 0;
+      h->prof_n[i] = 0;
+    }
+  }
+  return HS_OK;
+}
+
+int hs_probit_kernel_time(hs_probit* h, int which, double* total_ms, int64_t* launches) {
+  if (!h || which < 0 || which >= kProfGroups) return HS_EINVAL;
+  if (total_ms) *total_ms = h->prof_ms[which];
+  if (launches) *launches = h->prof_n[which];
+  return HS_OK;
+}
+
+int64_t hs_probit_launches_per_sweep(const hs_probit* h) {
+  if (!h) return HS_EINVAL;
+  return h->launches;
+}
+
+int hs_probit_debug_wait_timeout(hs_probit* h, int64_t max_spins) {
+  if (!h || max_spins < 0) return HS_EINVAL;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return HS_ECUDA;
+  int bits = 0;
+  cudaError_t e = cudaMemsetAsync(h->hook_flag, 0, sizeof(int), h->s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->hook_err, 0, sizeof(int), h->s0);
+  if (e == cudaSuccess) e = hs::wait_timeout_launch(h->hook_flag, max_spins, h->hook_err, h->s0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_err, h->hook_err, sizeof(int), cudaMemcpyDeviceToHost, h->s0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s0);
+  if (e != cudaSuccess) return HS_ECUDA;
+  bits = *h->h_err;
+  return (bits & hs::kErrTimeout) ? HS_ETIMEOUT : HS_OK;
+}
+
+void hs_probit_free(hs_probit* h) {
+  if (!h) return;
+  DeviceGuard dg(h->device);
+  destroy(h);
+}
+
+}  // extern "C"

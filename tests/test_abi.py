@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/hs_probit.h; host-side argument checks reject bad input before any
+CUDA call (CPU only: no kernel runs here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def lib():
+    from paper_1608_04329_gb300 import _build
+    import paper_1608_04329_gb300 as pkg
+    _build.build()
+    return pkg.load_library()
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(hs_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings(lib):
+    for st in (0, -1, -2, -3, -4, -5, -6, -7, -8):
+        assert lib.hs_probit_status_string(st)
+
+
+@pytest.mark.parametrize("N,p", [(1, 5), (0, 5), (10, 0), (10, 8193)])
+def test_init_rejects_bad_sizes_on_host(lib, N, p):
+    X = np.zeros((max(N, 1), max(p, 1)), dtype=np.float32)
+    y = np.zeros(max(N, 1), dtype=np.uint8)
+    h = lib.hs_probit_init(X.ctypes.data, y.ctypes.data, N, p, 0)
+    assert not h
+    assert lib.hs_probit_last_error() == -1
+
+
+def test_init_rejects_bad_y_on_host(lib):
+    X = np.zeros((4, 2), dtype=np.float32)
+    y = np.array([0, 1, 2, 0], dtype=np.uint8)
+    assert not lib.hs_probit_init(X.ctypes.data, y.ctypes.data, 4, 2, 0)
+    assert lib.hs_probit_last_error() == -1
+
+
+def test_null_handle_is_rejected(lib):
+    assert lib.hs_probit_sweep(None, 1) == -1
+    assert lib.hs_probit_draws_available(None) == -1
+    lib.hs_probit_free(None)
+
+
+def test_config_default(lib):
+    import paper_1608_04329_gb300 as pkg
+    cfg = pkg._Config()
+    lib.hs_probit_config_default(ctypes.byref(cfg))
+    assert cfg.x_dtype == pkg.X_F32 and cfg.thin == 1 and cfg.ring_size == 1024 and cfg.use_graph == 0
