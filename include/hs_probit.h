@@ -95,7 +95,7 @@ void hs_probit_config_default(hs_probit_config* cfg);
 
 /* Create a sampler for host X (float32, N x p row-major) and host y (N bytes in
  * {0,1}) with the cold start of Sect. 6.1 (beta = 0; lambda = nu = tau = xi = 1).
- * N >= 2 (Sect. 4, Eq. 1) and 1 <= p <= 8192.  X and y are copied; the
+ * N >= 2 (Sect. 4, Eq. 1) and 1 <= p <= 8192 (4096 for FP64 X).  X and y are copied; the
  * one-time Gram matrix X^T X (Sect. 5, beta update, step i) is formed in FP64
  * on the GPU.  Returns NULL on error; hs_probit_last_error() gives the status. */
 hs_probit* hs_probit_init(const float* X, const uint8_t* y, int64_t N, int64_t p,

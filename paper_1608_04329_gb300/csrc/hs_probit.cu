@@ -407,6 +407,15 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
     fail(HS_EINVAL);
     return nullptr;
   }
+  {
+    // The X-stream takes at most 2048 16-byte slices per row (p <= 4096 for FP64 X).
+    const int64_t eb = cfg.x_dtype == HS_X_F64 ? 8 : cfg.x_dtype == HS_X_F32 ? 4 : cfg.x_dtype == HS_X_BF16 ? 2 : 1;
+    const int64_t ve = 16 / eb;
+    if ((p + ve - 1) / ve > 2048) {
+      fail(HS_EINVAL);
+      return nullptr;
+    }
+  }
   if (!cfg.x_is_device) {
     for (int64_t i = 0; i < N; ++i)
       if (y[i] > 1) {

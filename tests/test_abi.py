@@ -68,3 +68,15 @@ def test_config_default(lib):
     cfg = pkg._Config()
     lib.hs_probit_config_default(ctypes.byref(cfg))
     assert cfg.x_dtype == pkg.X_F32 and cfg.thin == 1 and cfg.ring_size == 1024 and cfg.use_graph == 0
+
+
+def test_init_rejects_fp64_rows_beyond_the_kernel(lib):
+    import paper_1608_04329_gb300 as pkg
+    cfg = pkg._Config()
+    lib.hs_probit_config_default(ctypes.byref(cfg))
+    cfg.x_dtype = pkg.X_F64
+    X = np.zeros((4, 4097), dtype=np.float64)
+    y = np.zeros(4, dtype=np.uint8)
+    assert not lib.hs_probit_init_ex(ctypes.byref(cfg), X.ctypes.data, y.ctypes.data, 4, 4097, 0)
+    assert lib.hs_probit_last_error() == -1
+
