@@ -172,6 +172,41 @@ int64_t hs_probit_launches_per_sweep(const hs_probit* h);
  * and the kernel returned normally) or HS_ECUDA.  Does not touch the state. */
 int hs_probit_debug_wait_timeout(hs_probit* h, int64_t max_spins);
 
+/* The X-stream of one sweep on caller-owned buffers, allocating nothing.
+ * (The paper has no counterpart; this is a deployment entry point.)
+ *
+ * For callers that must not call cudaMalloc while they run: cudaMalloc can
+ * synchronize the whole device and takes memory outside the caller's own
+ * pool, so a runtime that plans all device memory up front, or a
+ * latency-critical loop that treats a device-wide synchronization as a fault,
+ * cannot create a handle (which allocates work buffers) mid-run.  This entry
+ * point runs the same kernels as the X-stream part of hs_probit_sweep:
+ *   z_i = y*_i TN+(y*_i x_i beta) with the counters of sweep number `sweep`
+ *   (purpose z, `chain`, `problem`, key `seed`), and X^T z.
+ * All arguments are device pointers on the current device:
+ *   X       N rows of type x_dtype with row stride ld elements; ld * element
+ *           size must be a multiple of 16 bytes; columns p..ld-1 must be zero.
+ *   y       N bytes in {0, 1} (not checked here).
+ *   beta_c  ld values, double for HS_X_F64 and float otherwise, equal to
+ *           beta_j * x_scales[j] (FP8) or beta_j, zero for j >= p.
+ *   x_scales p floats for HS_X_FP8E4M3 (multiplied into X^T z), else NULL.
+ *   xtz     output, p doubles.   z  output, N doubles, or NULL.
+ *   stream  cudaStream_t or NULL; the call waits for its own work on it.
+ * The per-block partial sums live in one fixed device array of 4 MiB
+ * (plus a 256-byte header) that every GPU loading the library holds until
+ * the process exits: sizes whose partials (one row of ld values per SM)
+ * exceed it are rejected with HS_EINVAL, as are p > 8192 and ld > 16384.
+ * The first call on a device looks up that array's device address (no
+ * allocation); make that first call before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialized by the caller.  The error word in the
+ * array is cleared by each call.  Returns HS_OK, HS_EINVAL, HS_ENONFINITE,
+ * HS_ETIMEOUT or HS_ECUDA. */
+int hs_probit_xstream_noalloc(int x_dtype, const void* X, int64_t ld, const uint8_t* y, int64_t N,
+                              int64_t p, const void* beta_c, const float* x_scales, uint64_t seed,
+                              uint32_t chain, uint32_t problem, int64_t sweep, double* xtz, double* z,
+                              void* stream);
+
 /* Release the handle and everything it owns.  NULL is allowed. */
 void hs_probit_free(hs_probit* h);
 

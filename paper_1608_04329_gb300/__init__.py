@@ -84,6 +84,10 @@ _PROTOS = {
     "hs_probit_launches_per_sweep": (ctypes.c_int64, [ctypes.c_void_p]),
     "hs_probit_debug_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "hs_probit_free": (None, [ctypes.c_void_p]),
+    "hs_probit_xstream_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                                 ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 

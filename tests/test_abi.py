@@ -80,3 +80,11 @@ def test_init_rejects_fp64_rows_beyond_the_kernel(lib):
     assert not lib.hs_probit_init_ex(ctypes.byref(cfg), X.ctypes.data, y.ctypes.data, 4, 4097, 0)
     assert lib.hs_probit_last_error() == -1
 
+
+def test_noalloc_rejects_bad_arguments_on_host(lib):
+    # NULL buffers and a row stride that is not a multiple of 16 bytes are
+    # rejected before any CUDA call.
+    assert lib.hs_probit_xstream_noalloc(1, None, 8, None, 10, 8, None, None, 0, 0, 0, 1, None, None, None) == -1
+    assert lib.hs_probit_xstream_noalloc(1, ctypes.c_void_p(16), 5, ctypes.c_void_p(16), 10, 5,
+                                         ctypes.c_void_p(16), None, 0, 0, 0, 1, ctypes.c_void_p(16), None,
+                                         None) == -1
