@@ -427,6 +427,24 @@ __device__ __forceinline__ void tile_load(df2 (*T)[NB + 1], const df2* M, int P,
       T[r][c] = v;
   }
 }
+// Three tile loads in one pass, so their global reads are in flight together.
+struct TileSrc {
+  const df2* M;
+  int ti, tj;
+  bool transposed;
+  df2 (*dst)[NB + 1];
+};
+__device__ __forceinline__ void tile_load3(const TileSrc& a, const TileSrc& b, const TileSrc& c, int P) {
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e >> 5, q = e & 31;
+    const df2 va = a.M[(size_t)(a.ti * NB + r) * P + a.tj * NB + q];
+    const df2 vb = b.M[(size_t)(b.ti * NB + r) * P + b.tj * NB + q];
+    const df2 vc = c.M[(size_t)(c.ti * NB + r) * P + c.tj * NB + q];
+    if (a.transposed) a.dst[q][r] = va; else a.dst[r][q] = va;
+    if (b.transposed) b.dst[q][r] = vb; else b.dst[r][q] = vb;
+    if (c.transposed) c.dst[q][r] = vc; else c.dst[r][q] = vc;
+  }
+}
 __device__ __forceinline__ void tile_load_gram(df2 (*T)[NB + 1], const DFCtx& cx, int ti, int tj) {
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e >> 5, c = e & 31;
@@ -470,6 +488,21 @@ __device__ __forceinline__ void tile_mma(df2 (*C)[NB + 1], const df2 (*As)[NB + 
   __syncthreads();
 }
 
+// Lower-triangle elements (r, q), r >= q, listed column by column (q = 0:
+// rows 0..31, q = 1: rows 1..31, ...).  The trailing part of column step c
+// (q > c) is a suffix of the list, (31 - c)(32 - c)/2 entries long, so every
+// thread takes entries tid and tid + 256 of that suffix.
+__device__ __forceinline__ void tri_entry(int idx, int& r, int& q) {
+  // idx in [0, 528): column q starts at q*32 - q(q-1)/2
+  int qq = (int)((65.0f - sqrtf(4225.0f - 8.0f * (float)idx)) * 0.5f);
+  if (qq < 0) qq = 0;
+  if (qq > 31) qq = 31;
+  while (qq > 0 && qq * 32 - qq * (qq - 1) / 2 > idx) --qq;
+  while (qq < 31 && (qq + 1) * 32 - (qq + 1) * qq / 2 <= idx) ++qq;
+  q = qq;
+  r = q + (idx - (q * 32 - q * (q - 1) / 2));
+}
+
 // Right-looking Cholesky of the lower triangle of D in place (upper set to 0),
 // one block barrier per column: the trailing update uses the unscaled column,
 // a_rq -= a_rc a_qc / a_cc, every thread forming 1 / a_cc itself; the columns
@@ -477,7 +510,11 @@ __device__ __forceinline__ void tile_mma(df2 (*C)[NB + 1], const df2 (*As)[NB + 
 // diagonal of the factor and its reciprocal.
 __device__ void potrf_df(df2 (*D)[NB + 1], df2* s_piv, df2* s_sq, df2* s_rs, int* err, bool report) {
   const int tid = threadIdx.x;
-  const int qo = tid & 31, ro = tid >> 5;  // 8 row phases
+  // this thread's two list entries, as offsets from the end of the list
+  int r0, q0, r1, q1;
+  tri_entry(527 - tid, r0, q0);
+  const bool has1 = tid + 256 < 528;
+  tri_entry(has1 ? 527 - tid - 256 : 0, r1, q1);
   for (int c = 0; c < NB; ++c) {
     __syncthreads();
     df2 d = D[c][c];
@@ -488,12 +525,21 @@ __device__ void potrf_df(df2 (*D)[NB + 1], df2* s_piv, df2* s_sq, df2* s_rs, int
       s_piv[c] = d;
     }
     const df2 dinv = df_recip_fast(d);
-    const int q = c + 1 + qo;
-    if (q < NB) {
-      const df2 aq = df_mul(D[q][c], dinv);
-      for (int r = c + 1 + ro; r < NB; r += 8)
-        if (q <= r) D[r][q] = df_sub(D[r][q], df_mul(D[r][c], aq));
+    const int ntr = (31 - c) * (32 - c) / 2;  // trailing entries
+    const bool e0 = tid < ntr, e1 = has1 && tid + 256 < ntr;
+    df2 a0, b0, x0, a1, b1, x1;
+    if (e0) {
+      a0 = D[r0][c];
+      b0 = D[q0][c];
+      x0 = D[r0][q0];
     }
+    if (e1) {
+      a1 = D[r1][c];
+      b1 = D[q1][c];
+      x1 = D[r1][q1];
+    }
+    if (e0) D[r0][q0] = df_sub(x0, df_mul(a0, df_mul(b0, dinv)));
+    if (e1) D[r1][q1] = df_sub(x1, df_mul(a1, df_mul(b1, dinv)));
   }
   __syncthreads();
   if (tid < NB) df_sqrt_rsqrt_fast(s_piv[tid], s_sq[tid], s_rs[tid]);
@@ -510,29 +556,44 @@ __device__ void potrf_df(df2 (*D)[NB + 1], df2* s_piv, df2* s_sq, df2* s_rs, int
   __syncthreads();
 }
 
-// Li = L^{-1} (lower) and LiT = its transpose.  Column j is formed by the
-// eight lanes (j, 0..7) of one warp: row r needs sum_{j<=m<r} L[r][m] Li[m][j].
-// s_rdiag holds 1 / L[r][r].
-__device__ void trtri_df(const df2 (*L)[NB + 1], df2 (*Li)[NB + 1], df2 (*LiT)[NB + 1], const df2* s_rdiag) {
+// Li = L^{-1} (lower) and LiT = its transpose by recursive doubling: with the
+// inverses of the two diagonal b x b blocks of every 2b x 2b diagonal block
+// known, its off-diagonal block is -Li22 (L21 Li11).  Five levels (b = 1..16),
+// each two small products with at most 256 outputs.  s_rdiag = 1 / L[r][r].
+// sT is a scratch tile.
+__device__ void trtri_df(const df2 (*L)[NB + 1], df2 (*Li)[NB + 1], df2 (*LiT)[NB + 1], df2 (*sT)[NB + 1],
+                         const df2* s_rdiag) {
   const int tid = threadIdx.x;
-  const int j = tid >> 3, q = tid & 7;
-  for (int r = 0; r < NB; ++r) {
-    float h = 0.0f, l = 0.0f;
-    for (int m = j + q; m < r; m += 8) df_fma(h, l, L[r][m], Li[m][j]);
-    df2 sm = df_renorm(h, l);
-    sm = df_add(sm, df_shfl_xor(sm, 4));
-    sm = df_add(sm, df_shfl_xor(sm, 2));
-    sm = df_add(sm, df_shfl_xor(sm, 1));
-    if (q == 0) {
-      df2 v = df2{0.0f, 0.0f};
-      if (r == j)
-        v = s_rdiag[r];
-      else if (r > j)
-        v = df_mul(df_neg(sm), s_rdiag[r]);
-      Li[r][j] = v;
-      LiT[j][r] = v;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int r = e >> 5, c = e & 31;
+    Li[r][c] = (r == c) ? s_rdiag[r] : df2{0.0f, 0.0f};
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 1; b < NB; b <<= 1) {
+    const int per = b * b;                 // outputs per 2b-block
+    const int blk = tid / per, e = tid - blk * per;
+    const bool act = blk < NB / (2 * b);
+    const int ro = e / b, co = e - (e / b) * b;
+    const int o = blk * 2 * b;
+    if (act) {
+      // T = L21 Li11: T[ro][co] = sum_{m=co}^{b-1} L[o+b+ro][o+m] Li[o+m][o+co]
+      float h = 0.0f, l = 0.0f;
+      for (int m = co; m < b; ++m) df_fma(h, l, L[o + b + ro][o + m], Li[o + m][o + co]);
+      sT[o + ro][co] = df_renorm(h, l);
     }
-    __syncwarp();
+    __syncthreads();
+    if (act) {
+      // Li21 = -Li22 T: Li[o+b+ro][o+co] = -sum_{m=0}^{ro} Li[o+b+ro][o+b+m] T[m][co]
+      float h = 0.0f, l = 0.0f;
+      for (int m = 0; m <= ro; ++m) df_fma(h, l, Li[o + b + ro][o + b + m], sT[o + m][co]);
+      Li[o + b + ro][o + co] = df_neg(df_renorm(h, l));
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int r = e >> 5, c = e & 31;
+    LiT[c][r] = Li[r][c];
   }
   __syncthreads();
 }
@@ -567,13 +628,17 @@ __global__ void __launch_bounds__(256) step_df_kernel(CholArgs a, int k) {
 
   // ---- own tile and its pending update from block column k-1 ----
   if (isA) {
-    if (from_gram)
+    if (from_gram) {
       tile_load_gram(sW, cx, i, j);
-    else
-      tile_load(sW, A, a.P, i, j, false);
+      if (k >= 1) {
+        tile_load(sX1, A, a.P, i, k - 1, false);
+        tile_load(sX2, A, a.P, j, k - 1, true);
+      }
+    } else {
+      tile_load3(TileSrc{A, i, j, false, sW}, TileSrc{A, i, k - 1, false, sX1}, TileSrc{A, j, k - 1, true, sX2},
+                 a.P);
+    }
     if (k >= 1) {
-      tile_load(sX1, A, a.P, i, k - 1, false);
-      tile_load(sX2, A, a.P, j, k - 1, true);
       __syncthreads();
       tile_mma<true>(sW, sX1, sX2);
     }
@@ -583,12 +648,14 @@ __global__ void __launch_bounds__(256) step_df_kernel(CholArgs a, int k) {
       return;
     }
   } else {
-    if (j == k - 1)
+    if (j == k - 1) {
       tile_zero(sW);
-    else
-      tile_load(sW, Linv, a.P, i, j, false);
-    tile_load(sX1, A, a.P, i, k - 1, false);
-    tile_load(sX2, Linv, a.P, k - 1, j, false);
+      tile_load(sX1, A, a.P, i, k - 1, false);
+      tile_load(sX2, Linv, a.P, k - 1, j, false);
+    } else {
+      tile_load3(TileSrc{Linv, i, j, false, sW}, TileSrc{A, i, k - 1, false, sX1},
+                 TileSrc{Linv, k - 1, j, false, sX2}, a.P);
+    }
     __syncthreads();
     tile_mma<true>(sW, sX1, sX2);
     if (i > k) {
@@ -601,21 +668,21 @@ __global__ void __launch_bounds__(256) step_df_kernel(CholArgs a, int k) {
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) sD[e >> 5][e & 31] = sW[e >> 5][e & 31];
     __syncthreads();
   } else {
-    if (from_gram)
+    if (from_gram) {
       tile_load_gram(sD, cx, k, k);
-    else
-      tile_load(sD, A, a.P, k, k, false);
-    if (k >= 1) {
-      tile_load(sX1, A, a.P, k, k - 1, false);
-      tile_load(sX2, A, a.P, k, k - 1, true);
-      __syncthreads();
-      tile_mma<true>(sD, sX1, sX2);
+      if (k >= 1) {
+        tile_load(sX1, A, a.P, k, k - 1, false);
+        tile_load(sX2, A, a.P, k, k - 1, true);
+      }
     } else {
-      __syncthreads();
+      tile_load3(TileSrc{A, k, k, false, sD}, TileSrc{A, k, k - 1, false, sX1}, TileSrc{A, k, k - 1, true, sX2},
+                 a.P);
     }
+    __syncthreads();
+    if (k >= 1) tile_mma<true>(sD, sX1, sX2);
   }
   potrf_df(sD, s_piv, s_sq, s_rs, a.err, isA && i == k);
-  trtri_df(sD, sLi, sX1, s_rs);  // sX1 <- (L_kk^{-1})^T
+  trtri_df(sD, sLi, sX1, sX2, s_rs);  // sX1 <- (L_kk^{-1})^T, sX2 scratch
   if (isA && i == k) {
     tile_store(Linv, a.P, k, k, sLi, false);
     tile_store(LinvT, a.P, k, k, sLi, true);
