@@ -155,8 +155,9 @@ int hs_probit_gram(hs_probit* h, double* G_out);
  * (cudaStream_t as void*).  Any out pointer may be NULL. */
 int hs_probit_info(const hs_probit* h, int64_t* N, int64_t* p, void** stream);
 
-/* Profiling.  While on, sweeps launch eagerly (no graph) and CUDA events on
- * the launching stream bracket each kernel group; hs_probit_kernel_time
+/* Profiling.  While on, CUDA events on the launching stream bracket each
+ * kernel group (in a captured graph, as event-record nodes re-pointed at fresh
+ * events before each launch); hs_probit_kernel_time
  * returns the summed milliseconds and the number of launches timed since
  * profiling was switched on.  which: 0 X-stream kernel, 1 X^T z reduce,
  * 2 lambda/tau kernel, 3 Cholesky+inverse branch (all its launches),

@@ -64,13 +64,14 @@ __device__ __forceinline__ df2 df_sqrt(df2 a) {
   return df_renorm(s, r / (2.0f * s));
 }
 
-// Same with a hardware-approximate seed (about 2^-22) and one correction:
-// about 2^-44 relative, without the slow path of a correctly rounded FP32
-// division.  Used on the latency-critical pivots of the factorization.
+// Same from a hardware-approximate seed q (about 2^-22): the residual
+// 1 - b q is formed by FMAs and applied once, about 2^-44 relative, without
+// the slow path of a correctly rounded FP32 division.  Used on the pivots.
 __device__ __forceinline__ df2 df_recip_fast(df2 b) {
   const float q = __fdividef(1.0f, b.hi);
-  const df2 r = df_sub(df2{1.0f, 0.0f}, df_mul(b, df2{q, 0.0f}));
-  return df_renorm(q, r.hi * q);
+  float e = fmaf(-b.hi, q, 1.0f);
+  e = fmaf(-b.lo, q, e);
+  return df_renorm(q, q * e);
 }
 // sqrt(a) and 1/sqrt(a), a > 0, from the approximate reciprocal square root.
 __device__ __forceinline__ void df_sqrt_rsqrt_fast(df2 a, df2& sq, df2& rs) {

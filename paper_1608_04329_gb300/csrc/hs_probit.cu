@@ -92,7 +92,13 @@ struct hs_probit {
   int64_t launches = 0;
 
   bool graph_ready = false;
+  cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  // Event-record nodes of the captured graph (start/end of each kernel group),
+  // re-pointed at fresh events before each launch while profiling.
+  bool capturing = false;
+  cudaEvent_t placeholder[kProfGroups][2] = {};
+  cudaGraphNode_t prof_node[kProfGroups][2] = {};
 
   int profiling = 0;
   std::vector<cudaEvent_t> ev_pool;
@@ -230,20 +236,27 @@ hs::TailArgs tail_args(hs_probit* h) {
   return a;
 }
 
-// Record a profiling event pair around a group on a stream.
+// Record a profiling event pair around a group on a stream.  While a graph is
+// being captured the group's placeholder events are recorded instead, which
+// become event-record nodes of the graph.
 struct ProfSpan {
   hs_probit* h;
   int group;
   cudaStream_t s;
   cudaEvent_t e0 = nullptr;
   ProfSpan(hs_probit* hh, int g, cudaStream_t ss) : h(hh), group(g), s(ss) {
-    if (h->profiling) {
+    if (h->capturing) {
+      // External records become event-record nodes of the captured graph.
+      cudaEventRecordWithFlags(h->placeholder[group][0], s, cudaEventRecordExternal);
+    } else if (h->profiling) {
       e0 = h->take_event();
       cudaEventRecord(e0, s);
     }
   }
   ~ProfSpan() {
-    if (h->profiling && e0) {
+    if (h->capturing) {
+      cudaEventRecordWithFlags(h->placeholder[group][1], s, cudaEventRecordExternal);
+    } else if (h->profiling && e0) {
       cudaEvent_t e1 = h->take_event();
       cudaEventRecord(e1, s);
       h->pending.push_back({group, {e0, e1}});
@@ -291,22 +304,57 @@ cudaError_t enqueue_sweep(hs_probit* h) {
 
 cudaError_t build_graph(hs_probit* h) {
   cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(h->s0, cudaStreamCaptureModeThreadLocal);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < kProfGroups && e == cudaSuccess; ++i)
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+      if (!h->placeholder[i][j]) e = cudaEventCreate(&h->placeholder[i][j]);
   if (e != cudaSuccess) return e;
-  const int saved = h->profiling;
-  h->profiling = 0;
+  e = cudaStreamBeginCapture(h->s0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  h->capturing = true;
   cudaError_t e2 = enqueue_sweep(h);
-  h->profiling = saved;
+  h->capturing = false;
   e = cudaStreamEndCapture(h->s0, &g);
   if (e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     return e2;
   }
   if (e != cudaSuccess) return e;
-  e = cudaGraphInstantiate(&h->gexec, g, 0);
-  cudaGraphDestroy(g);
-  if (e == cudaSuccess) h->graph_ready = true;
-  return e;
+  // locate the event-record nodes of the profiling spans
+  size_t n = 0;
+  e = cudaGraphGetNodes(g, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (e == cudaSuccess && n) e = cudaGraphGetNodes(g, nodes.data(), &n);
+  for (size_t q = 0; q < n && e == cudaSuccess; ++q) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nodes[q], &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t ev = nullptr;
+    if (cudaGraphEventRecordNodeGetEvent(nodes[q], &ev) != cudaSuccess) continue;
+    for (int i = 0; i < kProfGroups; ++i)
+      for (int j = 0; j < 2; ++j)
+        if (ev == h->placeholder[i][j]) h->prof_node[i][j] = nodes[q];
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return e;
+  }
+  h->graph = g;
+  h->graph_ready = true;
+  return cudaSuccess;
+}
+
+// Before a graph launch while profiling: point the span nodes at fresh events.
+cudaError_t arm_graph_events(hs_probit* h) {
+  for (int i = 0; i < kProfGroups; ++i) {
+    if (!h->prof_node[i][0] || !h->prof_node[i][1]) continue;
+    cudaEvent_t e0 = h->take_event(), e1 = h->take_event();
+    cudaError_t e = cudaGraphExecEventRecordNodeSetEvent(h->gexec, h->prof_node[i][0], e0);
+    if (e == cudaSuccess) e = cudaGraphExecEventRecordNodeSetEvent(h->gexec, h->prof_node[i][1], e1);
+    if (e != cudaSuccess) return e;
+    h->pending.push_back({i, {e0, e1}});
+  }
+  return cudaSuccess;
 }
 
 void collect_profile(hs_probit* h) {
@@ -328,6 +376,10 @@ void destroy(hs_probit* h) {
   if (h->s0) cudaStreamSynchronize(h->s0);
   if (h->s1) cudaStreamSynchronize(h->s1);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  for (int i = 0; i < kProfGroups; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (h->placeholder[i][j]) cudaEventDestroy(h->placeholder[i][j]);
   for (auto& pe : h->pending) {
     h->ev_pool.push_back(pe.second.first);
     h->ev_pool.push_back(pe.second.second);
@@ -572,16 +624,18 @@ int hs_probit_sweep(hs_probit* h, int64_t n_iter) {
   DeviceGuard dg(h->device);
   if (!dg.ok) return HS_ECUDA;
   cudaError_t e = cudaSuccess;
-  const bool graph = h->cfg.use_graph && !h->profiling;
+  const bool graph = h->cfg.use_graph != 0;
   if (graph && !h->graph_ready) {
     e = build_graph(h);
     if (e != cudaSuccess) return cuda_status(e);
   }
   for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
-    if (graph)
-      e = cudaGraphLaunch(h->gexec, h->s0);
-    else
+    if (graph) {
+      if (h->profiling) e = arm_graph_events(h);
+      if (e == cudaSuccess) e = cudaGraphLaunch(h->gexec, h->s0);
+    } else {
       e = enqueue_sweep(h);
+    }
   }
   if (e != cudaSuccess) {
     cudaStreamSynchronize(h->s0);

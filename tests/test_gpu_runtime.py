@@ -154,3 +154,19 @@ def test_long_run_moments_match_oracle_within_mc_error(pkg):
     mo, so = bm(ob)
     zs = (mg - mo) / np.sqrt(sg ** 2 + so ** 2 + 1e-12)
     assert np.all(np.abs(zs) < 5.0), zs
+
+
+def test_profiling_in_graph_and_eager_modes(pkg, data):
+    """Per-kernel CUDA events work with and without graph replay and do not
+    change the trajectory."""
+    out = {}
+    for graph in (False, True):
+        s = pkg.HSProbit(data["X"], data["y"], seed=6, use_graph=graph)
+        s.set_profiling(True)
+        s.sweep(4)
+        for g in ("xstream", "reduce", "shrink", "cholesky", "tail"):
+            ms, n = s.kernel_time(g)
+            assert n == 4 and ms > 0.0, (graph, g, ms, n)
+        out[graph] = _state(s)
+        s.close()
+    assert np.array_equal(out[False], out[True])
