@@ -60,6 +60,14 @@ extern "C" {
 #define HS_CHOL_F64   0  /* native FP64 (GB300 runs FP64 at ~1/64 of the FP32 rate) */
 #define HS_CHOL_DF32  1  /* FP32 pairs (~48-bit significand) on the FP32 pipe; default */
 
+/* ---- launch schedule of the HS_CHOL_DF32 factorization -------------------
+ * Both schedules compute the same tiles with the same operations in the same
+ * order, so their results are bit-identical. */
+#define HS_SCHED_AUTO     0  /* single launch where the device has cooperative launch, else columns */
+#define HS_SCHED_COLUMNS  1  /* one launch per 32-wide block column (P / 32 launches) */
+#define HS_SCHED_SINGLE   2  /* one cooperative launch, tiles scheduled by data readiness;
+                                init fails with HS_EUNSUPPORTED where the device lacks it */
+
 typedef struct hs_probit hs_probit;  /* opaque handle */
 
 typedef struct hs_probit_config {
@@ -75,7 +83,8 @@ typedef struct hs_probit_config {
   uint32_t problem;    /* problem id in the counter */
   void* stream;        /* cudaStream_t for the sweep; NULL: library-owned stream */
   const float* x_scales; /* HS_X_FP8E4M3 only: p column scales (host or device) */
-  int32_t reserved[8];
+  int32_t chol_sched;  /* HS_SCHED_*; ignored for HS_CHOL_F64 */
+  int32_t reserved[7];
 } hs_probit_config;
 
 /* Values of one sampler state (Eq. 12 variables).  Arrays are host memory of
@@ -90,7 +99,7 @@ typedef struct hs_probit_state_view {
 } hs_probit_state_view;
 
 /* Fill *cfg with defaults: F32 host X, thin 1, ring 1024, no debug, no graph,
- * HS_CHOL_DF32, device 0, chain 0, problem 0, library stream. */
+ * HS_CHOL_DF32 with HS_SCHED_AUTO, device 0, chain 0, problem 0, library stream. */
 void hs_probit_config_default(hs_probit_config* cfg);
 
 /* Create a sampler for host X (float32, N x p row-major) and host y (N bytes in

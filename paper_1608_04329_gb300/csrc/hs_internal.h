@@ -34,7 +34,9 @@ struct XStreamArgs {
   const int64_t* k_dev;  // sweeps done; this sweep is *k_dev + 1
   RngKey rng;
   int* err;
+  unsigned int* sm_mark;  // or nullptr: each block writes the sweep number at [its SM id] (< kSmMarks)
 };
+constexpr int kSmMarks = 1024;
 
 // Per-process kernel attributes (shared-memory carveout); call before launching.
 cudaError_t xstream_prepare();
@@ -89,10 +91,19 @@ struct CholArgs {
   void* LinvT;            // P x P; upper part becomes L~^{-T}
   int* err;
   int arith;              // HS_CHOL_*
+  unsigned long long* sync;  // HS_CHOL_DF32 single-launch schedule: readiness words (chol_sync_words)
+  int persistent_grid;       // > 0: that schedule with this many blocks; 0: one launch per block column
+  const unsigned int* sm_mark;  // SMs the X-stream of this sweep occupies (XStreamArgs::sm_mark), or nullptr
+  const int64_t* k_dev;         // sweeps done; this sweep is *k_dev + 1
 };
-// Enqueues the whole factorization (several launches); returns the count.
+// Enqueues the whole factorization; *launches receives the kernel count.
 cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches);
-int chol_launch_count(int P, int arith);
+int chol_launch_count(int P, int arith, int persistent_grid);
+// Readiness words the single-launch FP32-pair schedule needs (zeroed once).
+size_t chol_sync_words(int P);
+// Blocks for the single-launch schedule on the current device (all resident
+// at once, one per SM at most), or 0 where cooperative launch is unavailable.
+int chol_persistent_grid(int device);
 
 // ---- beta tail, nu/xi, commit ----------------------------------------------
 struct TailArgs {

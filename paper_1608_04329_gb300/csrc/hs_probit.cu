@@ -75,6 +75,9 @@ struct hs_probit {
   double *xtz = nullptr, *v = nullptr;
   double* shrink_part = nullptr;
   unsigned int* shrink_ticket = nullptr;
+  unsigned long long* chol_sync = nullptr;  // readiness words of the single-launch factorization
+  unsigned int* sm_mark = nullptr;          // SM occupancy marks of the X-stream (single launch only)
+  int chol_grid = 0;                        // its blocks; 0: one launch per block column
   void* partials = nullptr;
   int grid = 1;
   double* z = nullptr;
@@ -163,6 +166,7 @@ hs::XStreamArgs xstream_args(hs_probit* h) {
   a.k_dev = h->k_dev;
   a.rng = h->rng;
   a.err = h->err;
+  a.sm_mark = h->sm_mark;
   return a;
 }
 
@@ -199,6 +203,10 @@ hs::CholArgs chol_args(hs_probit* h) {
   a.LinvT = h->LinvT;
   a.err = h->err;
   a.arith = h->cfg.chol_arith;
+  a.sync = h->chol_sync;
+  a.persistent_grid = h->chol_grid;
+  a.sm_mark = h->sm_mark;
+  a.k_dev = h->k_dev;
   return a;
 }
 
@@ -420,6 +428,7 @@ void hs_probit_config_default(hs_probit_config* cfg) {
   cfg->debug = 0;
   cfg->use_graph = 0;
   cfg->chol_arith = HS_CHOL_DF32;
+  cfg->chol_sched = HS_SCHED_AUTO;
   cfg->device = 0;
 }
 
@@ -451,7 +460,8 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   // ---- argument checks (host only, before any CUDA call) ----
   if (!X || !y || N < 2 || p < 1 || p > kMaxP || cfg.thin < 1 || cfg.ring_size < 1 ||
       cfg.chain >= (1u << 24) || (cfg.x_dtype < HS_X_F64 || cfg.x_dtype > HS_X_FP8E4M3) ||
-      (cfg.chol_arith != HS_CHOL_F64 && cfg.chol_arith != HS_CHOL_DF32) || N > (int64_t)0xFFFFFFFF) {
+      (cfg.chol_arith != HS_CHOL_F64 && cfg.chol_arith != HS_CHOL_DF32) || N > (int64_t)0xFFFFFFFF ||
+      cfg.chol_sched < HS_SCHED_AUTO || cfg.chol_sched > HS_SCHED_SINGLE) {
     fail(HS_EINVAL);
     return nullptr;
   }
@@ -514,6 +524,14 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   check(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, h->device));
   check(hs::xstream_prepare());
   check(hs::linalg_prepare());
+  if (e == cudaSuccess && cfg.chol_arith == HS_CHOL_DF32 && cfg.chol_sched != HS_SCHED_COLUMNS) {
+    h->chol_grid = hs::chol_persistent_grid(h->device);
+    if (h->chol_grid == 0 && cfg.chol_sched == HS_SCHED_SINGLE) {
+      destroy(h);
+      fail(HS_EUNSUPPORTED);
+      return nullptr;
+    }
+  }
   if (cfg.stream) {
     h->s0 = static_cast<cudaStream_t>(cfg.stream);
   } else {
@@ -548,6 +566,10 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   check(h->alloc(&h->v, (size_t)h->P * sizeof(double)));
   check(h->alloc(&h->shrink_part, (size_t)((p + 127) / 128) * sizeof(double)));
   check(h->alloc(&h->shrink_ticket, sizeof(unsigned int)));
+  if (h->chol_grid > 0) {
+    check(h->alloc(&h->chol_sync, hs::chol_sync_words(h->P) * sizeof(unsigned long long)));
+    check(h->alloc(&h->sm_mark, hs::kSmMarks * sizeof(unsigned int)));
+  }
   check(h->alloc(&h->partials, (size_t)h->grid * h->ld * hs::partial_elem_bytes(h->x_dtype)));
   if (cfg.debug) check(h->alloc(&h->z, (size_t)N * sizeof(double)));
   check(h->alloc(&h->ring_beta, (size_t)h->ring_size * pd));
@@ -574,6 +596,10 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   check(cudaMemsetAsync(h->err, 0, sizeof(int), h->s0));
   check(cudaMemsetAsync(h->hook_err, 0, sizeof(int), h->s0));
   check(cudaMemsetAsync(h->shrink_ticket, 0, sizeof(unsigned int), h->s0));
+  if (h->chol_sync) {
+    check(cudaMemsetAsync(h->chol_sync, 0, hs::chol_sync_words(h->P) * sizeof(unsigned long long), h->s0));
+    check(cudaMemsetAsync(h->sm_mark, 0, hs::kSmMarks * sizeof(unsigned int), h->s0));
+  }
   if (cfg.x_is_device) check(hs::check_y_launch(h->y, N, h->err, h->s0));
   // ---- cold start (Sect. 6.1): beta = 0, lambda = nu = tau = xi = 1, k = 0 ----
   {
@@ -607,7 +633,7 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
     fail(st);
     return nullptr;
   }
-  h->launches = 1 + hs::chol_launch_count(h->P, h->cfg.chol_arith) + 2 + hs::kTailLaunches;
+  h->launches = 1 + hs::chol_launch_count(h->P, h->cfg.chol_arith, h->chol_grid) + 2 + hs::kTailLaunches;
   return h;
 }
 

@@ -493,119 +493,79 @@ __device__ __forceinline__ void tile_mma(df2 (*C)[NB + 1], const df2 (*As)[NB + 
   __syncthreads();
 }
 
-// Lower-triangle elements (r, q), r >= q, listed column by column (q = 0:
-// rows 0..31, q = 1: rows 1..31, ...).  The trailing part of column step c
-// (q > c) is a suffix of the list, (31 - c)(32 - c)/2 entries long, so every
-// thread takes entries tid and tid + 256 of that suffix.
-__device__ __forceinline__ void tri_entry(int idx, int& r, int& q) {
-  // idx in [0, 528): column q starts at q*32 - q(q-1)/2
-  int qq = (int)((65.0f - sqrtf(4225.0f - 8.0f * (float)idx)) * 0.5f);
-  if (qq < 0) qq = 0;
-  if (qq > 31) qq = 31;
-  while (qq > 0 && qq * 32 - qq * (qq - 1) / 2 > idx) --qq;
-  while (qq < 31 && (qq + 1) * 32 - (qq + 1) * qq / 2 <= idx) ++qq;
-  q = qq;
-  r = q + (idx - (q * 32 - q * (q - 1) / 2));
-}
-
-// Right-looking Cholesky of the lower triangle of D in place (upper set to 0),
-// one block barrier per column: the trailing update uses the unscaled column,
-// a_rq -= a_rc a_qc / a_cc, every thread forming 1 / a_cc itself; the columns
-// are scaled by 1 / sqrt(a_cc) once at the end.  s_sq / s_rs receive the
-// diagonal of the factor and its reciprocal.
-__device__ void potrf_df(df2 (*D)[NB + 1], df2* s_piv, df2* s_sq, df2* s_rs, int* err, bool report) {
+// Inverse Cholesky factor of a 32 x 32 tile: L^{-1} with D = L L^T.
+// Elimination in LDL^T form: at column c the multipliers m_rc = W_rc / W_cc
+// (r > c) update the trailing lower triangle, W_rq -= m_rc W_qc (c < q <= r),
+// and the same row operations act on U (the identity at the start),
+// U_rq -= m_rc U_cq (q <= c < r), so that U = L_u^{-1} for D = L_u diag(W_cc) L_u^T.
+// Then L^{-1} = diag(W_cc)^{-1/2} U.  Each update is formed as (W_rc y) / W_cc,
+// so the product overlaps the reciprocal of the pivot.  W and U are separate
+// tiles and no entry read at step c is written at step c, so one barrier per
+// column suffices.  Warp w owns rows w, w+8, w+16, w+24 and lane q column q;
+// the four rows are computed without branches (all loads first, stores
+// predicated), which keeps the step's work in flight together.
+// Output: Li = L^{-1} (lower, zero above) and LiT its transpose; W is
+// destroyed; s_rs[r] = W_rr^{-1/2} at elimination.  A pivot that is not
+// positive and finite is replaced by 1 and reported.  blockDim.x must be 256.
+__device__ void potri_df(df2 (*W)[NB + 1], df2 (*Li)[NB + 1], df2 (*LiT)[NB + 1], df2* s_piv, df2* s_rs,
+                         int* err, bool report) {
   const int tid = threadIdx.x;
-  // this thread's two list entries, as offsets from the end of the list
-  int r0, q0, r1, q1;
-  tri_entry(527 - tid, r0, q0);
-  const bool has1 = tid + 256 < 528;
-  tri_entry(has1 ? 527 - tid - 256 : 0, r1, q1);
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int r = e >> 5, c = e & 31;
+    Li[r][c] = df2{r == c ? 1.0f : 0.0f, 0.0f};
+  }
+  __syncthreads();
+  const int w = tid >> 5, q = tid & 31;
   for (int c = 0; c < NB; ++c) {
-    __syncthreads();
-    df2 d = D[c][c];
+    df2 d = W[c][c];
     const bool bad = !(d.hi > 0.0f) || !isfinite(d.hi);
     if (bad) d = df2{1.0f, 0.0f};
     if (tid == 0) {
-      if (bad && report && *(volatile int*)err == 0) set_error(err, isfinite(D[c][c].hi) ? kErrNotPD : kErrNonFinite);
+      if (bad && report && *(volatile int*)err == 0) set_error(err, isfinite(W[c][c].hi) ? kErrNotPD : kErrNonFinite);
       s_piv[c] = d;
     }
-    const df2 dinv = df_recip_fast(d);
-    const int ntr = (31 - c) * (32 - c) / 2;  // trailing entries
-    const bool e0 = tid < ntr, e1 = has1 && tid + 256 < ntr;
-    df2 a0, b0, x0, a1, b1, x1;
-    if (e0) {
-      a0 = D[r0][c];
-      b0 = D[q0][c];
-      x0 = D[r0][q0];
-    }
-    if (e1) {
-      a1 = D[r1][c];
-      b1 = D[q1][c];
-      x1 = D[r1][q1];
-    }
-    if (e0) D[r0][q0] = df_sub(x0, df_mul(a0, df_mul(b0, dinv)));
-    if (e1) D[r1][q1] = df_sub(x1, df_mul(a1, df_mul(b1, dinv)));
-  }
-  __syncthreads();
-  if (tid < NB) df_sqrt_rsqrt_fast(s_piv[tid], s_sq[tid], s_rs[tid]);
-  __syncthreads();
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    const int r = e >> 5, c = e & 31;
-    if (c > r)
-      D[r][c] = df2{0.0f, 0.0f};
-    else if (c == r)
-      D[r][c] = s_sq[c];
-    else
-      D[r][c] = df_mul(D[r][c], s_rs[c]);
-  }
-  __syncthreads();
-}
-
-// Li = L^{-1} (lower) and LiT = its transpose by recursive doubling: with the
-// inverses of the two diagonal b x b blocks of every 2b x 2b diagonal block
-// known, its off-diagonal block is -Li22 (L21 Li11).  Five levels (b = 1..16),
-// each two small products with at most 256 outputs.  s_rdiag = 1 / L[r][r].
-// sT is a scratch tile.
-__device__ void trtri_df(const df2 (*L)[NB + 1], df2 (*Li)[NB + 1], df2 (*LiT)[NB + 1], df2 (*sT)[NB + 1],
-                         const df2* s_rdiag) {
-  const int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    const int r = e >> 5, c = e & 31;
-    Li[r][c] = (r == c) ? s_rdiag[r] : df2{0.0f, 0.0f};
-  }
-  __syncthreads();
+    if (w + 24 > c) {  // some of this warp's rows are still below the pivot
+      const df2 dinv = df_recip_fast(d);
+      const bool trailing = q > c;
+      df2 wr[4], y[4], x[4];
 #pragma unroll
-  for (int b = 1; b < NB; b <<= 1) {
-    const int per = b * b;                 // outputs per 2b-block
-    const int blk = tid / per, e = tid - blk * per;
-    const bool act = blk < NB / (2 * b);
-    const int ro = e / b, co = e - (e / b) * b;
-    const int o = blk * 2 * b;
-    if (act) {
-      // T = L21 Li11: T[ro][co] = sum_{m=co}^{b-1} L[o+b+ro][o+m] Li[o+m][o+co]
-      float h = 0.0f, l = 0.0f;
-      for (int m = co; m < b; ++m) df_fma(h, l, L[o + b + ro][o + m], Li[o + m][o + co]);
-      sT[o + ro][co] = df_renorm(h, l);
-    }
-    __syncthreads();
-    if (act) {
-      // Li21 = -Li22 T: Li[o+b+ro][o+co] = -sum_{m=0}^{ro} Li[o+b+ro][o+b+m] T[m][co]
-      float h = 0.0f, l = 0.0f;
-      for (int m = 0; m <= ro; ++m) df_fma(h, l, Li[o + b + ro][o + b + m], sT[o + m][co]);
-      Li[o + b + ro][o + co] = df_neg(df_renorm(h, l));
+      for (int i = 0; i < 4; ++i) {
+        const int r = w + 8 * i;
+        wr[i] = W[r][c];
+        y[i] = trailing ? W[q][c] : Li[c][q];
+        x[i] = trailing ? W[r][q] : Li[r][q];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = w + 8 * i;
+        const df2 v = df_sub(x[i], df_mul(df_mul(wr[i], y[i]), dinv));  // x - (W_rc y) / W_cc
+        if (r > c && q <= r) {
+          if (trailing)
+            W[r][q] = v;
+          else
+            Li[r][q] = v;
+        }
+      }
     }
     __syncthreads();
   }
+  if (tid < NB) {
+    df2 sq;
+    df_sqrt_rsqrt_fast(s_piv[tid], sq, s_rs[tid]);
+  }
+  __syncthreads();
   for (int e = tid; e < NB * NB; e += blockDim.x) {
     const int r = e >> 5, c = e & 31;
-    LiT[c][r] = Li[r][c];
+    const df2 v = c < r ? df_mul(Li[r][c], s_rs[r]) : (c == r ? s_rs[r] : df2{0.0f, 0.0f});
+    Li[r][c] = v;
+    LiT[c][r] = v;
   }
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(256) step_df_kernel(CholArgs a, int k) {
   __shared__ DTile sD, sW, sX1, sX2, sLi;
-  __shared__ df2 s_piv[NB], s_sq[NB], s_rs[NB];
+  __shared__ df2 s_piv[NB], s_rs[NB];
   const int T = a.P / NB;
   // Block order: the blocks that finish block column k (they carry the
   // critical path) come first so they are dispatched in the first wave:
@@ -703,8 +663,7 @@ __global__ void __launch_bounds__(256) step_df_kernel(CholArgs a, int k) {
     __syncthreads();
     if (k >= 1) tile_mma<true>(sD, sX1, sX2);
   }
-  potrf_df(sD, s_piv, s_sq, s_rs, a.err, isA && i == k);
-  trtri_df(sD, sLi, sX1, sX2, s_rs);  // sX1 <- (L_kk^{-1})^T, sX2 scratch
+  potri_df(sD, sLi, sX1, s_piv, s_rs, a.err, isA && i == k);  // sX1 <- (L_kk^{-1})^T
   if (isA && i == k) {
     tile_store(Linv, a.P, k, k, sLi, false);
     tile_store(LinvT, a.P, k, k, sLi, true);
@@ -715,6 +674,380 @@ __global__ void __launch_bounds__(256) step_df_kernel(CholArgs a, int k) {
     tile_mma<false>(sX2, sLi, sW);  // X_kj = L_kk^{-1} B_kj
     tile_store(Linv, a.P, k, j, sX2, false);
     tile_store(LinvT, a.P, j, k, sX2, true);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32-pair factorization in ONE persistent launch (tile dataflow)
+// ---------------------------------------------------------------------------
+// The same tile algebra as step_df_kernel, scheduled by data dependencies
+// instead of one launch per block column.  Block 0 runs the diagonal chain:
+// for each k it applies the last pending update to A_kk, factors it, forms
+// L_kk^{-1}, and computes the next panel tile L_{k+1,k}.  All other blocks
+// take the remaining tile tasks in a fixed topological order (round robin):
+//   C(i,k)   L_ik = A_ik L_kk^{-T}                  i >= k+2
+//   X(k,j)   X_kj = L_kk^{-1} B_kj                   j < k
+//   UA(i,j,k) A_ij -= L_ik L_jk^T   k < j <= i, except the diagonal tile's last update
+//   UB(i,j,k) B_ij -= L_ik X_kj     i > k, j <= k
+// Readiness lives in per-tile words tagged with the sweep number e: a flag
+// holds e once its tile is published; an update counter holds e*64 + n after
+// n updates (values of earlier sweeps are smaller, so nothing is reset).
+// Every wait is bounded (2 s) and a global abort word stops all blocks after
+// a timeout.  Blocks must all be resident: the kernel is launched
+// cooperatively.
+// Word layout of the scheduling buffer (u64, zeroed once when the handle is
+// made): header [0] epoch of the last finished launch, [1] exit ticket,
+// [2] abort, [3] chain claim (epoch), [4] start ticket, [5] chain SM
+// (epoch << 16 | SM id), [6] next worker task; then cntA and cntB (T*T
+// each: updates applied to tile (i, j) of A or B, at i*T + j), flagL and
+// flagX (T*T: L_ik, X_kj published), flagLi (T: L_kk^{-1} published).
+// Flags hold the epoch of the launch that published them; counters hold
+// epoch * kEpochStride + updates, so nothing is reset between launches.
+constexpr int kSyncHeader = 8;
+constexpr unsigned long long kEpochStride = 1024;  // > the largest update count (T <= 256)
+constexpr int kMaxTiles = 8192 / NB;
+
+// worker task counts of step k (host and device)
+__host__ __device__ __forceinline__ int nC(int T, int k) { return T - k - 2 > 0 ? T - k - 2 : 0; }
+__host__ __device__ __forceinline__ int nUA(int T, int k) {
+  const int m = T - k - 1;  // tile rows/cols k+1..T-1
+  return m > 0 ? m * (m + 1) / 2 - 1 : 0;  // without the diagonal tile (k+1, k+1)
+}
+__host__ __device__ __forceinline__ int nUB(int T, int k) { return (T - k - 1) * (k + 1); }
+__host__ __device__ __forceinline__ int nTasks(int T, int k) { return nC(T, k) + k + nUA(T, k) + nUB(T, k); }
+__host__ __device__ inline int total_tasks(int T) {
+  int n = 0;
+  for (int k = 0; k < T; ++k) n += nTasks(T, k);
+  return n;
+}
+struct PSync {
+  unsigned long long *epoch, *ticket, *abort, *claim, *start, *chain_sm, *next;
+  unsigned long long *cntA, *cntB, *flagL, *flagX, *flagLi;
+  __device__ PSync(unsigned long long* w, int T) {
+    epoch = w;
+    ticket = w + 1;
+    abort = w + 2;
+    claim = w + 3;
+    start = w + 4;
+    chain_sm = w + 5;
+    next = w + 6;
+    cntA = w + kSyncHeader;
+    cntB = cntA + T * T;
+    flagL = cntB + T * T;
+    flagX = flagL + T * T;
+    flagLi = flagX + T * T;
+  }
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0 waits until *p[n] >= target[n] for every n; the block then
+// proceeds together.  The words are read together (relaxed) and one
+// acquire fence follows, so a task whose inputs are ready pays one L2 round
+// trip.  Returns false (in every thread) if a wait ran out (2 s; the
+// timeout bit is set and the abort word raised) or another block gave up.
+template <int N>
+__device__ bool block_wait(const unsigned long long* const (&p)[N], const unsigned long long (&target)[N],
+                           const PSync& ps, unsigned long long e, int* err) {
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    unsigned long long v[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) v[n] = ld_relaxed_u64(p[n]);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      if (ok && v[n] < target[n]) {
+        const uint64_t t0 = global_ns();
+        while (ld_relaxed_u64(p[n]) < target[n]) {
+          if (ld_relaxed_u64(ps.abort) >= e) {
+            ok = 0;
+            break;
+          }
+          if (global_ns() - t0 > 2000000000ull) {
+            set_error(err, kErrTimeout);
+            st_release_u64(ps.abort, e);
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  }
+  return __syncthreads_and(ok) != 0;
+}
+__device__ __forceinline__ bool block_wait(const unsigned long long* p, unsigned long long target, const PSync& ps,
+                                           unsigned long long e, int* err) {
+  const unsigned long long* const pp[1] = {p};
+  const unsigned long long tt[1] = {target};
+  return block_wait<1>(pp, tt, ps, e, err);
+}
+
+// All threads' global writes of the block become visible before *p = v.
+__device__ __forceinline__ void block_publish(unsigned long long* p, unsigned long long v) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release_u64(p, v);
+  }
+}
+
+// Tile moves of data other blocks write during this launch go through L2.
+// Up to three tiles per call, all global loads issued before the shared
+// stores; 16-byte accesses (two FP32 pairs); blockDim.x must be 256.
+struct TileRef {
+  const df2* M;
+  int ti, tj;
+  bool transposed;
+  df2 (*dst)[NB + 1];
+};
+template <int NT>
+__device__ __forceinline__ void tiles_load_cg(const TileRef (&t)[NT], int P) {
+  float4 v[NT][2];
+#pragma unroll
+  for (int n = 0; n < NT; ++n)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = threadIdx.x + h * 256, r = e >> 4, c = (e & 15) * 2;
+      v[n][h] = __ldcg(reinterpret_cast<const float4*>(t[n].M + (size_t)(t[n].ti * NB + r) * P + t[n].tj * NB + c));
+    }
+#pragma unroll
+  for (int n = 0; n < NT; ++n)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = threadIdx.x + h * 256, r = e >> 4, c = (e & 15) * 2;
+      const df2 x0{v[n][h].x, v[n][h].y}, x1{v[n][h].z, v[n][h].w};
+      if (t[n].transposed) {
+        t[n].dst[c][r] = x0;
+        t[n].dst[c + 1][r] = x1;
+      } else {
+        t[n].dst[r][c] = x0;
+        t[n].dst[r][c + 1] = x1;
+      }
+    }
+}
+__device__ __forceinline__ void tile_store_cg(df2* M, int P, int ti, int tj, const df2 (*T)[NB + 1], bool transposed) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int e = threadIdx.x + h * 256, r = e >> 4, c = (e & 15) * 2;
+    const df2 x0 = transposed ? T[c][r] : T[r][c];
+    const df2 x1 = transposed ? T[c + 1][r] : T[r][c + 1];
+    __stcg(reinterpret_cast<float4*>(M + (size_t)(ti * NB + r) * P + tj * NB + c), make_float4(x0.hi, x0.lo, x1.hi, x1.lo));
+  }
+}
+
+__global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
+  __shared__ DTile sD, sW, sX1, sX2, sLi;
+  __shared__ df2 s_piv[NB], s_rs[NB];
+  __shared__ int s_step0[kMaxTiles + 1];
+  __shared__ unsigned long long s_e;
+  __shared__ int s_role;  // 0 worker, 1 chain, 2 idle
+  __shared__ int s_task;
+  const int T = a.P / NB;
+  const int P = a.P;
+  const PSync ps(a.sync, T);
+  unsigned int smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  if (threadIdx.x == 0) {
+    const unsigned long long e0 = *ps.epoch + 1;  // (kernel-ordered after the previous launch's update)
+    s_e = e0;
+    // Role election.  The chain goes to a block on an SM the X-stream left
+    // free (no mark of this sweep), else to the last block to start.
+    const unsigned int stamp = (unsigned int)(*a.k_dev + 1);
+    const bool free_sm = a.sm_mark && smid < (unsigned)kSmMarks && __ldcg(a.sm_mark + smid) != stamp;
+    int role = 0;
+    if (free_sm && atomicCAS(ps.claim, e0 - 1, e0) == e0 - 1) role = 1;
+    const unsigned long long st = atomicAdd(ps.start, 1ull);
+    if (st == gridDim.x - 1) {
+      *ps.start = 0;  // every block has taken its ticket
+      if (role == 0 && atomicCAS(ps.claim, e0 - 1, e0) == e0 - 1) role = 1;
+    }
+    if (role == 1) st_release_u64(ps.chain_sm, (e0 << 16) | smid);
+    s_role = role;
+  }
+  __syncthreads();
+  const unsigned long long e = s_e;
+  const unsigned long long base = e * kEpochStride;
+  df2* A = reinterpret_cast<df2*>(a.A);
+  df2* Linv = reinterpret_cast<df2*>(a.Linv);
+  df2* LinvT = reinterpret_cast<df2*>(a.LinvT);
+  const DFCtx cx{a.p, a.P, a.G, a.S, a.lam_new, *a.tau_new};
+  if (s_role == 0 && gridDim.x >= 16) {
+    // Blocks that share the chain's SM stay idle, leaving it the whole SM
+    // (at most 3 of them: 4 blocks fit on an SM).
+    if (block_wait(ps.chain_sm, e << 16, ps, e, a.err)) {
+      if (threadIdx.x == 0 && (unsigned)(ld_acquire_u64(ps.chain_sm) & 0xFFFFu) == smid) s_role = 2;
+    } else if (threadIdx.x == 0) {
+      s_role = 2;
+    }
+    __syncthreads();
+  }
+
+  if (s_role == 1) {
+    // ---------------- the diagonal chain ----------------
+    // Entering step k, sD holds D_k = A_kk after all k updates.
+    tile_load_gram(sD, cx, 0, 0);
+    __syncthreads();
+    for (int k = 0; k < T; ++k) {
+      potri_df(sD, sLi, sX1, s_piv, s_rs, a.err, true);  // sLi <- L_kk^{-1}, sX1 <- its transpose
+      tile_store_cg(Linv, P, k, k, sLi, false);
+      tile_store_cg(LinvT, P, k, k, sLi, true);
+      block_publish(&ps.flagLi[k], e);
+      if (k + 1 == T) break;
+      // A_{k+1,k} and A_{k+1,k+1} after updates 0..k-1 (workers)
+      if (k >= 1) {
+        const unsigned long long* const wp2[2] = {&ps.cntA[(k + 1) * T + k], &ps.cntA[(k + 1) * T + k + 1]};
+        const unsigned long long wt2[2] = {base + (unsigned long long)k, base + (unsigned long long)k};
+        if (!block_wait<2>(wp2, wt2, ps, e, a.err)) break;
+        const TileRef t[2] = {{A, k + 1, k, false, sW}, {A, k + 1, k + 1, false, sD}};
+        tiles_load_cg<2>(t, P);
+      } else {
+        tile_load_gram(sW, cx, 1, 0);
+        tile_load_gram(sD, cx, 1, 1);
+      }
+      __syncthreads();
+      tile_mma<false>(sLi, sW, sX1);  // L_{k+1,k} = A_{k+1,k} L_kk^{-T}
+      tile_store_cg(A, P, k + 1, k, sLi, false);
+      block_publish(&ps.flagL[(k + 1) * T + k], e);
+      for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) sX2[t & 31][t >> 5] = sLi[t >> 5][t & 31];
+      __syncthreads();
+      tile_mma<true>(sD, sLi, sX2);  // D_{k+1} = A_{k+1,k+1} - L_{k+1,k} L_{k+1,k}^T
+    }
+  } else if (s_role == 0) {
+    // ---------------- workers: tasks in list order from a shared counter ----------------
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int k = 0; k <= T; ++k) {
+        s_step0[k] = acc;
+        if (k < T) acc += nTasks(T, k);
+      }
+    }
+    __syncthreads();
+    const int total = s_step0[T];
+    int k = 0;
+    unsigned long long grabbed = 0;
+    if (threadIdx.x == 0) grabbed = atomicAdd(ps.next, 1ull);
+    for (;;) {
+      if (threadIdx.x == 0) s_task = grabbed >= (unsigned long long)total ? total : (int)grabbed;
+      __syncthreads();
+      const int t = s_task;
+      if (t >= total) break;
+      if (threadIdx.x == 0) grabbed = atomicAdd(ps.next, 1ull);  // the following task, early
+      while (t >= s_step0[k + 1]) ++k;  // a worker's tasks come in increasing order
+      int u = t - s_step0[k];
+      const unsigned long long done_k = base + (unsigned long long)k;  // A tile after updates 0..k-1
+      const int c = nC(T, k), ua = nUA(T, k);
+      if (u < c) {
+        // C(i,k): L_ik = A_ik L_kk^{-T}, i = k + 2 + u
+        const int i = k + 2 + u;
+        const unsigned long long* const wp2[2] = {&ps.flagLi[k], &ps.cntA[i * T + k]};
+        const unsigned long long wt2[2] = {e, k >= 1 ? done_k : 0ull};
+        if (!block_wait<2>(wp2, wt2, ps, e, a.err)) break;
+        if (k == 0) {
+          tile_load_gram(sW, cx, i, 0);
+          const TileRef t1[1] = {{LinvT, k, k, false, sX1}};
+          tiles_load_cg<1>(t1, P);
+        } else {
+          const TileRef t2[2] = {{A, i, k, false, sW}, {LinvT, k, k, false, sX1}};  // sX1[q][c] = (L_kk^{-1})[c][q]
+          tiles_load_cg<2>(t2, P);
+        }
+        __syncthreads();
+        tile_mma<false>(sX2, sW, sX1);
+        tile_store_cg(A, P, i, k, sX2, false);
+        block_publish(&ps.flagL[i * T + k], e);
+        continue;
+      }
+      u -= c;
+      if (u < k) {
+        // X(k,j): X_kj = L_kk^{-1} B_kj, j = u; B_kj after its k - j updates
+        const int j = u;
+        const unsigned long long* const wp2[2] = {&ps.flagLi[k], &ps.cntB[k * T + j]};
+        const unsigned long long wt2[2] = {e, base + (unsigned long long)(k - j)};
+        if (!block_wait<2>(wp2, wt2, ps, e, a.err)) break;
+        const TileRef t2[2] = {{Linv, k, k, false, sX1}, {Linv, k, j, false, sW}};
+        tiles_load_cg<2>(t2, P);
+        __syncthreads();
+        tile_mma<false>(sX2, sX1, sW);
+        tile_store_cg(Linv, P, k, j, sX2, false);
+        tile_store_cg(LinvT, P, j, k, sX2, true);
+        block_publish(&ps.flagX[k * T + j], e);
+        continue;
+      }
+      u -= k;
+      if (u < ua) {
+        // UA(i,j,k): A_ij -= L_ik L_jk^T.  The lower triangle of tile rows/cols
+        // k+1..T-1 is listed column by column (column k+1, which feeds the
+        // diagonal chain, first), without its first entry (k+1, k+1).
+        const int m = T - k - 1;
+        int idx = u + 1, q = 0;
+        while (idx >= m - q) {
+          idx -= m - q;
+          ++q;
+        }
+        const int j = k + 1 + q, i = j + idx;
+        const unsigned long long* const wp3[3] = {&ps.flagL[i * T + k], &ps.flagL[j * T + k], &ps.cntA[i * T + j]};
+        const unsigned long long wt3[3] = {e, e, k >= 1 ? done_k : 0ull};
+        if (!block_wait<3>(wp3, wt3, ps, e, a.err)) break;
+        if (k == 0) {
+          tile_load_gram(sW, cx, i, j);
+          const TileRef t2[2] = {{A, i, k, false, sX1}, {A, j, k, true, sX2}};
+          tiles_load_cg<2>(t2, P);
+        } else {
+          const TileRef t3[3] = {{A, i, j, false, sW}, {A, i, k, false, sX1}, {A, j, k, true, sX2}};
+          tiles_load_cg<3>(t3, P);
+        }
+        __syncthreads();
+        tile_mma<true>(sW, sX1, sX2);
+        tile_store_cg(A, P, i, j, sW, false);
+        block_publish(&ps.cntA[i * T + j], done_k + 1);
+        continue;
+      }
+      u -= ua;
+      {
+        // UB(i,j,k): B_ij -= L_ik X_kj (X_kk = L_kk^{-1}; B_ik starts at zero)
+        const int i = k + 1 + u / (k + 1), j = u % (k + 1);
+        const unsigned long long* const wp3[3] = {&ps.flagL[i * T + k], j < k ? &ps.flagX[k * T + j] : &ps.flagLi[k],
+                                                   &ps.cntB[i * T + j]};
+        const unsigned long long wt3[3] = {e, e, k > j ? base + (unsigned long long)(k - j) : 0ull};
+        if (!block_wait<3>(wp3, wt3, ps, e, a.err)) break;
+        if (k == j) {
+          tile_zero(sW);
+          const TileRef t2[2] = {{A, i, k, false, sX1}, {Linv, k, j, false, sX2}};
+          tiles_load_cg<2>(t2, P);
+        } else {
+          const TileRef t3[3] = {{Linv, i, j, false, sW}, {A, i, k, false, sX1}, {Linv, k, j, false, sX2}};
+          tiles_load_cg<3>(t3, P);
+        }
+        __syncthreads();
+        tile_mma<true>(sW, sX1, sX2);
+        tile_store_cg(Linv, P, i, j, sW, false);
+        block_publish(&ps.cntB[i * T + j], base + (unsigned long long)(k - j + 1));
+      }
+    }
+  }
+  // the last block out records the epoch for the next launch
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ps.ticket, 1ull) == (unsigned long long)(gridDim.x - 1)) {
+      *ps.ticket = 0;
+      *ps.next = 0;
+      *ps.epoch = e;
+    }
   }
 }
 
@@ -857,6 +1190,7 @@ cudaError_t linalg_prepare() {
                        (const void*)update_kernel<HS_CHOL_F64>,
 
                        (const void*)step_df_kernel,
+                       (const void*)chol_persistent_kernel,
                        (const void*)tail_w_kernel<double>,
                        (const void*)tail_beta_kernel<double>,
                        (const void*)tail_w_kernel<df2>,
@@ -873,20 +1207,51 @@ cudaError_t linalg_prepare() {
                               kStepPadBytes);
 }
 
+int chol_persistent_grid(int device) {
+  int coop = 0, sms = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_persistent_kernel, 256, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  if (!coop || sms < 2 || per_sm < 1) return 0;
+  return sms;
+}
+
 cudaError_t shrink_launch(const ShrinkArgs& a, cudaStream_t s) {
   shrink_kernel<<<(a.p + kShrinkThreads - 1) / kShrinkThreads, kShrinkThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-int chol_launch_count(int P, int arith) {
+size_t chol_sync_words(int P) {
+  const size_t T = (size_t)(P / NB);
+  return kSyncHeader + 4 * T * T + T;
+}
+
+int chol_launch_count(int P, int arith, int persistent_grid) {
   const int T = P / NB;
-  if (arith == HS_CHOL_DF32) return T;
+  if (arith == HS_CHOL_DF32) return persistent_grid > 0 ? 1 : T;
   return 1 + T + (T - 1);  // build, panels, updates (the last step has none)
 }
 
 cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches) {
   const int T = a.P / NB;
   int n = 0;
+  if (a.arith == HS_CHOL_DF32 && a.persistent_grid > 0) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)a.persistent_grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (launches) *launches = 1;
+    return cudaLaunchKernelEx(&cfg, chol_persistent_kernel, a);
+  }
   if (a.arith == HS_CHOL_DF32) {
     for (int k = 0; k < T; ++k) {
       const int m = T - k;

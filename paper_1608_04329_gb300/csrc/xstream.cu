@@ -175,6 +175,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nvec = a.ld / VE;
 
   if (tid == 0) {
+    if (a.sm_mark) {
+      // tell the factorization, running beside this kernel, which SMs are busy here
+      unsigned int smid;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      if (smid < (unsigned)kSmMarks) a.sm_mark[smid] = (unsigned int)(*a.k_dev + 1);
+    }
     for (int s = 0; s < nstage; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kConsumerWarps);
@@ -388,7 +394,10 @@ int grid_dtype(int ld, int64_t N, int num_sms) {
   const int S = (nvec + kConsumers - 1) / kConsumers;
   const int R = S <= 1 ? rows_s1<XD>() : S <= 2 ? 4 : S <= 4 ? 2 : 1;
   const int64_t ntiles = (N + R - 1) / R;
-  int64_t g = (int64_t)num_sms;  // one persistent CTA per SM
+  // One persistent CTA per SM but one: the SM left free runs the diagonal
+  // chain of the factorization beside this kernel (the same grid whatever the
+  // factorization schedule, so every entry point partitions X alike).
+  int64_t g = num_sms > 1 ? (int64_t)num_sms - 1 : 1;
   if (g > ntiles) g = ntiles;
   if (g < 1) g = 1;
   return (int)g;

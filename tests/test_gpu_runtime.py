@@ -35,6 +35,24 @@ def test_graph_replay_equals_eager(pkg, data):
     b.close()
 
 
+@pytest.mark.parametrize("N,p", [(300, 1), (500, 33), (900, 64), (2000, 257), (3001, 600), (2500, 1100),
+                                 (3000, 2500)])
+@pytest.mark.parametrize("graph", [False, True], ids=["eager", "graph"])
+def test_single_launch_factorization_equals_column_launches(pkg, N, p, graph):
+    """The FP32-pair factorization scheduled by tile readiness in one
+    cooperative launch performs the same operations on every tile as the
+    one-launch-per-block-column schedule, so whole chains agree bit for bit."""
+    d = problem(N, p, min(4, p), "f32", seed=p)
+    a = pkg.HSProbit(d["X"], d["y"], seed=5, use_graph=graph, chol_sched=pkg.SCHED_COLUMNS)
+    b = pkg.HSProbit(d["X"], d["y"], seed=5, use_graph=graph, chol_sched=pkg.SCHED_SINGLE)
+    assert a.launches_per_sweep() - b.launches_per_sweep() == (p + 31) // 32 - 1
+    a.sweep(4)
+    b.sweep(4)
+    assert np.array_equal(_state(a), _state(b))
+    a.close()
+    b.close()
+
+
 def test_deterministic_and_seed_sensitive(pkg, data):
     a = pkg.HSProbit(data["X"], data["y"], seed=3)
     b = pkg.HSProbit(data["X"], data["y"], seed=3)
