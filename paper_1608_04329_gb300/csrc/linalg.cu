@@ -493,72 +493,100 @@ __device__ __forceinline__ void tile_mma(df2 (*C)[NB + 1], const df2 (*As)[NB + 
   __syncthreads();
 }
 
-// Inverse Cholesky factor of a 32 x 32 tile: L^{-1} with D = L L^T.
-// Elimination in LDL^T form: at column c the multipliers m_rc = W_rc / W_cc
-// (r > c) update the trailing lower triangle, W_rq -= m_rc W_qc (c < q <= r),
-// and the same row operations act on U (the identity at the start),
-// U_rq -= m_rc U_cq (q <= c < r), so that U = L_u^{-1} for D = L_u diag(W_cc) L_u^T.
-// Then L^{-1} = diag(W_cc)^{-1/2} U.  Each update is formed as (W_rc y) / W_cc,
-// so the product overlaps the reciprocal of the pivot.  W and U are separate
-// tiles and no entry read at step c is written at step c, so one barrier per
-// column suffices.  Warp w owns rows w, w+8, w+16, w+24 and lane q column q;
-// the four rows are computed without branches (all loads first, stores
-// predicated), which keeps the step's work in flight together.
-// Output: Li = L^{-1} (lower, zero above) and LiT its transpose; W is
-// destroyed; s_rs[r] = W_rr^{-1/2} at elimination.  A pivot that is not
-// positive and finite is replaced by 1 and reported.  blockDim.x must be 256.
-__device__ void potri_df(df2 (*W)[NB + 1], df2 (*Li)[NB + 1], df2 (*LiT)[NB + 1], df2* s_piv, df2* s_rs,
-                         int* err, bool report) {
-  const int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    const int r = e >> 5, c = e & 31;
-    Li[r][c] = df2{r == c ? 1.0f : 0.0f, 0.0f};
-  }
+// Inverse Cholesky factor of a 16 x 16 diagonal block of a tile, at rows
+// and columns o..o+15.  Elimination in LDL^T form: at column c the
+// multipliers m_rc = W_rc / W_cc (r > c) update the trailing lower triangle,
+// W_rq -= m_rc W_qc (c < q <= r), and the same row operations act on U (the
+// identity at the start), U_rq -= m_rc U_cq (q <= c < r), so that
+// U = L_u^{-1} for W = L_u diag(W_cc) L_u^T; then L^{-1} = diag(W_cc)^{-1/2} U.
+// Each update is formed as (W_rc y) / W_cc, so the product overlaps the
+// reciprocal of the pivot.  No entry read at step c is written at step c
+// (column c of W, row c of U), so one barrier per column suffices; thread
+// (r, q) = (tid / 16, tid % 16) owns entry (r, q) of W and U.  U is written at
+// the same place of Ui; W is destroyed.  A pivot that is not positive and
+// finite is replaced by 1 and reported.  blockDim.x must be 256.
+__device__ void potri16_df(df2 (*W)[NB + 1], df2 (*Ui)[NB + 1], int o, df2* s_piv, df2* s_rs, int* err,
+                           bool report) {
+  const int tid = threadIdx.x, r = tid >> 4, q = tid & 15;
+  Ui[o + r][o + q] = df2{r == q ? 1.0f : 0.0f, 0.0f};
   __syncthreads();
-  const int w = tid >> 5, q = tid & 31;
-  for (int c = 0; c < NB; ++c) {
-    df2 d = W[c][c];
+  for (int c = 0; c < 16; ++c) {
+    df2 d = W[o + c][o + c];
     const bool bad = !(d.hi > 0.0f) || !isfinite(d.hi);
     if (bad) d = df2{1.0f, 0.0f};
     if (tid == 0) {
-      if (bad && report && *(volatile int*)err == 0) set_error(err, isfinite(W[c][c].hi) ? kErrNotPD : kErrNonFinite);
-      s_piv[c] = d;
+      if (bad && report && *(volatile int*)err == 0)
+        set_error(err, isfinite(W[o + c][o + c].hi) ? kErrNotPD : kErrNonFinite);
+      s_piv[o + c] = d;
     }
-    if (w + 24 > c) {  // some of this warp's rows are still below the pivot
-      const df2 dinv = df_recip_fast(d);
-      const bool trailing = q > c;
-      df2 wr[4], y[4], x[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = w + 8 * i;
-        wr[i] = W[r][c];
-        y[i] = trailing ? W[q][c] : Li[c][q];
-        x[i] = trailing ? W[r][q] : Li[r][q];
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = w + 8 * i;
-        const df2 v = df_sub(x[i], df_mul(df_mul(wr[i], y[i]), dinv));  // x - (W_rc y) / W_cc
-        if (r > c && q <= r) {
-          if (trailing)
-            W[r][q] = v;
-          else
-            Li[r][q] = v;
-        }
-      }
+    const bool trailing = q > c;
+    const df2 wr = W[o + r][o + c];
+    const df2 y = trailing ? W[o + q][o + c] : Ui[o + c][o + q];
+    const df2 x = trailing ? W[o + r][o + q] : Ui[o + r][o + q];
+    const df2 dinv = df_recip_fast(d);
+    const df2 v = df_sub(x, df_mul(df_mul(wr, y), dinv));  // x - (W_rc y) / W_cc
+    if (r > c && q <= r) {
+      if (trailing)
+        W[o + r][o + q] = v;
+      else
+        Ui[o + r][o + q] = v;
     }
     __syncthreads();
   }
-  if (tid < NB) {
+  if (tid < 16) {
     df2 sq;
-    df_sqrt_rsqrt_fast(s_piv[tid], sq, s_rs[tid]);
+    df_sqrt_rsqrt_fast(s_piv[o + tid], sq, s_rs[o + tid]);
   }
   __syncthreads();
+  const df2 u = Ui[o + r][o + q];
+  Ui[o + r][o + q] = q < r ? df_mul(u, s_rs[o + r]) : (q == r ? s_rs[o + r] : df2{0.0f, 0.0f});
+  __syncthreads();
+}
+
+// One entry of a 16 x 16 product of tile blocks, sum_{q in [q0, q1)} a(q) b(q),
+// with two accumulators (even and odd q).
+template <typename FA, typename FB>
+__device__ __forceinline__ df2 dot16(int q0, int q1, FA fa, FB fb) {
+  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+  int q = q0;
+  for (; q + 1 < q1; q += 2) {
+    df_fma(h0, l0, fa(q), fb(q));
+    df_fma(h1, l1, fa(q + 1), fb(q + 1));
+  }
+  if (q < q1) df_fma(h0, l0, fa(q), fb(q));
+  return df_add(df_renorm(h0, l0), df_renorm(h1, l1));
+}
+
+// Inverse Cholesky factor of a 32 x 32 tile, L^{-1} with D = L L^T, by 2 x 2
+// blocks of 16: L11^{-1} of D11; L21 = D21 L11^{-T}; S = D22 - L21 L21^T;
+// L22^{-1} of S; (L^{-1})21 = -L22^{-1} (L21 L11^{-1}).  Output: Li = L^{-1}
+// (lower, zero above) and LiT its transpose; D (W) is destroyed; LiT serves
+// as scratch until the end.  s_rs receives the reciprocal square roots of
+// the pivots.  blockDim.x must be 256.
+__device__ void potri_df(df2 (*W)[NB + 1], df2 (*Li)[NB + 1], df2 (*LiT)[NB + 1], df2* s_piv, df2* s_rs,
+                         int* err, bool report) {
+  const int tid = threadIdx.x, r = tid >> 4, c = tid & 15;
+  potri16_df(W, Li, 0, s_piv, s_rs, err, report);  // Li11
+  // L21[r][c] = sum_{q <= c} D21[r][q] Li11[c][q]       -> LiT[r][c]
+  LiT[r][c] = dot16(0, c + 1, [&](int q) { return W[16 + r][q]; }, [&](int q) { return Li[c][q]; });
+  __syncthreads();
+  // S = D22 - L21 L21^T (lower part), in place in W
+  if (c <= r) {
+    const df2 t = dot16(0, 16, [&](int q) { return LiT[r][q]; }, [&](int q) { return LiT[c][q]; });
+    W[16 + r][16 + c] = df_sub(W[16 + r][16 + c], t);
+  }
+  // T2 = L21 Li11: T2[r][c] = sum_{q >= c} L21[r][q] Li11[q][c]   -> LiT[16 + r][16 + c]
+  LiT[16 + r][16 + c] = dot16(c, 16, [&](int q) { return LiT[r][q]; }, [&](int q) { return Li[q][c]; });
+  __syncthreads();
+  potri16_df(W, Li, 16, s_piv, s_rs, err, report);  // Li22
+  // Li21[r][c] = -sum_{q <= r} Li22[r][q] T2[q][c]; upper block zero
+  Li[16 + r][c] = df_neg(dot16(0, r + 1, [&](int q) { return Li[16 + r][16 + q]; },
+                               [&](int q) { return LiT[16 + q][16 + c]; }));
+  Li[r][16 + c] = df2{0.0f, 0.0f};
+  __syncthreads();
   for (int e = tid; e < NB * NB; e += blockDim.x) {
-    const int r = e >> 5, c = e & 31;
-    const df2 v = c < r ? df_mul(Li[r][c], s_rs[r]) : (c == r ? s_rs[r] : df2{0.0f, 0.0f});
-    Li[r][c] = v;
-    LiT[c][r] = v;
+    const int rr = e >> 5, cc = e & 31;
+    LiT[cc][rr] = Li[rr][cc];
   }
   __syncthreads();
 }
