@@ -743,6 +743,16 @@ __host__ __device__ __forceinline__ int nUA(int T, int k) {
 }
 __host__ __device__ __forceinline__ int nUB(int T, int k) { return (T - k - 1) * (k + 1); }
 __host__ __device__ __forceinline__ int nTasks(int T, int k) { return nC(T, k) + k + nUA(T, k) + nUB(T, k); }
+// Worker tasks split in two families: A tasks (C, UA) build L and feed the
+// diagonal chain; B tasks (X, UB) build L^{-1} and are needed only after the
+// factorization.  The list runs in blocks s = 0..T-1+kBLag: block s holds the
+// A tasks of step s, then the B tasks of step s - kBLag, so inverse-factor
+// work fills the gaps behind the factorization instead of delaying it.  Every
+// task still comes after the tasks it reads.
+constexpr int kBLag = 4;
+__host__ __device__ __forceinline__ int nAt(int T, int k) { return k >= 0 && k < T ? nC(T, k) + nUA(T, k) : 0; }
+__host__ __device__ __forceinline__ int nBt(int T, int k) { return k >= 0 && k < T ? k + nUB(T, k) : 0; }
+__host__ __device__ __forceinline__ int nBlock(int T, int s) { return nAt(T, s) + nBt(T, s - kBLag); }
 __host__ __device__ inline int total_tasks(int T) {
   int n = 0;
   for (int k = 0; k < T; ++k) n += nTasks(T, k);
@@ -881,7 +891,7 @@ __device__ __forceinline__ void tile_store_cg(df2* M, int P, int ti, int tj, con
 __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
   __shared__ DTile sD, sW, sX1, sX2, sLi;
   __shared__ df2 s_piv[NB], s_rs[NB];
-  __shared__ int s_step0[kMaxTiles + 1];
+  __shared__ int s_step0[kMaxTiles + kBLag + 1];
   __shared__ unsigned long long s_e;
   __shared__ int s_role;  // 0 worker, 1 chain, 2 idle
   __shared__ int s_task;
@@ -957,16 +967,17 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
     }
   } else if (s_role == 0) {
     // ---------------- workers: tasks in list order from a shared counter ----------------
+    const int nblk = T + kBLag;
     if (threadIdx.x == 0) {
       int acc = 0;
-      for (int k = 0; k <= T; ++k) {
-        s_step0[k] = acc;
-        if (k < T) acc += nTasks(T, k);
+      for (int b = 0; b <= nblk; ++b) {
+        s_step0[b] = acc;
+        if (b < nblk) acc += nBlock(T, b);
       }
     }
     __syncthreads();
-    const int total = s_step0[T];
-    int k = 0;
+    const int total = s_step0[nblk];
+    int blk = 0;
     unsigned long long grabbed = 0;
     if (threadIdx.x == 0) grabbed = atomicAdd(ps.next, 1ull);
     for (;;) {
@@ -975,11 +986,14 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
       const int t = s_task;
       if (t >= total) break;
       if (threadIdx.x == 0) grabbed = atomicAdd(ps.next, 1ull);  // the following task, early
-      while (t >= s_step0[k + 1]) ++k;  // a worker's tasks come in increasing order
-      int u = t - s_step0[k];
+      while (t >= s_step0[blk + 1]) ++blk;  // a worker's tasks come in increasing order
+      int u = t - s_step0[blk];
+      const bool a_task = u < nAt(T, blk);
+      const int k = a_task ? blk : blk - kBLag;
+      if (!a_task) u -= nAt(T, blk);
       const unsigned long long done_k = base + (unsigned long long)k;  // A tile after updates 0..k-1
       const int c = nC(T, k), ua = nUA(T, k);
-      if (u < c) {
+      if (a_task && u < c) {
         // C(i,k): L_ik = A_ik L_kk^{-T}, i = k + 2 + u
         const int i = k + 2 + u;
         const unsigned long long* const wp2[2] = {&ps.flagLi[k], &ps.cntA[i * T + k]};
@@ -999,8 +1013,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         block_publish(&ps.flagL[i * T + k], e);
         continue;
       }
-      u -= c;
-      if (u < k) {
+      if (!a_task && u < k) {
         // X(k,j): X_kj = L_kk^{-1} B_kj, j = u; B_kj after its k - j updates
         const int j = u;
         const unsigned long long* const wp2[2] = {&ps.flagLi[k], &ps.cntB[k * T + j]};
@@ -1015,8 +1028,8 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         block_publish(&ps.flagX[k * T + j], e);
         continue;
       }
-      u -= k;
-      if (u < ua) {
+      if (a_task) {
+        u -= c;
         // UA(i,j,k): A_ij -= L_ik L_jk^T.  The lower triangle of tile rows/cols
         // k+1..T-1 is listed column by column (column k+1, which feeds the
         // diagonal chain, first), without its first entry (k+1, k+1).
@@ -1044,7 +1057,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         block_publish(&ps.cntA[i * T + j], done_k + 1);
         continue;
       }
-      u -= ua;
+      u -= k;
       {
         // UB(i,j,k): B_ij -= L_ik X_kj (X_kk = L_kk^{-1}; B_ik starts at zero)
         const int i = k + 1 + u / (k + 1), j = u % (k + 1);
