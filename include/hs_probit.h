@@ -84,7 +84,8 @@ typedef struct hs_probit_config {
   void* stream;        /* cudaStream_t for the sweep; NULL: library-owned stream */
   const float* x_scales; /* HS_X_FP8E4M3 only: p column scales (host or device) */
   int32_t chol_sched;  /* HS_SCHED_*; ignored for HS_CHOL_F64 */
-  int32_t reserved[7];
+  int32_t num_chains;  /* K independent chains sharing X (1..32; > 1 needs HS_X_BF16 and p <= 1152) */
+  int32_t reserved[6];
 } hs_probit_config;
 
 /* Values of one sampler state (Eq. 12 variables).  Arrays are host memory of
@@ -99,7 +100,8 @@ typedef struct hs_probit_state_view {
 } hs_probit_state_view;
 
 /* Fill *cfg with defaults: F32 host X, thin 1, ring 1024, no debug, no graph,
- * HS_CHOL_DF32 with HS_SCHED_AUTO, device 0, chain 0, problem 0, library stream. */
+ * HS_CHOL_DF32 with HS_SCHED_AUTO, device 0, chain 0, problem 0, library stream,
+ * one chain. */
 void hs_probit_config_default(hs_probit_config* cfg);
 
 /* Create a sampler for host X (float32, N x p row-major) and host y (N bytes in
@@ -216,6 +218,36 @@ int hs_probit_xstream_noalloc(int x_dtype, const void* X, int64_t ld, const uint
                               int64_t p, const void* beta_c, const float* x_scales, uint64_t seed,
                               uint32_t chain, uint32_t problem, int64_t sweep, double* xtz, double* z,
                               void* stream);
+
+/* ---- K chains on one X (Sect. 5 sweep for each chain; batched form) --------
+ * A handle made with cfg.num_chains = K > 1 runs K independent chains on the
+ * same BF16 X.  Chain m uses chain id cfg.chain + m in its Philox counters, so
+ * it is the same transition as a one-chain handle with that chain id.  The
+ * X-stream of all K chains is one pass over X on the tensor cores (eta = X B
+ * and X^T Z as BF16 products, beta and z each split into two BF16 parts,
+ * FP32 accumulation); every other step runs per chain.  The sweep count k is
+ * shared: hs_probit_sweep advances every chain, and the last set_state call
+ * sets k for all of them.  The functions without a chain argument act on
+ * chain 0. */
+
+/* Number of chains of the handle (>= 1), or HS_EINVAL. */
+int hs_probit_num_chains(const hs_probit* h);
+
+/* hs_probit_get_state / set_state for chain 0 <= chain < K.  HS_EINVAL for a
+ * chain out of range. */
+int hs_probit_get_state_chain(const hs_probit* h, int chain, hs_probit_state_view* out);
+int hs_probit_set_state_chain(hs_probit* h, int chain, const hs_probit_state_view* in);
+
+/* hs_probit_draws_available / hs_probit_draws for one chain (each chain keeps
+ * its own read position). */
+int64_t hs_probit_draws_available_chain(const hs_probit* h, int chain);
+int64_t hs_probit_draws_chain(hs_probit* h, int chain, double* beta, double* lambda_inv2, double* tau_inv2,
+                              int64_t max_draws);
+
+/* Debug copies (cfg.debug) of the last sweep's z (N values) and X^T z (p
+ * values) of one chain; host buffers owned by the caller. */
+int hs_probit_debug_z_chain(hs_probit* h, int chain, double* z_out);
+int hs_probit_debug_xtz_chain(hs_probit* h, int chain, double* xtz_out);
 
 /* Release the handle and everything it owns.  NULL is allowed. */
 void hs_probit_free(hs_probit* h);

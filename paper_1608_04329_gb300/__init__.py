@@ -50,7 +50,7 @@ class _Config(ctypes.Structure):
                 ("ring_size", ctypes.c_int32), ("debug", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("chol_arith", ctypes.c_int32), ("device", ctypes.c_int32), ("chain", ctypes.c_uint32),
                 ("problem", ctypes.c_uint32), ("stream", ctypes.c_void_p), ("x_scales", ctypes.c_void_p),
-                ("chol_sched", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("chol_sched", ctypes.c_int32), ("num_chains", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class _StateView(ctypes.Structure):
@@ -85,6 +85,14 @@ _PROTOS = {
                                              ctypes.POINTER(ctypes.c_int64)]),
     "hs_probit_launches_per_sweep": (ctypes.c_int64, [ctypes.c_void_p]),
     "hs_probit_debug_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "hs_probit_num_chains": (ctypes.c_int, [ctypes.c_void_p]),
+    "hs_probit_draws_available_chain": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int]),
+    "hs_probit_get_state_chain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(_StateView)]),
+    "hs_probit_set_state_chain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(_StateView)]),
+    "hs_probit_draws_chain": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_int64]),
+    "hs_probit_debug_z_chain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "hs_probit_debug_xtz_chain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "hs_probit_free": (None, [ctypes.c_void_p]),
     "hs_probit_xstream_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
@@ -142,7 +150,7 @@ class HSProbit:
     def __init__(self, X, y, seed: int = 0, *, scales=None, thin: int = 1, ring_size: int = 1024,
                  debug: bool = False, use_graph: bool = False, chol_arith: int = CHOL_DF32, chain: int = 0,
                  problem: int = 0, stream=None, device: int = 0, x_dtype: int | None = None,
-                 chol_sched: int = SCHED_AUTO):
+                 chol_sched: int = SCHED_AUTO, num_chains: int = 1):
         self._lib = load_library()
         self._h = None
         is_dev = hasattr(X, "is_cuda") and bool(X.is_cuda)
@@ -170,6 +178,7 @@ class HSProbit:
         cfg.use_graph = 1 if use_graph else 0
         cfg.chol_arith = chol_arith
         cfg.chol_sched = chol_sched
+        cfg.num_chains = num_chains
         cfg.device = device
         cfg.chain = chain
         cfg.problem = problem
@@ -198,50 +207,55 @@ class HSProbit:
     def sweep_status(self, n: int = 1) -> int:
         return int(self._lib.hs_probit_sweep(self._h, int(n)))
 
-    def draws(self, max_draws: int | None = None) -> dict:
-        avail = int(self._lib.hs_probit_draws_available(self._h))
+    def num_chains(self) -> int:
+        return int(self._lib.hs_probit_num_chains(self._h))
+
+    def draws(self, max_draws: int | None = None, chain: int = 0) -> dict:
+        avail = int(self._lib.hs_probit_draws_available_chain(self._h, int(chain)))
+        if avail < 0:
+            raise HSProbitError(avail, "hs_probit_draws_available_chain")
         n = avail if max_draws is None else min(avail, int(max_draws))
         beta = np.empty((n, self.p))
         lam = np.empty((n, self.p))
         tau = np.empty(n)
-        got = self._lib.hs_probit_draws(self._h, _ptr(beta), _ptr(lam), _ptr(tau), n)
+        got = self._lib.hs_probit_draws_chain(self._h, int(chain), _ptr(beta), _ptr(lam), _ptr(tau), n)
         if got < 0:
-            raise HSProbitError(got, "hs_probit_draws")
+            raise HSProbitError(got, "hs_probit_draws_chain")
         return {"beta": beta[:got], "lambda_inv2": lam[:got], "tau_inv2": tau[:got]}
 
-    def get_state(self) -> dict:
+    def get_state(self, chain: int = 0) -> dict:
         beta, lam, nu = np.empty(self.p), np.empty(self.p), np.empty(self.p)
         v = _StateView(_ptr(beta).value, _ptr(lam).value, _ptr(nu).value, 0.0, 0.0, 0)
-        st = self._lib.hs_probit_get_state(self._h, ctypes.byref(v))
+        st = self._lib.hs_probit_get_state_chain(self._h, int(chain), ctypes.byref(v))
         if st != 0:
-            raise HSProbitError(st, "hs_probit_get_state")
+            raise HSProbitError(st, "hs_probit_get_state_chain")
         return {"beta": beta, "lambda_inv2": lam, "nu_inv": nu, "tau_inv2": v.tau_inv2, "xi_inv": v.xi_inv,
                 "k": int(v.k)}
 
-    def set_state(self, beta, lambda_inv2, nu_inv, tau_inv2, xi_inv, k) -> None:
+    def set_state(self, beta, lambda_inv2, nu_inv, tau_inv2, xi_inv, k, chain: int = 0) -> None:
         b = np.ascontiguousarray(beta, dtype=np.float64)
         l_ = np.ascontiguousarray(lambda_inv2, dtype=np.float64)
         n_ = np.ascontiguousarray(nu_inv, dtype=np.float64)
         if b.shape != (self.p,) or l_.shape != (self.p,) or n_.shape != (self.p,):
             raise ValueError("state arrays must have length p")
         v = _StateView(_ptr(b).value, _ptr(l_).value, _ptr(n_).value, float(tau_inv2), float(xi_inv), int(k))
-        st = self._lib.hs_probit_set_state(self._h, ctypes.byref(v))
+        st = self._lib.hs_probit_set_state_chain(self._h, int(chain), ctypes.byref(v))
         if st != 0:
-            raise HSProbitError(st, "hs_probit_set_state")
+            raise HSProbitError(st, "hs_probit_set_state_chain")
 
     # ---- debug / inspection ----
-    def debug_z(self) -> np.ndarray:
+    def debug_z(self, chain: int = 0) -> np.ndarray:
         z = np.empty(self.N)
-        st = self._lib.hs_probit_debug_z(self._h, _ptr(z))
+        st = self._lib.hs_probit_debug_z_chain(self._h, int(chain), _ptr(z))
         if st != 0:
-            raise HSProbitError(st, "hs_probit_debug_z")
+            raise HSProbitError(st, "hs_probit_debug_z_chain")
         return z
 
-    def debug_xtz(self) -> np.ndarray:
+    def debug_xtz(self, chain: int = 0) -> np.ndarray:
         v = np.empty(self.p)
-        st = self._lib.hs_probit_debug_xtz(self._h, _ptr(v))
+        st = self._lib.hs_probit_debug_xtz_chain(self._h, int(chain), _ptr(v))
         if st != 0:
-            raise HSProbitError(st, "hs_probit_debug_xtz")
+            raise HSProbitError(st, "hs_probit_debug_xtz_chain")
         return v
 
     def gram(self) -> np.ndarray:

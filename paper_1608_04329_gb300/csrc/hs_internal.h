@@ -38,6 +38,35 @@ struct XStreamArgs {
 };
 constexpr int kSmMarks = 1024;
 
+// ---- batched X-stream of K chains on the tensor cores (BF16 X) ---------------
+struct XKArgs {
+  const uint8_t* y;       // N
+  int64_t N;
+  int p;
+  int nch;                // 64-feature chunks (even)
+  int fpad;               // nch * 64
+  int K;                  // chains (<= 32)
+  const void* bsw;        // nch x 8 KB: B^T (BF16 high and low parts), swizzled for the MMA
+  float* partials;        // grid x fpad x 32 FP32 (written)
+  double* z_out;          // K x N (chain-major), or nullptr
+  const int64_t* k_dev;   // sweeps done; this sweep is *k_dev + 1
+  RngKey rng;             // rng.chain is chain 0's id; chain m uses rng.chain + m
+  int* err;
+  unsigned int* sm_mark;  // or nullptr, as XStreamArgs::sm_mark
+};
+int xstream_k_chunks(int p);
+bool xstream_k_supported(int p);
+size_t xstream_k_smem_bytes(int p);
+cudaError_t xstream_k_prepare(int p);
+int xstream_k_grid(int64_t N, int num_sms);
+size_t xstream_k_partial_floats(int p, int grid);
+// Tensor map of BF16 X (N rows, ld columns) into map_out (128 bytes, 64-byte aligned); 0 on success.
+int xstream_k_make_map(const void* X, int64_t N, int ld, void* map_out);
+// B^T preparation and the X-stream kernel; then the fixed-order reduce of the partials.
+cudaError_t xstream_k_enqueue(const void* map, const XKArgs& a, const double* beta, int64_t beta_stride,
+                              unsigned char* bsw, int grid, cudaStream_t s);
+cudaError_t xstream_k_reduce(const XKArgs& a, int grid, double* xtz, int64_t xtz_stride, cudaStream_t s);
+
 // Per-process kernel attributes (shared-memory carveout); call before launching.
 cudaError_t xstream_prepare();
 cudaError_t linalg_prepare();
@@ -137,6 +166,10 @@ struct TailArgs {
 };
 cudaError_t tail_enqueue(const TailArgs& a, cudaStream_t s, int* launches);
 constexpr int kTailLaunches = 3;
+// The same in two parts (beta and nu draws; commit), for K chains whose commits
+// must all follow every chain's draws.
+cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s);
+cudaError_t commit_enqueue(const TailArgs& a, cudaStream_t s);
 
 // beta_c = (compute type)(beta * colscale), pads zero.
 cudaError_t beta_c_launch(const double* beta, const float* colscale, int p, int ld, void* beta_c,

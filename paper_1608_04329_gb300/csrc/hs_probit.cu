@@ -78,6 +78,14 @@ struct hs_probit {
   unsigned long long* chol_sync = nullptr;  // readiness words of the single-launch factorization
   unsigned int* sm_mark = nullptr;          // SM occupancy marks of the X-stream (single launch only)
   int chol_grid = 0;                        // its blocks; 0: one launch per block column
+  size_t chol_words = 0;                    // scheduling words per chain
+  // K chains sharing X: every per-chain buffer holds K slices (chain m at offset m * size)
+  int K = 1;
+  int64_t* k_scratch = nullptr;             // K: commits of chains 0..K-2 record the sweep here
+  int kgrid = 0;                            // batched X-stream CTAs
+  unsigned char* bsw = nullptr;             // B^T of the batched X-stream
+  float* kpartials = nullptr;
+  alignas(64) unsigned char xmap[128];      // tensor map of X (batched X-stream)
   void* partials = nullptr;
   int grid = 1;
   double* z = nullptr;
@@ -91,7 +99,7 @@ struct hs_probit {
 
   int sticky = HS_OK;
   int64_t k_host = 0;
-  int64_t drained = 0;       // draws (index k/thin) already handed out
+  std::vector<int64_t> drained;  // per chain: draws (index k/thin) already handed out
   int64_t launches = 0;
 
   bool graph_ready = false;
@@ -170,74 +178,104 @@ hs::XStreamArgs xstream_args(hs_probit* h) {
   return a;
 }
 
-hs::ShrinkArgs shrink_args(hs_probit* h) {
+hs::XKArgs xk_args(hs_probit* h) {
+  hs::XKArgs a{};
+  a.y = h->y;
+  a.N = h->N;
+  a.p = h->p;
+  a.nch = hs::xstream_k_chunks(h->p);
+  a.fpad = a.nch * 64;
+  a.K = h->K;
+  a.bsw = h->bsw;
+  a.partials = h->kpartials;
+  a.z_out = h->cfg.debug ? h->z : nullptr;
+  a.k_dev = h->k_dev;
+  a.rng = h->rng;
+  a.err = h->err;
+  a.sm_mark = h->sm_mark;
+  return a;
+}
+
+hs::RngKey chain_rng(const hs_probit* h, int m) {
+  hs::RngKey r = h->rng;
+  r.chain += (uint32_t)m;
+  return r;
+}
+
+size_t shrink_blocks(const hs_probit* h) { return (size_t)((h->p + 127) / 128); }
+
+hs::ShrinkArgs shrink_args(hs_probit* h, int m) {
+  const size_t p = (size_t)h->p;
   hs::ShrinkArgs a{};
   a.p = h->p;
   a.P = h->P;
-  a.rng = h->rng;
+  a.rng = chain_rng(h, m);
   a.k_dev = h->k_dev;
-  a.beta = h->beta;
-  a.lam = h->lam;
-  a.nu = h->nu;
-  a.scal = h->scal;
-  a.lam_new = h->lam_new;
-  a.tau_new = h->tau_new;
+  a.beta = h->beta + m * p;
+  a.lam = h->lam + m * p;
+  a.nu = h->nu + m * p;
+  a.scal = h->scal + 2 * m;
+  a.lam_new = h->lam_new + m * p;
+  a.tau_new = h->tau_new + m;
   a.G = h->G;
-  a.S = h->S;
-  a.part = h->shrink_part;
-  a.ticket = h->shrink_ticket;
+  a.S = h->S + (size_t)m * h->P;
+  a.part = h->shrink_part + m * shrink_blocks(h);
+  a.ticket = h->shrink_ticket + m;
   a.err = h->err;
   return a;
 }
 
-hs::CholArgs chol_args(hs_probit* h) {
+hs::CholArgs chol_args(hs_probit* h, int m) {
+  const size_t p = (size_t)h->p, P2 = (size_t)h->P * h->P;
   hs::CholArgs a{};
   a.p = h->p;
   a.P = h->P;
   a.G = h->G;
-  a.S = h->S;
-  a.lam_new = h->lam_new;
-  a.tau_new = h->tau_new;
-  a.A = h->A;
-  a.Linv = h->Linv;
-  a.LinvT = h->LinvT;
+  a.S = h->S + (size_t)m * h->P;
+  a.lam_new = h->lam_new + m * p;
+  a.tau_new = h->tau_new + m;
+  a.A = h->A + m * P2;
+  a.Linv = h->Linv + m * P2;
+  a.LinvT = h->LinvT + m * P2;
   a.err = h->err;
   a.arith = h->cfg.chol_arith;
-  a.sync = h->chol_sync;
+  a.sync = h->chol_sync ? h->chol_sync + m * h->chol_words : nullptr;
   a.persistent_grid = h->chol_grid;
   a.sm_mark = h->sm_mark;
   a.k_dev = h->k_dev;
   return a;
 }
 
-hs::TailArgs tail_args(hs_probit* h) {
+hs::TailArgs tail_args(hs_probit* h, int m) {
+  const size_t p = (size_t)h->p, P2 = (size_t)h->P * h->P, rp = (size_t)h->ring_size * p;
   hs::TailArgs a{};
   a.p = h->p;
   a.P = h->P;
   a.ld = h->ld;
-  a.rng = h->rng;
+  a.rng = chain_rng(h, m);
   a.k_dev = h->k_dev;
-  a.xtz = h->xtz;
-  a.S = h->S;
-  a.Linv = h->Linv;
-  a.LinvT = h->LinvT;
+  a.xtz = h->xtz + m * p;
+  a.S = h->S + (size_t)m * h->P;
+  a.Linv = h->Linv + m * P2;
+  a.LinvT = h->LinvT + m * P2;
   a.df32 = (h->cfg.chol_arith == HS_CHOL_DF32);
-  a.v = h->v;
-  a.beta_new = h->beta_new;
-  a.nu_new = h->nu_new;
-  a.lam_new = h->lam_new;
-  a.tau_new = h->tau_new;
-  a.beta = h->beta;
-  a.lam = h->lam;
-  a.nu = h->nu;
-  a.scal = h->scal;
-  a.k_dev_rw = h->k_dev;
-  a.beta_c = h->beta_c;
+  a.v = h->v + (size_t)m * h->P;
+  a.beta_new = h->beta_new + m * p;
+  a.nu_new = h->nu_new + m * p;
+  a.lam_new = h->lam_new + m * p;
+  a.tau_new = h->tau_new + m;
+  a.beta = h->beta + m * p;
+  a.lam = h->lam + m * p;
+  a.nu = h->nu + m * p;
+  a.scal = h->scal + 2 * m;
+  // the shared sweep count moves with the last chain's commit, after every chain's draws
+  a.k_dev_rw = (m == h->K - 1) ? h->k_dev : h->k_scratch + m;
+  a.beta_c = static_cast<unsigned char*>(h->beta_c) + (size_t)m * h->ld * (h->x_dtype == HS_X_F64 ? 8 : 4);
   a.beta_c_is_double = (h->x_dtype == HS_X_F64);
   a.colscale = h->colscale;
-  a.ring_beta = h->ring_beta;
-  a.ring_lam = h->ring_lam;
-  a.ring_tau = h->ring_tau;
+  a.ring_beta = h->ring_beta + m * rp;
+  a.ring_lam = h->ring_lam + m * rp;
+  a.ring_tau = h->ring_tau + (size_t)m * h->ring_size;
   a.ring_size = h->ring_size;
   a.thin = h->thin;
   a.err = h->err;
@@ -275,38 +313,52 @@ struct ProfSpan {
 // Enqueue one sweep (eager launches).  Returns a CUDA error or success.
 cudaError_t enqueue_sweep(hs_probit* h) {
   cudaError_t e;
-  int n = 0;
   if ((e = cudaEventRecord(h->ev_fork, h->s0)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(h->s1, h->ev_fork, 0)) != cudaSuccess) return e;
   {
     ProfSpan sp(h, 2, h->s1);
-    if ((e = hs::shrink_launch(shrink_args(h), h->s1)) != cudaSuccess) return e;
+    for (int m = 0; m < h->K; ++m)
+      if ((e = hs::shrink_launch(shrink_args(h, m), h->s1)) != cudaSuccess) return e;
   }
   {
     ProfSpan sp(h, 3, h->s1);
-    int nl = 0;
-    if ((e = hs::chol_enqueue(chol_args(h), h->s1, &nl)) != cudaSuccess) return e;
-    n += nl;
+    for (int m = 0; m < h->K; ++m) {
+      int nl = 0;
+      if ((e = hs::chol_enqueue(chol_args(h, m), h->s1, &nl)) != cudaSuccess) return e;
+    }
   }
   if ((e = cudaEventRecord(h->ev_join, h->s1)) != cudaSuccess) return e;
-  {
-    ProfSpan sp(h, 0, h->s0);
-    if ((e = hs::xstream_launch(h->x_dtype, xstream_args(h), h->grid, h->s0)) != cudaSuccess) return e;
-  }
-  {
-    ProfSpan sp(h, 1, h->s0);
-    if ((e = hs::reduce_partials_launch(h->x_dtype, h->partials, h->grid, h->ld, h->p, h->colscale, h->xtz,
-                                        h->s0)) != cudaSuccess)
-      return e;
+  if (h->K == 1) {
+    {
+      ProfSpan sp(h, 0, h->s0);
+      if ((e = hs::xstream_launch(h->x_dtype, xstream_args(h), h->grid, h->s0)) != cudaSuccess) return e;
+    }
+    {
+      ProfSpan sp(h, 1, h->s0);
+      if ((e = hs::reduce_partials_launch(h->x_dtype, h->partials, h->grid, h->ld, h->p, h->colscale, h->xtz,
+                                          h->s0)) != cudaSuccess)
+        return e;
+    }
+  } else {
+    const hs::XKArgs xa = xk_args(h);
+    {
+      ProfSpan sp(h, 0, h->s0);
+      if ((e = hs::xstream_k_enqueue(h->xmap, xa, h->beta, h->p, h->bsw, h->kgrid, h->s0)) != cudaSuccess)
+        return e;
+    }
+    {
+      ProfSpan sp(h, 1, h->s0);
+      if ((e = hs::xstream_k_reduce(xa, h->kgrid, h->xtz, h->p, h->s0)) != cudaSuccess) return e;
+    }
   }
   if ((e = cudaStreamWaitEvent(h->s0, h->ev_join, 0)) != cudaSuccess) return e;
   {
     ProfSpan sp(h, 4, h->s0);
-    int nl = 0;
-    if ((e = hs::tail_enqueue(tail_args(h), h->s0, &nl)) != cudaSuccess) return e;
-    n += nl;
+    for (int m = 0; m < h->K; ++m)
+      if ((e = hs::tail_draw_enqueue(tail_args(h, m), h->s0)) != cudaSuccess) return e;
+    for (int m = 0; m < h->K; ++m)
+      if ((e = hs::commit_enqueue(tail_args(h, m), h->s0)) != cudaSuccess) return e;
   }
-  (void)n;
   return cudaSuccess;
 }
 
@@ -429,6 +481,7 @@ void hs_probit_config_default(hs_probit_config* cfg) {
   cfg->use_graph = 0;
   cfg->chol_arith = HS_CHOL_DF32;
   cfg->chol_sched = HS_SCHED_AUTO;
+  cfg->num_chains = 1;
   cfg->device = 0;
 }
 
@@ -469,6 +522,16 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
     fail(HS_EINVAL);
     return nullptr;
   }
+  // K chains (num_chains > 1): BF16 X on the tensor-core X-stream, chain ids chain .. chain+K-1
+  const int Kc = cfg.num_chains > 1 ? cfg.num_chains : 1;
+  if (cfg.num_chains < 0 || Kc > 32 || (uint64_t)cfg.chain + (uint64_t)Kc > (1u << 24)) {
+    fail(HS_EINVAL);
+    return nullptr;
+  }
+  if (Kc > 1 && (cfg.x_dtype != HS_X_BF16 || !hs::xstream_k_supported((int)p))) {
+    fail(HS_EUNSUPPORTED);
+    return nullptr;
+  }
   {
     // The X-stream takes at most 2048 16-byte slices per row (p <= 4096 for FP64 X).
     const int64_t eb = cfg.x_dtype == HS_X_F64 ? 8 : cfg.x_dtype == HS_X_F32 ? 4 : cfg.x_dtype == HS_X_BF16 ? 2 : 1;
@@ -502,6 +565,8 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
     return nullptr;
   }
   h->cfg = cfg;
+  h->K = Kc;
+  h->drained.assign((size_t)Kc, 0);
   h->device = cfg.device;
   h->x_dtype = cfg.x_dtype;
   h->N = N;
@@ -543,38 +608,51 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   check(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   const size_t P2 = (size_t)h->P * h->P;
   const size_t pd = (size_t)p * sizeof(double);
+  const size_t K = (size_t)h->K;
+  const size_t bc_bytes = (size_t)h->ld * (h->x_dtype == HS_X_F64 ? 8 : 4);
   h->grid = hs::xstream_grid(h->x_dtype, h->p, h->ld, N, num_sms > 0 ? num_sms : 1);
+  if (h->K > 1) {
+    check(hs::xstream_k_prepare(h->p));
+    h->kgrid = hs::xstream_k_grid(N, num_sms > 0 ? num_sms : 1);
+  }
+  h->chol_words = hs::chol_sync_words(h->P);
   check(h->alloc(&h->X, (size_t)N * h->ld * h->elem));
   check(h->alloc(&h->y, (size_t)N));
   if (cfg.x_dtype == HS_X_FP8E4M3) check(h->alloc(&h->colscale, (size_t)p * sizeof(float)));
-  check(h->alloc(&h->beta, pd));
-  check(h->alloc(&h->lam, pd));
-  check(h->alloc(&h->nu, pd));
-  check(h->alloc(&h->scal, 2 * sizeof(double)));
+  check(h->alloc(&h->beta, K * pd));
+  check(h->alloc(&h->lam, K * pd));
+  check(h->alloc(&h->nu, K * pd));
+  check(h->alloc(&h->scal, K * 2 * sizeof(double)));
   check(h->alloc(&h->k_dev, sizeof(int64_t)));
-  check(h->alloc(&h->lam_new, pd));
-  check(h->alloc(&h->tau_new, sizeof(double)));
-  check(h->alloc(&h->beta_new, pd));
-  check(h->alloc(&h->nu_new, pd));
-  check(h->alloc(&h->beta_c, (size_t)h->ld * (h->x_dtype == HS_X_F64 ? 8 : 4)));
+  check(h->alloc(&h->k_scratch, K * sizeof(int64_t)));
+  check(h->alloc(&h->lam_new, K * pd));
+  check(h->alloc(&h->tau_new, K * sizeof(double)));
+  check(h->alloc(&h->beta_new, K * pd));
+  check(h->alloc(&h->nu_new, K * pd));
+  check(h->alloc(&h->beta_c, K * bc_bytes));
   check(h->alloc(&h->G, (size_t)p * p * sizeof(double)));
-  check(h->alloc(&h->S, (size_t)h->P * sizeof(double)));
-  check(h->alloc(&h->A, P2 * sizeof(double)));
-  check(h->alloc(&h->Linv, P2 * sizeof(double)));
-  check(h->alloc(&h->LinvT, P2 * sizeof(double)));
-  check(h->alloc(&h->xtz, pd));
-  check(h->alloc(&h->v, (size_t)h->P * sizeof(double)));
-  check(h->alloc(&h->shrink_part, (size_t)((p + 127) / 128) * sizeof(double)));
-  check(h->alloc(&h->shrink_ticket, sizeof(unsigned int)));
+  check(h->alloc(&h->S, K * (size_t)h->P * sizeof(double)));
+  check(h->alloc(&h->A, K * P2 * sizeof(double)));
+  check(h->alloc(&h->Linv, K * P2 * sizeof(double)));
+  check(h->alloc(&h->LinvT, K * P2 * sizeof(double)));
+  check(h->alloc(&h->xtz, K * pd));
+  check(h->alloc(&h->v, K * (size_t)h->P * sizeof(double)));
+  check(h->alloc(&h->shrink_part, K * shrink_blocks(h) * sizeof(double)));
+  check(h->alloc(&h->shrink_ticket, K * sizeof(unsigned int)));
   if (h->chol_grid > 0) {
-    check(h->alloc(&h->chol_sync, hs::chol_sync_words(h->P) * sizeof(unsigned long long)));
+    check(h->alloc(&h->chol_sync, K * h->chol_words * sizeof(unsigned long long)));
     check(h->alloc(&h->sm_mark, hs::kSmMarks * sizeof(unsigned int)));
   }
-  check(h->alloc(&h->partials, (size_t)h->grid * h->ld * hs::partial_elem_bytes(h->x_dtype)));
-  if (cfg.debug) check(h->alloc(&h->z, (size_t)N * sizeof(double)));
-  check(h->alloc(&h->ring_beta, (size_t)h->ring_size * pd));
-  check(h->alloc(&h->ring_lam, (size_t)h->ring_size * pd));
-  check(h->alloc(&h->ring_tau, (size_t)h->ring_size * sizeof(double)));
+  if (h->K == 1) {
+    check(h->alloc(&h->partials, (size_t)h->grid * h->ld * hs::partial_elem_bytes(h->x_dtype)));
+  } else {
+    check(h->alloc(&h->bsw, (size_t)hs::xstream_k_chunks(h->p) * 8192));
+    check(h->alloc(&h->kpartials, hs::xstream_k_partial_floats(h->p, h->kgrid) * sizeof(float)));
+  }
+  if (cfg.debug) check(h->alloc(&h->z, K * (size_t)N * sizeof(double)));
+  check(h->alloc(&h->ring_beta, K * (size_t)h->ring_size * pd));
+  check(h->alloc(&h->ring_lam, K * (size_t)h->ring_size * pd));
+  check(h->alloc(&h->ring_tau, K * (size_t)h->ring_size * sizeof(double)));
   check(h->alloc(&h->err, sizeof(int)));
   check(h->alloc(&h->hook_err, sizeof(int)));
   check(h->alloc(&h->hook_flag, sizeof(int)));
@@ -595,23 +673,23 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   if (h->colscale) check(cudaMemcpyAsync(h->colscale, cfg.x_scales, (size_t)p * sizeof(float), kind, h->s0));
   check(cudaMemsetAsync(h->err, 0, sizeof(int), h->s0));
   check(cudaMemsetAsync(h->hook_err, 0, sizeof(int), h->s0));
-  check(cudaMemsetAsync(h->shrink_ticket, 0, sizeof(unsigned int), h->s0));
+  check(cudaMemsetAsync(h->shrink_ticket, 0, K * sizeof(unsigned int), h->s0));
   if (h->chol_sync) {
-    check(cudaMemsetAsync(h->chol_sync, 0, hs::chol_sync_words(h->P) * sizeof(unsigned long long), h->s0));
+    check(cudaMemsetAsync(h->chol_sync, 0, K * h->chol_words * sizeof(unsigned long long), h->s0));
     check(cudaMemsetAsync(h->sm_mark, 0, hs::kSmMarks * sizeof(unsigned int), h->s0));
   }
+  if (h->K > 1 && e == cudaSuccess && hs::xstream_k_make_map(h->X, N, h->ld, h->xmap) != 0) e = cudaErrorInvalidValue;
   if (cfg.x_is_device) check(hs::check_y_launch(h->y, N, h->err, h->s0));
-  // ---- cold start (Sect. 6.1): beta = 0, lambda = nu = tau = xi = 1, k = 0 ----
+  // ---- cold start (Sect. 6.1): beta = 0, lambda = nu = tau = xi = 1, k = 0, every chain ----
   {
-    std::vector<double> ones((size_t)p, 1.0);
-    const double sc[2] = {1.0, 1.0};
+    std::vector<double> ones(K * (size_t)p, 1.0), sc(2 * K, 1.0);
     const int64_t k0 = 0;
-    check(cudaMemsetAsync(h->beta, 0, pd, h->s0));
-    check(cudaMemcpyAsync(h->lam, ones.data(), pd, cudaMemcpyHostToDevice, h->s0));
-    check(cudaMemcpyAsync(h->nu, ones.data(), pd, cudaMemcpyHostToDevice, h->s0));
-    check(cudaMemcpyAsync(h->scal, sc, sizeof(sc), cudaMemcpyHostToDevice, h->s0));
+    check(cudaMemsetAsync(h->beta, 0, K * pd, h->s0));
+    check(cudaMemcpyAsync(h->lam, ones.data(), K * pd, cudaMemcpyHostToDevice, h->s0));
+    check(cudaMemcpyAsync(h->nu, ones.data(), K * pd, cudaMemcpyHostToDevice, h->s0));
+    check(cudaMemcpyAsync(h->scal, sc.data(), 2 * K * sizeof(double), cudaMemcpyHostToDevice, h->s0));
     check(cudaMemcpyAsync(h->k_dev, &k0, sizeof(k0), cudaMemcpyHostToDevice, h->s0));
-    check(cudaMemsetAsync(h->beta_c, 0, (size_t)h->ld * (h->x_dtype == HS_X_F64 ? 8 : 4), h->s0));
+    check(cudaMemsetAsync(h->beta_c, 0, K * bc_bytes, h->s0));
     check(cudaStreamSynchronize(h->s0));  // host staging buffers go out of scope
   }
   // ---- one-time Gram matrix (Sect. 5, beta update, step i) ----
@@ -633,7 +711,9 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
     fail(st);
     return nullptr;
   }
-  h->launches = 1 + hs::chol_launch_count(h->P, h->cfg.chol_arith, h->chol_grid) + 2 + hs::kTailLaunches;
+  // per chain: shrink, the factorization, two draws, commit; then the X-stream and its reduce
+  h->launches = (int64_t)h->K * (1 + hs::chol_launch_count(h->P, h->cfg.chol_arith, h->chol_grid) + 2 + 1) +
+                (h->K == 1 ? 2 : 3);
   return h;
 }
 
@@ -676,58 +756,69 @@ int hs_probit_sweep(hs_probit* h, int64_t n_iter) {
   return st;
 }
 
-int64_t hs_probit_draws_available(const hs_probit* h) {
-  if (!h) return HS_EINVAL;
+int64_t hs_probit_draws_available_chain(const hs_probit* h, int chain) {
+  if (!h || chain < 0 || chain >= h->K) return HS_EINVAL;
   const int64_t newest = h->k_host / h->thin;
-  int64_t first = h->drained + 1;
+  int64_t first = h->drained[chain] + 1;
   if (newest - first + 1 > h->ring_size) first = newest - h->ring_size + 1;
   return newest >= first ? newest - first + 1 : 0;
 }
 
-int64_t hs_probit_draws(hs_probit* h, double* beta, double* lambda_inv2, double* tau_inv2, int64_t max_draws) {
-  if (!h || max_draws < 0) return HS_EINVAL;
+int64_t hs_probit_draws_available(const hs_probit* h) { return hs_probit_draws_available_chain(h, 0); }
+
+int64_t hs_probit_draws_chain(hs_probit* h, int chain, double* beta, double* lambda_inv2, double* tau_inv2,
+                              int64_t max_draws) {
+  if (!h || max_draws < 0 || chain < 0 || chain >= h->K) return HS_EINVAL;
   DeviceGuard dg(h->device);
   if (!dg.ok) return HS_ECUDA;
   if (cudaStreamSynchronize(h->s0) != cudaSuccess) return HS_ECUDA;
   const int64_t newest = h->k_host / h->thin;
-  int64_t first = h->drained + 1;
+  int64_t first = h->drained[chain] + 1;
   if (newest - first + 1 > h->ring_size) first = newest - h->ring_size + 1;
   int64_t count = newest >= first ? newest - first + 1 : 0;
   if (count > max_draws) count = max_draws;
   const size_t p = (size_t)h->p;
+  const double* rb = h->ring_beta + (size_t)chain * h->ring_size * p;
+  const double* rl = h->ring_lam + (size_t)chain * h->ring_size * p;
+  const double* rt = h->ring_tau + (size_t)chain * h->ring_size;
   for (int64_t d = 0; d < count;) {
     const int64_t slot = (first + d - 1) % h->ring_size;
     int64_t run = h->ring_size - slot;
     if (run > count - d) run = count - d;
     cudaError_t e = cudaSuccess;
-    if (beta)
-      e = cudaMemcpy(beta + d * p, h->ring_beta + slot * p, run * p * sizeof(double), cudaMemcpyDeviceToHost);
+    if (beta) e = cudaMemcpy(beta + d * p, rb + slot * p, run * p * sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && lambda_inv2)
-      e = cudaMemcpy(lambda_inv2 + d * p, h->ring_lam + slot * p, run * p * sizeof(double),
-                     cudaMemcpyDeviceToHost);
+      e = cudaMemcpy(lambda_inv2 + d * p, rl + slot * p, run * p * sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && tau_inv2)
-      e = cudaMemcpy(tau_inv2 + d, h->ring_tau + slot, run * sizeof(double), cudaMemcpyDeviceToHost);
+      e = cudaMemcpy(tau_inv2 + d, rt + slot, run * sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return HS_ECUDA;
     d += run;
   }
-  h->drained = first + count - 1;
+  h->drained[chain] = first + count - 1;
   return count;
 }
 
-int hs_probit_get_state(const hs_probit* hc, hs_probit_state_view* out) {
+int64_t hs_probit_draws(hs_probit* h, double* beta, double* lambda_inv2, double* tau_inv2, int64_t max_draws) {
+  return hs_probit_draws_chain(h, 0, beta, lambda_inv2, tau_inv2, max_draws);
+}
+
+int hs_probit_num_chains(const hs_probit* h) { return h ? h->K : HS_EINVAL; }
+
+int hs_probit_get_state_chain(const hs_probit* hc, int chain, hs_probit_state_view* out) {
   hs_probit* h = const_cast<hs_probit*>(hc);
-  if (!h || !out) return HS_EINVAL;
+  if (!h || !out || chain < 0 || chain >= h->K) return HS_EINVAL;
   DeviceGuard dg(h->device);
   if (!dg.ok) return HS_ECUDA;
   if (cudaStreamSynchronize(h->s0) != cudaSuccess) return HS_ECUDA;
-  const size_t pd = (size_t)h->p * sizeof(double);
+  const size_t pd = (size_t)h->p * sizeof(double), off = (size_t)chain * h->p;
   cudaError_t e = cudaSuccess;
-  if (out->beta) e = cudaMemcpy(out->beta, h->beta, pd, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && out->lambda_inv2) e = cudaMemcpy(out->lambda_inv2, h->lam, pd, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && out->nu_inv) e = cudaMemcpy(out->nu_inv, h->nu, pd, cudaMemcpyDeviceToHost);
+  if (out->beta) e = cudaMemcpy(out->beta, h->beta + off, pd, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && out->lambda_inv2)
+    e = cudaMemcpy(out->lambda_inv2, h->lam + off, pd, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && out->nu_inv) e = cudaMemcpy(out->nu_inv, h->nu + off, pd, cudaMemcpyDeviceToHost);
   double sc[2] = {0, 0};
   int64_t k = 0;
-  if (e == cudaSuccess) e = cudaMemcpy(sc, h->scal, sizeof(sc), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(sc, h->scal + 2 * chain, sizeof(sc), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&k, h->k_dev, sizeof(k), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return HS_ECUDA;
   out->tau_inv2 = sc[0];
@@ -736,48 +827,61 @@ int hs_probit_get_state(const hs_probit* hc, hs_probit_state_view* out) {
   return HS_OK;
 }
 
-int hs_probit_set_state(hs_probit* h, const hs_probit_state_view* in) {
+int hs_probit_get_state(const hs_probit* h, hs_probit_state_view* out) { return hs_probit_get_state_chain(h, 0, out); }
+
+int hs_probit_set_state_chain(hs_probit* h, int chain, const hs_probit_state_view* in) {
   if (!h || !in || !in->beta || !in->lambda_inv2 || !in->nu_inv || in->k < 0 || !std::isfinite(in->tau_inv2) ||
-      !std::isfinite(in->xi_inv) || in->k >= (int64_t)0xFFFFFFFF)
+      !std::isfinite(in->xi_inv) || in->k >= (int64_t)0xFFFFFFFF || chain < 0 || chain >= h->K)
     return HS_EINVAL;
   DeviceGuard dg(h->device);
   if (!dg.ok) return HS_ECUDA;
   if (cudaStreamSynchronize(h->s0) != cudaSuccess) return HS_ECUDA;
   if (cudaStreamSynchronize(h->s1) != cudaSuccess) return HS_ECUDA;
-  const size_t pd = (size_t)h->p * sizeof(double);
+  const size_t pd = (size_t)h->p * sizeof(double), off = (size_t)chain * h->p;
   const double sc[2] = {in->tau_inv2, in->xi_inv};
   const int64_t k = in->k;
-  cudaError_t e = cudaMemcpy(h->beta, in->beta, pd, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->lam, in->lambda_inv2, pd, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->nu, in->nu_inv, pd, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->scal, sc, sizeof(sc), cudaMemcpyHostToDevice);
+  const size_t bc_bytes = (size_t)h->ld * (h->x_dtype == HS_X_F64 ? 8 : 4);
+  cudaError_t e = cudaMemcpy(h->beta + off, in->beta, pd, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->lam + off, in->lambda_inv2, pd, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->nu + off, in->nu_inv, pd, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->scal + 2 * chain, sc, sizeof(sc), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->k_dev, &k, sizeof(k), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int));
   if (e == cudaSuccess)
-    e = hs::beta_c_launch(h->beta, h->colscale, h->p, h->ld, h->beta_c, h->x_dtype == HS_X_F64 ? 1 : 0, h->s0);
+    e = hs::beta_c_launch(h->beta + off, h->colscale, h->p, h->ld,
+                          static_cast<unsigned char*>(h->beta_c) + (size_t)chain * bc_bytes,
+                          h->x_dtype == HS_X_F64 ? 1 : 0, h->s0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s0);
   if (e != cudaSuccess) return HS_ECUDA;
   h->sticky = HS_OK;
   h->k_host = k;
-  h->drained = k / h->thin;
+  for (auto& d : h->drained) d = k / h->thin;
   return HS_OK;
 }
 
-int hs_probit_debug_z(hs_probit* h, double* z_out) {
-  if (!h || !z_out) return HS_EINVAL;
+int hs_probit_set_state(hs_probit* h, const hs_probit_state_view* in) { return hs_probit_set_state_chain(h, 0, in); }
+
+int hs_probit_debug_z_chain(hs_probit* h, int chain, double* z_out) {
+  if (!h || !z_out || chain < 0 || chain >= h->K) return HS_EINVAL;
   if (!h->cfg.debug) return HS_EUNSUPPORTED;
   DeviceGuard dg(h->device);
   if (cudaStreamSynchronize(h->s0) != cudaSuccess) return HS_ECUDA;
-  return cuda_status(cudaMemcpy(z_out, h->z, (size_t)h->N * sizeof(double), cudaMemcpyDeviceToHost));
+  return cuda_status(cudaMemcpy(z_out, h->z + (size_t)chain * h->N, (size_t)h->N * sizeof(double),
+                                cudaMemcpyDeviceToHost));
 }
 
-int hs_probit_debug_xtz(hs_probit* h, double* xtz_out) {
-  if (!h || !xtz_out) return HS_EINVAL;
+int hs_probit_debug_z(hs_probit* h, double* z_out) { return hs_probit_debug_z_chain(h, 0, z_out); }
+
+int hs_probit_debug_xtz_chain(hs_probit* h, int chain, double* xtz_out) {
+  if (!h || !xtz_out || chain < 0 || chain >= h->K) return HS_EINVAL;
   if (!h->cfg.debug) return HS_EUNSUPPORTED;
   DeviceGuard dg(h->device);
   if (cudaStreamSynchronize(h->s0) != cudaSuccess) return HS_ECUDA;
-  return cuda_status(cudaMemcpy(xtz_out, h->xtz, (size_t)h->p * sizeof(double), cudaMemcpyDeviceToHost));
+  return cuda_status(cudaMemcpy(xtz_out, h->xtz + (size_t)chain * h->p, (size_t)h->p * sizeof(double),
+                                cudaMemcpyDeviceToHost));
 }
+
+int hs_probit_debug_xtz(hs_probit* h, double* xtz_out) { return hs_probit_debug_xtz_chain(h, 0, xtz_out); }
 
 int hs_probit_gram(hs_probit* h, double* G_out) {
   if (!h || !G_out) return HS_EINVAL;

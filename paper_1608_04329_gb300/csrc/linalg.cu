@@ -1324,6 +1324,23 @@ cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches) {
   return cudaGetLastError();
 }
 
+cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s) {
+  const int nb = (a.p * 32 + 255) / 256;
+  if (a.df32) {
+    tail_w_kernel<df2><<<nb, 256, 0, s>>>(a);
+    tail_beta_kernel<df2><<<nb, 256, 0, s>>>(a);
+  } else {
+    tail_w_kernel<double><<<nb, 256, 0, s>>>(a);
+    tail_beta_kernel<double><<<nb, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t commit_enqueue(const TailArgs& a, cudaStream_t s) {
+  commit_kernel<<<1, 1024, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t tail_enqueue(const TailArgs& a, cudaStream_t s, int* launches) {
   const int nb = (a.p * 32 + 255) / 256;
   if (a.df32) {

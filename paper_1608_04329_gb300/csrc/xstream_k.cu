@@ -1,0 +1,435 @@
+// Batched X-stream on the fifth-generation tensor cores: K chains that share
+// one BF16 design matrix X (Sect. 5 schedule, step (i) latent draw and the
+// X^T z of the beta update, for K chains at once).
+//
+// For a tile of 128 rows of X:
+//   pass 1   eta'  = X_tile [B_hi | B_lo]            (128 x 2K, tcgen05, TMEM)
+//            eta   = eta'_hi + eta'_lo               (per row and chain)
+//            z     ~ TN(eta, 1) truncated by y (Eq. 12, first line), branch-free
+//                    inverse CDF on the chain's own Philox counters
+//   pass 2   XtZ  += X_tile^T Z_hi + X_tile^T Z_lo   (p x K, tcgen05, TMEM)
+// where beta (FP64) is split into two BF16 parts B_hi + B_lo and so is z, so
+// that the products carry about 16 significant bits of beta and z; X itself
+// is exact in BF16 and the tensor cores accumulate in FP32.
+//
+// Data movement: X tiles arrive by TMA (box 64 features x 128 rows, 128-byte
+// swizzle) in a ring of 4 stages; pass 2 reads the same tile again, which the
+// 129 MB L2 still holds, so HBM sees X once per sweep.  B^T (both parts, all
+// features) stays in shared memory for the whole launch.  Each CTA owns a
+// contiguous range of row tiles and keeps its X^T Z partial in TMEM; at the
+// end it writes the partial (p x 32, FP32) and a second kernel sums the
+// partials in a fixed order in FP64.
+//
+// Warp roles (256 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues
+// tcgen05.mma, warp 2 owns the TMEM allocation, warps 4..7 (one per TMEM lane
+// quadrant, thread = tile row) read eta, draw z and write Z^T.  Every wait is
+// bounded (2 s); a wait that runs out sets the timeout bit and all roles wind
+// down through a shared abort flag.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "hs_common.cuh"
+#include "hs_internal.h"
+
+namespace hs {
+namespace {
+
+constexpr int kKc = 32;          // chains per launch (padded)
+constexpr int kTR = 128;         // rows per tile (MMA M of pass 1; K of pass 2)
+constexpr int kCF = 64;          // features per chunk (one 128-byte swizzle row)
+constexpr int kXStages = 4;      // ring stages
+constexpr uint32_t kStageBytes = kTR * kCF * 2;       // 16 KB
+constexpr uint32_t kBChunkBytes = 2 * kKc * kCF * 2;  // 8 KB: 64 rows (hi chains, lo chains) x 128 B
+constexpr uint32_t kZBlock = kKc * 128;               // 4 KB: 32 chains x 64 rows x 2 B
+constexpr int kThreads = 256;
+
+// ---- tcgen05 helpers (shared-memory descriptors, 128-byte swizzle) ---------
+// Descriptor: start address >> 4 in bits 0-13, leading byte offset >> 4 in
+// 16-29, stride byte offset >> 4 in 32-45, version 1 in 46-47, layout in
+// 61-63 (2 = 128-byte swizzle).  K-major operand: 8-row groups of 128-byte
+// rows SBO apart.  MN-major operand: 64-element atoms LBO apart along M/N and
+// 8-row K groups SBO apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (2ull << 61);
+}
+// Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9, 10-12 = 1), A/B major (bits 15, 16; 1 = MN-major), N >> 3 in
+// bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on an mbarrier once every tcgen05.mma issued so far has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 32 consecutive columns of TMEM into 32 registers per thread.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 2-D TMA load of one box into shared memory, completing on an mbarrier.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Byte offset of element (row n, column k < 64) in a 128-byte-swizzled K-major
+// block whose 8-row groups are 1024 bytes apart (the layout TMA writes).
+__host__ __device__ __forceinline__ uint32_t sw128_off(int n, int k) {
+  const uint32_t byte = (uint32_t)k * 2;
+  return (uint32_t)(n >> 3) * 1024u + (uint32_t)(n & 7) * 128u + ((((byte >> 4) ^ (uint32_t)(n & 7)) & 7u) << 4) +
+         (byte & 15u);
+}
+
+struct XKShared {
+  uint64_t full[kXStages], empty[kXStages];
+  uint64_t bfull, eta_full, eta_empty, z_ready, zt_empty, acc_done;
+  uint32_t tmem;
+  int abort;
+};
+
+// Bounded wait; on timeout records the error and raises the CTA's abort flag.
+__device__ __forceinline__ bool xk_wait(uint64_t* bar, uint32_t parity, XKShared* sh, int* err) {
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_test(bar, parity)) {
+    if (*(volatile int*)&sh->abort) return false;
+    if (global_ns() - t0 > 2000000000ull) {
+      set_error(err, kErrTimeout);
+      *(volatile int*)&sh->abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    xstream_k_kernel(const __grid_constant__ CUtensorMap xmap, XKArgs a) {
+  extern __shared__ unsigned char dyn[];
+  __shared__ XKShared sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* base = dyn + ((1024u - (smem_u32(dyn) & 1023u)) & 1023u);  // 1024-byte aligned
+  unsigned char* sB = base;                                           // nch x 8 KB
+  unsigned char* sX = sB + (size_t)a.nch * kBChunkBytes;              // kXStages x 16 KB
+  unsigned char* sZ = sX + (size_t)kXStages * kStageBytes;            // [hi/lo][rows 0-63 | 64-127] x 4 KB
+  const int64_t ntiles = (a.N + kTR - 1) / kTR;
+  const int64_t t0 = ntiles * blockIdx.x / gridDim.x;
+  const int64_t t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+  const int nch = a.nch;       // even
+  const int ngrp = nch / 2;    // 128-feature groups of pass 2
+
+  if (tid == 0) {
+    if (a.sm_mark) {
+      // tell the factorization, running beside this kernel, which SMs are busy here
+      unsigned int smid;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      if (smid < (unsigned)kSmMarks) a.sm_mark[smid] = (unsigned int)(*a.k_dev + 1);
+    }
+    for (int s = 0; s < kXStages; ++s) {
+      mbar_init(&sh.full[s], 1);
+      mbar_init(&sh.empty[s], 1);
+    }
+    mbar_init(&sh.bfull, 1);
+    mbar_init(&sh.eta_full, 1);
+    mbar_init(&sh.eta_empty, 128);
+    mbar_init(&sh.z_ready, 128);
+    mbar_init(&sh.zt_empty, 1);
+    mbar_init(&sh.acc_done, 1);
+    sh.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&sh.tmem)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh.tmem;
+  const uint32_t tm_eta = tmem;        // columns [0, 64): eta' (hi chains, lo chains)
+  const uint32_t tm_xtz = tmem + 64;   // columns [64 + 32 g, 96 + 32 g): X^T Z of feature group g
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    mbar_arrive_expect_tx(&sh.bfull, (uint32_t)nch * kBChunkBytes);
+    bulk_g2s(sB, a.bsw, (uint32_t)nch * kBChunkBytes, &sh.bfull);
+    uint32_t q = 0;
+    for (int64_t t = t0; t < t1 && !sh.abort; ++t) {
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int c = 0; c < nch; ++c, ++q) {
+          const int s = q % kXStages;
+          if (!xk_wait(&sh.empty[s], ((q / kXStages) & 1) ^ 1, &sh, a.err)) break;
+          mbar_arrive_expect_tx(&sh.full[s], kStageBytes);
+          tma_load_2d(sX + (size_t)s * kStageBytes, &xmap, c * kCF, (int)(t * kTR), &sh.full[s]);
+        }
+      }
+    }
+    // drain: every issued load must land before the CTA may exit
+    const uint32_t nd = q < (uint32_t)kXStages ? q : (uint32_t)kXStages;
+    for (uint32_t d = 1; d <= nd; ++d) {
+      const uint32_t qq = q - d;
+      mbar_wait(&sh.full[qq % kXStages], (qq / kXStages) & 1, 2000000000ull);
+    }
+    mbar_wait(&sh.bfull, 0, 2000000000ull);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    const uint32_t id_eta = idesc_bf16(kTR, 2 * kKc, 0, 0);   // M 128 rows, N 64 (hi, lo), both K-major
+    const uint32_t id_xtz = idesc_bf16(128, kKc, 1, 0);       // M 128 features (MN-major A), N 32 chains
+    bool ok = xk_wait(&sh.bfull, 0, &sh, a.err);
+    tc_fence_after();
+    uint32_t q = 0;
+    int it = 0;
+    for (int64_t t = t0; t < t1 && ok; ++t, ++it) {
+      // pass 1: eta' of the tile (the epilogue must have read the previous one)
+      if (!(ok = xk_wait(&sh.eta_empty, (it & 1) ^ 1, &sh, a.err))) break;
+      tc_fence_after();
+      for (int c = 0; c < nch; ++c, ++q) {
+        const int s = q % kXStages;
+        if (!(ok = xk_wait(&sh.full[s], (q / kXStages) & 1, &sh, a.err))) break;
+        tc_fence_after();
+        const uint32_t xa = smem_u32(sX + (size_t)s * kStageBytes);
+        const uint32_t ba = smem_u32(sB + (size_t)c * kBChunkBytes);
+#pragma unroll
+        for (int kk = 0; kk < kCF / 16; ++kk)
+          mma_bf16(tm_eta, sw128_desc(xa + kk * 32, 16, 1024), sw128_desc(ba + kk * 32, 16, 1024), id_eta,
+                   (c > 0 || kk > 0) ? 1 : 0);
+        mma_commit(&sh.empty[s]);
+      }
+      if (!ok) break;
+      mma_commit(&sh.eta_full);
+      // pass 2: X^T Z once the epilogue has written Z^T of this tile
+      if (!(ok = xk_wait(&sh.z_ready, it & 1, &sh, a.err))) break;
+      tc_fence_after();
+      for (int g = 0; g < ngrp && ok; ++g) {
+        const int s0 = q % kXStages;  // even: chunks 2g and 2g+1 sit in stages s0, s0+1
+        if (!(ok = xk_wait(&sh.full[s0], (q / kXStages) & 1, &sh, a.err))) break;
+        if (!(ok = xk_wait(&sh.full[s0 + 1], ((q + 1) / kXStages) & 1, &sh, a.err))) break;
+        tc_fence_after();
+        const uint32_t xa = smem_u32(sX + (size_t)s0 * kStageBytes);
+#pragma unroll
+        for (int kk = 0; kk < kTR / 16; ++kk) {
+          const uint64_t ad = sw128_desc(xa + kk * 2048, kStageBytes, 1024);  // rows 16kk.., features of both stages
+#pragma unroll
+          for (int hl = 0; hl < 2; ++hl) {
+            const uint32_t za = smem_u32(sZ + (size_t)(hl * 2 + kk / 4) * kZBlock) + (kk % 4) * 32;
+            mma_bf16(tm_xtz + 32 * g, ad, sw128_desc(za, 16, 1024), id_xtz, (it > 0 || kk > 0 || hl > 0) ? 1 : 0);
+          }
+        }
+        mma_commit(&sh.empty[s0]);
+        mma_commit(&sh.empty[s0 + 1]);
+        q += 2;
+      }
+      if (!ok) break;
+      mma_commit(&sh.zt_empty);
+    }
+    mma_commit(&sh.acc_done);
+  } else if (warp >= 4) {
+    // ---------------- epilogue: z draws and Z^T ----------------
+    const int er = tid - 128;  // row within the tile = TMEM lane
+    const uint32_t lane_off = (uint32_t)(32 * (warp - 4)) << 16;
+    const Rng rng{a.rng.k0, a.rng.k1, a.rng.chain, a.rng.problem};
+    const uint32_t sweep = (uint32_t)(*a.k_dev + 1);
+    int it = 0;
+    for (int64_t t = t0; t < t1; ++t, ++it) {
+      if (!xk_wait(&sh.eta_full, it & 1, &sh, a.err)) break;
+      tc_fence_after();
+      uint32_t hi[32], lo[32];
+      tmem_ld32(tm_eta + lane_off, hi);
+      tmem_ld32(tm_eta + lane_off + 32, lo);
+      tmem_ld_wait();
+      tc_fence_before();
+      mbar_arrive(&sh.eta_empty);
+      const int64_t i = t * kTR + er;
+      const bool active = i < a.N;
+      const int yi = active ? a.y[i] : 1;
+      // Z^T (both parts) for pass 2, once pass 2 of the previous tile is done with it
+      if (!xk_wait(&sh.zt_empty, (it & 1) ^ 1, &sh, a.err)) break;
+      const int katom = er >> 6, kr = er & 63;
+#pragma unroll 4
+      for (int m = 0; m < kKc; ++m) {
+        const float eta = __uint_as_float(hi[m]) + __uint_as_float(lo[m]);
+        const bool on = active && m < a.K;
+        double u = 0.5, uc = 0.5;
+        if (on) {
+          const Rng r{rng.k0, rng.k1, rng.chain + (uint32_t)m, rng.problem};
+          const uint4 wd = r.words((uint32_t)i, sweep, kPurZ);
+          unit_pair(wd.x, wd.y, u, uc);
+        }
+        const float ms = on ? (yi ? eta : -eta) : 0.0f;
+        float zp = tn_main<float>(ms, (float)u, (float)uc);
+        const bool tail = on && ms < TnMath<float>::kTail;
+        if (tail) zp = tn_tail<float>(ms, (float)u, (float)uc);
+        zp = zp > TnMath<float>::tiny() ? zp : TnMath<float>::tiny();
+        float zz = on ? (yi ? zp : -zp) : 0.0f;
+        if (on && !isfinite(zz)) {
+          set_error(a.err, kErrNonFinite);
+          zz = 0.0f;
+        }
+        if (on && a.z_out) a.z_out[(size_t)m * a.N + i] = (double)zz;
+        const __nv_bfloat16 zh = __float2bfloat16_rn(zz);
+        const __nv_bfloat16 zl = __float2bfloat16_rn(zz - __bfloat162float(zh));
+        const uint32_t o = sw128_off(m, kr);
+        *reinterpret_cast<__nv_bfloat16*>(sZ + (size_t)(0 * 2 + katom) * kZBlock + o) = zh;
+        *reinterpret_cast<__nv_bfloat16*>(sZ + (size_t)(1 * 2 + katom) * kZBlock + o) = zl;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+      mbar_arrive(&sh.z_ready);
+    }
+    // the CTA's X^T Z partial: row = feature 128 g + er, 32 chains
+    if (xk_wait(&sh.acc_done, 0, &sh, a.err)) {
+      tc_fence_after();
+      for (int g = 0; g < ngrp; ++g) {
+        uint32_t r[32];
+        tmem_ld32(tm_xtz + 32 * g + lane_off, r);
+        tmem_ld_wait();
+        const int f = 128 * g + er;
+        float* out = a.partials + ((size_t)blockIdx.x * a.fpad + f) * kKc;
+#pragma unroll
+        for (int m = 0; m < kKc; m += 4)
+          *reinterpret_cast<float4*>(out + m) = make_float4(__uint_as_float(r[m]), __uint_as_float(r[m + 1]),
+                                                            __uint_as_float(r[m + 2]), __uint_as_float(r[m + 3]));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+// B^T in the shared-memory layout of pass 1: chunk c holds features 64c..64c+63
+// of 64 rows (rows 0..31: BF16 high parts of the K chains' beta (scaled to
+// the stored X), rows 32..63: the low parts beta - hi), 128-byte swizzled.
+__global__ void bsw_prep_kernel(const double* __restrict__ beta, int64_t beta_stride, int K, int p, int nch,
+                                unsigned char* __restrict__ bsw) {
+  const int64_t n_el = (int64_t)nch * 64 * kCF;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / (64 * kCF)), rem = (int)(e % (64 * kCF));
+    const int n = rem / kCF, k = rem % kCF;
+    const int m = n & 31, f = c * kCF + k;
+    float v = 0.0f;
+    if (m < K && f < p) {
+      const double b = beta[(int64_t)m * beta_stride + f];
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)b);
+      v = n < 32 ? __bfloat162float(h) : (float)(b - (double)__bfloat162float(h));
+    }
+    *reinterpret_cast<__nv_bfloat16*>(bsw + (size_t)c * kBChunkBytes + sw128_off(n, k)) = __float2bfloat16_rn(v);
+  }
+}
+
+// X^T z of chain m, feature j: fixed-order FP64 sum over the CTAs' partials.
+__global__ void reduce_k_kernel(const float* __restrict__ part, int grid, int fpad, int p, int K,
+                                double* __restrict__ xtz, int64_t xtz_stride) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p * K) return;
+  const int m = e / p, j = e % p;
+  double s = 0.0;
+  for (int c = 0; c < grid; ++c) s += (double)part[((size_t)c * fpad + j) * kKc + m];
+  xtz[(int64_t)m * xtz_stride + j] = s;
+}
+
+}  // namespace
+
+int xstream_k_chunks(int p) {
+  const int nch = (p + kCF - 1) / kCF;
+  return (nch + 1) & ~1;
+}
+
+size_t xstream_k_smem_bytes(int p) {
+  return 1024 + (size_t)xstream_k_chunks(p) * kBChunkBytes + (size_t)kXStages * kStageBytes + 4 * (size_t)kZBlock;
+}
+
+bool xstream_k_supported(int p) {
+  const int nch = xstream_k_chunks(p);
+  // TMEM: 64 columns of eta' + 32 per 128-feature group; shared memory as above
+  return p >= 1 && 64 + 32 * (nch / 2) <= 512 && xstream_k_smem_bytes(p) <= 227 * 1024;
+}
+
+cudaError_t xstream_k_prepare(int p) {
+  return cudaFuncSetAttribute((const void*)xstream_k_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)xstream_k_smem_bytes(p));
+}
+
+// The tensor map of X (ld columns, N rows, BF16, row stride ld * 2 bytes):
+// boxes of 64 x 128 with 128-byte swizzle; reads outside X return zeros.
+int xstream_k_make_map(const void* X, int64_t N, int ld, void* map_out) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult qr;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess || !fn)
+      return -1;
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)N};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kCF, (cuuint32_t)kTR};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                            const_cast<void*>(X), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+int xstream_k_grid(int64_t N, int num_sms) {
+  const int64_t ntiles = (N + kTR - 1) / kTR;
+  int64_t g = num_sms > 1 ? (int64_t)num_sms - 1 : 1;
+  if (g > ntiles) g = ntiles;
+  return (int)(g < 1 ? 1 : g);
+}
+
+size_t xstream_k_partial_floats(int p, int grid) {
+  return (size_t)grid * (size_t)(xstream_k_chunks(p) * kCF) * kKc;
+}
+
+cudaError_t xstream_k_enqueue(const void* map, const XKArgs& a, const double* beta, int64_t beta_stride,
+                              unsigned char* bsw, int grid, cudaStream_t s) {
+  bsw_prep_kernel<<<64, 256, 0, s>>>(beta, beta_stride, a.K, a.p, a.nch, bsw);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap m;
+  memcpy(&m, map, sizeof(m));
+  xstream_k_kernel<<<grid, kThreads, xstream_k_smem_bytes(a.p), s>>>(m, a);
+  return cudaGetLastError();
+}
+
+cudaError_t xstream_k_reduce(const XKArgs& a, int grid, double* xtz, int64_t xtz_stride, cudaStream_t s) {
+  reduce_k_kernel<<<(a.p * a.K + 255) / 256, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, xtz, xtz_stride);
+  return cudaGetLastError();
+}
+
+}  // namespace hs

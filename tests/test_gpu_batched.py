@@ -1,0 +1,107 @@
+"""K chains on one BF16 X through the C ABI: the tensor-core X-stream (eta = X B
+and X^T Z with two-part BF16 operands) and the per-chain factorization and
+draws.  Chain m of a K-chain handle must reproduce the oracle's transition
+for chain id (chain + m) from the same state (Eq. 12 and the schedule of
+Sect. 5).
+
+Tolerance.  X is exact in BF16; beta enters the tensor cores as hi + lo, two
+BF16 numbers, so each beta_j carries a relative error of at most 2^-16 (two
+roundings to 8 significant bits), and the products accumulate in FP32 over p
+terms.  Hence per row |d eta_i| <= (2^-16 + p 2^-24) sum_j |x_ij beta_j|, and
+since the truncated-normal quantile moves by at most as much as its mean,
+|d z_i| is bounded by the same amount plus the FP32 sampler's own error
+(1e-5 max(|z|, 1), as on the single-chain FP32 path).  X^T z (z also split
+in two parts) and beta are compared normwise at 1e-4; lambda, tau, nu, xi
+have identical inputs on both sides (1e-12).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests.gpu_common import lib_pkg, problem, random_state, x_f64
+
+
+def assert_batched_close(got, ref, X, beta0):
+    z, zt = got["z"], ref.extra["z"]
+    assert np.all(np.sign(z) == np.sign(zt)) and np.all(z != 0)
+    p = X.shape[1]
+    bound = (2.0**-16 + p * 2.0**-24) * (np.abs(X) @ np.abs(beta0)) + 1e-5 * np.maximum(np.abs(zt), 1.0)
+    excess = np.abs(z - zt) / bound
+    assert excess.max() <= 1.0, ("z", excess.max(), int(excess.argmax()))
+    xt = ref.extra["xtz"]
+    assert np.linalg.norm(got["xtz"] - xt) <= 1e-4 * max(np.linalg.norm(xt), 1.0), "xtz"
+    db = np.linalg.norm(got["beta"] - ref.beta) / max(np.linalg.norm(ref.beta), 1e-300)
+    assert db <= 1e-4, ("beta", db)
+    np.testing.assert_allclose(got["lambda_inv2"], ref.lam_inv2, rtol=1e-12)
+    np.testing.assert_allclose(got["tau_inv2"], ref.tau_inv2, rtol=1e-12)
+    np.testing.assert_allclose(got["nu_inv"], ref.nu_inv, rtol=1e-12)
+    np.testing.assert_allclose(got["xi_inv"], ref.xi_inv, rtol=1e-12)
+    assert got["k"] == ref.k
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    return lib_pkg()
+
+
+def _batched_transitions(pkg, d, states, seed, chain0=0, **kw):
+    K = len(states)
+    s = pkg.HSProbit(d["X"], d["y"], seed=seed, debug=True, num_chains=K, chain=chain0, **kw)
+    try:
+        assert s.num_chains() == K
+        for m, st in enumerate(states):
+            s.set_state(st.beta, st.lam_inv2, st.nu_inv, st.tau_inv2, st.xi_inv, st.k, chain=m)
+        s.sweep(1)
+        out = []
+        for m in range(K):
+            g = s.get_state(chain=m)
+            g["z"] = s.debug_z(chain=m)
+            g["xtz"] = s.debug_xtz(chain=m)
+            out.append(g)
+    finally:
+        s.close()
+    return out
+
+
+@pytest.mark.parametrize("N,p,K", [(3001, 200, 5), (1000, 64, 2), (20003, 1000, 32), (257, 1, 3), (4099, 1100, 8)])
+def test_batched_chains_match_oracle(pkg, N, p, K):
+    d = problem(N, p, min(5, p), "bf16", seed=N % 97)
+    X = x_f64(d)
+    G = oracle.gram(X)
+    states = [random_state(p, k=9, seed=100 + m) for m in range(K)]
+    got = _batched_transitions(pkg, d, states, seed=321, chain0=7)
+    for m, st in enumerate(states):
+        ref = oracle.sweep_once(st.copy(), X, d["y"], G, 321, chain=7 + m, keep=True)
+        assert_batched_close(got[m], ref, X, st.beta)
+
+
+def test_batched_graph_equals_eager_and_chains_differ(pkg):
+    d = problem(5000, 300, 5, "bf16", seed=3)
+    outs = []
+    for graph in (False, True):
+        s = pkg.HSProbit(d["X"], d["y"], seed=11, num_chains=4, use_graph=graph)
+        s.sweep(3)
+        outs.append([s.get_state(chain=m)["beta"] for m in range(4)])
+        s.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    assert not np.array_equal(outs[0][0], outs[0][1])
+
+
+def test_batched_draw_rings_per_chain(pkg):
+    d = problem(3000, 50, 3, "bf16", seed=5)
+    s = pkg.HSProbit(d["X"], d["y"], seed=2, num_chains=3, ring_size=8)
+    s.sweep(5)
+    for m in range(3):
+        dr = s.draws(chain=m)
+        assert dr["beta"].shape == (5, 50)
+        assert np.array_equal(dr["beta"][-1], s.get_state(chain=m)["beta"])
+    s.close()
+
+
+def test_batched_needs_bf16(pkg):
+    d = problem(1000, 20, 2, "f32", seed=1)
+    with pytest.raises(pkg.HSProbitError):
+        pkg.HSProbit(d["X"], d["y"], num_chains=4)
