@@ -31,7 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "Gibbs sweeps/sec at N=1e6,p=1000 (1 chain); % HBM roofline"
+METRIC = "Gibbs sweeps/sec at N=1e6,p=1000 (1 chain and K chains); % HBM roofline"
 WORKLOADS = {
     "c1s": dict(N=200_000, p=1000, nz=10, dt="f32",
                 name="horseshoe-probit sweep, N=2e5, p=1000, X iid N(0,1) fp32 (profiling case, 800 MB)"),
@@ -39,6 +39,10 @@ WORKLOADS = {
                name="horseshoe-probit sweep, N=1e6, p=1000, X iid N(0,1) fp32, 10 nonzeros U[1,3], 1 chain"),
     "c0": dict(N=10_000, p=100, nz=5, dt="f64",
                name="horseshoe-probit sweep, N=1e4, p=100, X iid N(0,1) fp64, 5 nonzeros U[1,3], 1 chain"),
+    "c2": dict(N=1_000_000, p=1000, nz=10, dt="bf16",
+               name="horseshoe-probit sweep of K chains, N=1e6, p=1000, X iid N(0,1) bf16, 10 nonzeros U[1,3]"),
+    "c2s": dict(N=200_000, p=1000, nz=10, dt="bf16",
+                name="horseshoe-probit sweep of K chains, N=2e5, p=1000, X iid N(0,1) bf16 (profiling case, 400 MB)"),
 }
 XSTREAM_SOURCES = ["paper_1608_04329_gb300/csrc/xstream.cu", "paper_1608_04329_gb300/csrc/hs_common.cuh"]
 
@@ -200,6 +204,49 @@ def run_reference(args, wl, dist, rank):
     return 0
 
 
+def run_k_chains(args, wk, pkg, torch, dist, ws, rank, local, chol, one_chain_value):
+    """The batched form: K chains on BF16 X; chain-sweeps/s and the X-stream roofline."""
+    peak, peak_kind = _peaks()
+    dk = make_data(wk)
+    sk = pkg.HSProbit(dk["X"], dk["y"], seed=0, chain=32 * rank, device=local, use_graph=bool(args.graph),
+                      chol_arith=chol, num_chains=args.k_chains, ring_size=max(args.k_steps + 3, 16))
+    streamk = torch.cuda.ExternalStream(sk.stream(), device=local)
+    sk.sweep(3)
+    sk.set_profiling(bool(args.profile))
+    barrier(dist)
+    torch.cuda.synchronize()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        k0.record(streamk)
+        sk.sweep(args.k_steps)
+        k1.record(streamk)
+        torch.cuda.synchronize()
+    barrier(dist)
+    kms = max_over_ranks(dist, k0.elapsed_time(k1))
+    kgroups = {g: sk.kernel_time(g) for g in ("xstream", "reduce", "shrink", "cholesky", "tail")}
+    klaunches = sk.launches_per_sweep()
+    sk.set_profiling(False)
+    sk.close()
+    kx_ms, kx_n = kgroups["xstream"]
+    kbytes = wk["N"] * (wk["p"] * 2 + 1)
+    kroof = None
+    if kx_n > 0:
+        kavg = kx_ms / kx_n
+        kach = kbytes / (kavg / 1e3) / 1e9
+        kroof = {"bound": "hbm", "achieved": kach, "peak": peak, "unit": "GB/s", "frac": kach / peak,
+                 "traffic": None, "peak_source": peak_kind,
+                 "kernel": "xstream_k (B prep + tensor-core X-stream)", "avg_launch_ms": kavg,
+                 "tensor_tflops": 4.0 * wk["N"] * 1024 * 2 * 32 / (kavg / 1e3) / 1e12}
+    kvalue = ws * args.k_chains * args.k_steps / (kms / 1e3)
+    return {"value": kvalue, "unit": "chain-sweeps/s", "K": args.k_chains, "x_dtype": "bf16",
+            "steps": args.k_steps, "warmup": 3, "ms_per_sweep": kms / args.k_steps,
+            "vs_one_chain_fp32": (kvalue / one_chain_value) if one_chain_value else None,
+            "kernel_ms_per_sweep": {g: (v[0] / max(v[1], 1)) for g, v in kgroups.items()},
+            "gpu_launches_per_sweep": klaunches, "roofline": kroof, "clocks": clk.summary(),
+            "workload": wk["name"]}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -215,6 +262,9 @@ def main(argv=None):
     ap.add_argument("--profile", type=int, default=1,
                     help="1: CUDA events around each kernel group in the timed region (eager launches)")
     ap.add_argument("--ref-budget", type=float, default=120.0)
+    ap.add_argument("--k-chains", type=int, default=32,
+                    help="also time the batched form: K chains on BF16 X (0: skip)")
+    ap.add_argument("--k-steps", type=int, default=20)
     args = ap.parse_args(argv)
     wl = WORKLOADS[args.workload]
     dist, rank, ws, local = _dist()
@@ -230,8 +280,20 @@ def main(argv=None):
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     torch.cuda.set_device(local)
-    d = make_data(wl)
     chol = pkg.CHOL_F64 if args.chol == "f64" else pkg.CHOL_DF32
+    if wl["dt"] == "bf16":
+        # the batched form alone (profiling and K-chain runs)
+        kch = run_k_chains(args, wl, pkg, torch, dist, ws, rank, local, chol, None)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": kch["value"], "unit": kch["unit"], "n_gpus": ws,
+                              "steps": args.k_steps, "warmup": 3, "ms_per_step": kch["ms_per_sweep"],
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                              "data": "synthetic", "config": {"workload": wl["name"], "K": args.k_chains},
+                              "k_chains": kch}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    d = make_data(wl)
     s = pkg.HSProbit(d["X"], d["y"], seed=0, chain=rank, device=local, use_graph=bool(args.graph),
                      chol_arith=chol, ring_size=max(args.steps + args.warmup, 16))
     stream = torch.cuda.ExternalStream(s.stream(), device=local)
@@ -293,6 +355,11 @@ def main(argv=None):
                "includes": "init from pinned host X and y (H2D copy + FP64 Gram) amortised over the steps, "
                            "then per step one sweep and the D2H of its draw (beta, lambda^-2, tau^-2)"}
 
+    # ---- K chains on BF16 X (tensor-core X-stream), same N and p ----
+    kch = None
+    if args.k_chains > 1:
+        kch = run_k_chains(args, WORKLOADS["c2"], pkg, torch, dist, ws, rank, local, chol, value)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, done, t, t_gram = cpu_oracle_rate(d, wl, n_sweeps=args.cpu_sweeps)
@@ -313,7 +380,8 @@ def main(argv=None):
                 "gpu_launches": launches,
                 "clocks": clk.summary(),
                 "kernel_ms_per_sweep": {g: (v[0] / max(v[1], 1)) for g, v in groups.items()},
-                "hbm_roofline_frac_whole_sweep": (bytes_per_launch / (ms / args.steps / 1e3) / 1e9) / 8000.0}
+                "hbm_roofline_frac_whole_sweep": (bytes_per_launch / (ms / args.steps / 1e3) / 1e9) / 8000.0,
+                "k_chains": kch}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -106,7 +106,8 @@ struct ShrinkArgs {
   unsigned int* ticket;   // zero between sweeps (scratch)
   int* err;
 };
-cudaError_t shrink_launch(const ShrinkArgs& a, cudaStream_t s);
+// nchains > 1: chains 0..nchains-1 at fixed strides past a's buffers (blockIdx.y = chain)
+cudaError_t shrink_launch(const ShrinkArgs& a, cudaStream_t s, int nchains = 1);
 
 // ---- Cholesky of A = G + tau^{-2} Lambda^{-2} (scaled) and its inverse ------
 struct CholArgs {
@@ -124,6 +125,11 @@ struct CholArgs {
   int persistent_grid;       // > 0: that schedule with this many blocks; 0: one launch per block column
   const unsigned int* sm_mark;  // SMs the X-stream of this sweep occupies (XStreamArgs::sm_mark), or nullptr
   const int64_t* k_dev;         // sweeps done; this sweep is *k_dev + 1
+  // Single-launch schedule for several chains at once: chain m's S, lam_new,
+  // tau_new, A, Linv, LinvT and readiness words are at m times P, p, 1, P*P,
+  // P*P and sync_words past the pointers above.
+  int nchains;                  // 0 or 1: one chain
+  size_t sync_words;
 };
 // Enqueues the whole factorization; *launches receives the kernel count.
 cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches);
@@ -131,8 +137,9 @@ int chol_launch_count(int P, int arith, int persistent_grid);
 // Readiness words the single-launch FP32-pair schedule needs (zeroed once).
 size_t chol_sync_words(int P);
 // Blocks for the single-launch schedule on the current device (all resident
-// at once, one per SM at most), or 0 where cooperative launch is unavailable.
-int chol_persistent_grid(int device);
+// at once: one per SM for one chain, as many as fit for several), or 0 where
+// cooperative launch is unavailable.
+int chol_persistent_grid(int device, int nchains = 1);
 
 // ---- beta tail, nu/xi, commit ----------------------------------------------
 struct TailArgs {
@@ -164,12 +171,10 @@ struct TailArgs {
   int ring_size, thin;
   int* err;
 };
-cudaError_t tail_enqueue(const TailArgs& a, cudaStream_t s, int* launches);
-constexpr int kTailLaunches = 3;
-// The same in two parts (beta and nu draws; commit), for K chains whose commits
-// must all follow every chain's draws.
-cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s);
-cudaError_t commit_enqueue(const TailArgs& a, cudaStream_t s);
+// The beta tail in two parts: the beta and nu draws, then the commit (every
+// chain's commit must follow every chain's draws).
+cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s, int nchains = 1);
+cudaError_t commit_enqueue(const TailArgs& a, cudaStream_t s, int nchains = 1);
 
 // beta_c = (compute type)(beta * colscale), pads zero.
 cudaError_t beta_c_launch(const double* beta, const float* colscale, int p, int ld, void* beta_c,

@@ -243,6 +243,8 @@ hs::CholArgs chol_args(hs_probit* h, int m) {
   a.persistent_grid = h->chol_grid;
   a.sm_mark = h->sm_mark;
   a.k_dev = h->k_dev;
+  a.nchains = 1;
+  a.sync_words = h->chol_words;
   return a;
 }
 
@@ -317,14 +319,18 @@ cudaError_t enqueue_sweep(hs_probit* h) {
   if ((e = cudaStreamWaitEvent(h->s1, h->ev_fork, 0)) != cudaSuccess) return e;
   {
     ProfSpan sp(h, 2, h->s1);
-    for (int m = 0; m < h->K; ++m)
-      if ((e = hs::shrink_launch(shrink_args(h, m), h->s1)) != cudaSuccess) return e;
+    if ((e = hs::shrink_launch(shrink_args(h, 0), h->s1, h->K)) != cudaSuccess) return e;
   }
   {
     ProfSpan sp(h, 3, h->s1);
-    for (int m = 0; m < h->K; ++m) {
-      int nl = 0;
-      if ((e = hs::chol_enqueue(chol_args(h, m), h->s1, &nl)) != cudaSuccess) return e;
+    if (h->K > 1 && h->chol_grid > 0) {
+      // every chain's factorization in one launch
+      hs::CholArgs ca = chol_args(h, 0);
+      ca.nchains = h->K;
+      if ((e = hs::chol_enqueue(ca, h->s1, nullptr)) != cudaSuccess) return e;
+    } else {
+      for (int m = 0; m < h->K; ++m)
+        if ((e = hs::chol_enqueue(chol_args(h, m), h->s1, nullptr)) != cudaSuccess) return e;
     }
   }
   if ((e = cudaEventRecord(h->ev_join, h->s1)) != cudaSuccess) return e;
@@ -354,10 +360,10 @@ cudaError_t enqueue_sweep(hs_probit* h) {
   if ((e = cudaStreamWaitEvent(h->s0, h->ev_join, 0)) != cudaSuccess) return e;
   {
     ProfSpan sp(h, 4, h->s0);
-    for (int m = 0; m < h->K; ++m)
-      if ((e = hs::tail_draw_enqueue(tail_args(h, m), h->s0)) != cudaSuccess) return e;
-    for (int m = 0; m < h->K; ++m)
-      if ((e = hs::commit_enqueue(tail_args(h, m), h->s0)) != cudaSuccess) return e;
+    if ((e = hs::tail_draw_enqueue(tail_args(h, 0), h->s0, h->K)) != cudaSuccess) return e;
+    // every chain's commit reads the sweep count before the last one advances it
+    if (h->K > 1 && (e = hs::commit_enqueue(tail_args(h, 0), h->s0, h->K - 1)) != cudaSuccess) return e;
+    if ((e = hs::commit_enqueue(tail_args(h, h->K - 1), h->s0, 1)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -590,7 +596,7 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   check(hs::xstream_prepare());
   check(hs::linalg_prepare());
   if (e == cudaSuccess && cfg.chol_arith == HS_CHOL_DF32 && cfg.chol_sched != HS_SCHED_COLUMNS) {
-    h->chol_grid = hs::chol_persistent_grid(h->device);
+    h->chol_grid = hs::chol_persistent_grid(h->device, Kc);
     if (h->chol_grid == 0 && cfg.chol_sched == HS_SCHED_SINGLE) {
       destroy(h);
       fail(HS_EUNSUPPORTED);
@@ -712,7 +718,9 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
     return nullptr;
   }
   // per chain: shrink, the factorization, two draws, commit; then the X-stream and its reduce
-  h->launches = (int64_t)h->K * (1 + hs::chol_launch_count(h->P, h->cfg.chol_arith, h->chol_grid) + 2 + 1) +
+  const int64_t chol_l = hs::chol_launch_count(h->P, h->cfg.chol_arith, h->chol_grid);
+  // shrink, factorization (one launch for every chain when single-launch), two draws, commits
+  h->launches = 1 + ((h->K > 1 && h->chol_grid > 0) ? chol_l : h->K * chol_l) + 2 + (h->K > 1 ? 2 : 1) +
                 (h->K == 1 ? 2 : 3);
   return h;
 }

@@ -49,7 +49,26 @@ __device__ __forceinline__ double equil_scale(double d) {
   return scalbn((double)rsqrtf(m), -e / 2);
 }
 
-__global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a) {
+// Several chains in one launch: blockIdx.y is the chain, whose buffers sit at
+// fixed strides past chain 0's (p per vector, P per scaling, 2 scalars, one
+// block partial per block of x) and whose counters use chain id + blockIdx.y.
+__device__ __forceinline__ ShrinkArgs shrink_chain(ShrinkArgs a, int m) {
+  const size_t p = (size_t)a.p;
+  a.rng.chain += (uint32_t)m;
+  a.beta += m * p;
+  a.lam += m * p;
+  a.nu += m * p;
+  a.scal += 2 * m;
+  a.lam_new += m * p;
+  a.tau_new += m;
+  a.S += (size_t)m * a.P;
+  a.part += (size_t)m * gridDim.x;
+  a.ticket += m;
+  return a;
+}
+
+__global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
+  const ShrinkArgs a = shrink_chain(a0, blockIdx.y);
   __shared__ double s_part[kShrinkThreads / 32];
   __shared__ double s_tau;
   __shared__ int s_last;
@@ -888,47 +907,69 @@ __device__ __forceinline__ void tile_store_cg(df2* M, int P, int ti, int tj, con
   }
 }
 
+// The buffers of one chain of the launch.
+struct ChainView {
+  df2 *A, *Linv, *LinvT;
+  DFCtx cx;
+  PSync ps;
+  __device__ ChainView(const CholArgs& a, int m, int T)
+      : A(reinterpret_cast<df2*>(a.A) + (size_t)m * a.P * a.P),
+        Linv(reinterpret_cast<df2*>(a.Linv) + (size_t)m * a.P * a.P),
+        LinvT(reinterpret_cast<df2*>(a.LinvT) + (size_t)m * a.P * a.P),
+        cx{a.p, a.P, a.G, a.S + (size_t)m * a.P, a.lam_new + (size_t)m * a.p, a.tau_new[m]},
+        ps(a.sync + (size_t)m * a.sync_words, T) {}
+};
+
 __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
   __shared__ DTile sD, sW, sX1, sX2, sLi;
   __shared__ df2 s_piv[NB], s_rs[NB];
   __shared__ int s_step0[kMaxTiles + kBLag + 1];
   __shared__ unsigned long long s_e;
   __shared__ int s_role;  // 0 worker, 1 chain, 2 idle
+  __shared__ int s_chain;
   __shared__ int s_task;
   const int T = a.P / NB;
   const int P = a.P;
-  const PSync ps(a.sync, T);
+  const int nch = a.nchains > 1 ? a.nchains : 1;
+  const PSync ps0(a.sync, T);  // chain 0's words also hold the launch-wide header
   unsigned int smid;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
   if (threadIdx.x == 0) {
-    const unsigned long long e0 = *ps.epoch + 1;  // (kernel-ordered after the previous launch's update)
+    const unsigned long long e0 = *ps0.epoch + 1;  // (kernel-ordered after the previous launch's update)
     s_e = e0;
-    // Role election.  The chain goes to a block on an SM the X-stream left
-    // free (no mark of this sweep), else to the last block to start.
-    const unsigned int stamp = (unsigned int)(*a.k_dev + 1);
-    const bool free_sm = a.sm_mark && smid < (unsigned)kSmMarks && __ldcg(a.sm_mark + smid) != stamp;
-    int role = 0;
-    if (free_sm && atomicCAS(ps.claim, e0 - 1, e0) == e0 - 1) role = 1;
-    const unsigned long long st = atomicAdd(ps.start, 1ull);
-    if (st == gridDim.x - 1) {
-      *ps.start = 0;  // every block has taken its ticket
-      if (role == 0 && atomicCAS(ps.claim, e0 - 1, e0) == e0 - 1) role = 1;
+    int role = 0, chain = 0;
+    if (nch == 1) {
+      // The chain goes to a block on an SM the X-stream left free (no mark
+      // of this sweep), else to the last block to start.
+      const unsigned int stamp = (unsigned int)(*a.k_dev + 1);
+      const bool free_sm = a.sm_mark && smid < (unsigned)kSmMarks && __ldcg(a.sm_mark + smid) != stamp;
+      if (free_sm && atomicCAS(ps0.claim, e0 - 1, e0) == e0 - 1) role = 1;
+      const unsigned long long st = atomicAdd(ps0.start, 1ull);
+      if (st == gridDim.x - 1) {
+        *ps0.start = 0;  // every block has taken its ticket
+        if (role == 0 && atomicCAS(ps0.claim, e0 - 1, e0) == e0 - 1) role = 1;
+      }
+      if (role == 1) st_release_u64(ps0.chain_sm, (e0 << 16) | smid);
+    } else {
+      // several chains: the first nch blocks to start walk the diagonal chains
+      const unsigned long long st = atomicAdd(ps0.start, 1ull);
+      if (st == gridDim.x - 1) *ps0.start = 0;
+      if (st < (unsigned long long)nch) {
+        role = 1;
+        chain = (int)st;
+      }
     }
-    if (role == 1) st_release_u64(ps.chain_sm, (e0 << 16) | smid);
     s_role = role;
+    s_chain = chain;
   }
   __syncthreads();
   const unsigned long long e = s_e;
   const unsigned long long base = e * kEpochStride;
-  df2* A = reinterpret_cast<df2*>(a.A);
-  df2* Linv = reinterpret_cast<df2*>(a.Linv);
-  df2* LinvT = reinterpret_cast<df2*>(a.LinvT);
-  const DFCtx cx{a.p, a.P, a.G, a.S, a.lam_new, *a.tau_new};
-  if (s_role == 0 && gridDim.x >= 16) {
+  if (nch == 1 && s_role == 0 && gridDim.x >= 16) {
     // Blocks that share the chain's SM stay idle, leaving it the whole SM
     // (at most 3 of them: 4 blocks fit on an SM).
-    if (block_wait(ps.chain_sm, e << 16, ps, e, a.err)) {
-      if (threadIdx.x == 0 && (unsigned)(ld_acquire_u64(ps.chain_sm) & 0xFFFFu) == smid) s_role = 2;
+    if (block_wait(ps0.chain_sm, e << 16, ps0, e, a.err)) {
+      if (threadIdx.x == 0 && (unsigned)(ld_acquire_u64(ps0.chain_sm) & 0xFFFFu) == smid) s_role = 2;
     } else if (threadIdx.x == 0) {
       s_role = 2;
     }
@@ -937,6 +978,12 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
 
   if (s_role == 1) {
     // ---------------- the diagonal chain ----------------
+    const ChainView cv(a, s_chain, T);
+    df2* const A = cv.A;
+    df2* const Linv = cv.Linv;
+    df2* const LinvT = cv.LinvT;
+    const DFCtx& cx = cv.cx;
+    const PSync& ps = cv.ps;
     // Entering step k, sD holds D_k = A_kk after all k updates.
     tile_load_gram(sD, cx, 0, 0);
     __syncthreads();
@@ -950,7 +997,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
       if (k >= 1) {
         const unsigned long long* const wp2[2] = {&ps.cntA[(k + 1) * T + k], &ps.cntA[(k + 1) * T + k + 1]};
         const unsigned long long wt2[2] = {base + (unsigned long long)k, base + (unsigned long long)k};
-        if (!block_wait<2>(wp2, wt2, ps, e, a.err)) break;
+        if (!block_wait<2>(wp2, wt2, ps0, e, a.err)) break;
         const TileRef t[2] = {{A, k + 1, k, false, sW}, {A, k + 1, k + 1, false, sD}};
         tiles_load_cg<2>(t, P);
       } else {
@@ -976,18 +1023,26 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
       }
     }
     __syncthreads();
-    const int total = s_step0[nblk];
+    const int total1 = s_step0[nblk];
+    const long long total = (long long)total1 * nch;  // task t: chain t % nch, its list entry t / nch
     int blk = 0;
     unsigned long long grabbed = 0;
-    if (threadIdx.x == 0) grabbed = atomicAdd(ps.next, 1ull);
+    if (threadIdx.x == 0) grabbed = atomicAdd(ps0.next, 1ull);
     for (;;) {
-      if (threadIdx.x == 0) s_task = grabbed >= (unsigned long long)total ? total : (int)grabbed;
+      if (threadIdx.x == 0) s_task = grabbed >= (unsigned long long)total ? -1 : (int)grabbed;
       __syncthreads();
       const int t = s_task;
-      if (t >= total) break;
-      if (threadIdx.x == 0) grabbed = atomicAdd(ps.next, 1ull);  // the following task, early
-      while (t >= s_step0[blk + 1]) ++blk;  // a worker's tasks come in increasing order
-      int u = t - s_step0[blk];
+      if (t < 0) break;
+      if (threadIdx.x == 0) grabbed = atomicAdd(ps0.next, 1ull);  // the following task, early
+      const ChainView cv(a, t % nch, T);
+      df2* const A = cv.A;
+      df2* const Linv = cv.Linv;
+      df2* const LinvT = cv.LinvT;
+      const DFCtx& cx = cv.cx;
+      const PSync& ps = cv.ps;
+      const int tl = t / nch;
+      while (tl >= s_step0[blk + 1]) ++blk;  // a worker's tasks come in increasing order
+      int u = tl - s_step0[blk];
       const bool a_task = u < nAt(T, blk);
       const int k = a_task ? blk : blk - kBLag;
       if (!a_task) u -= nAt(T, blk);
@@ -998,7 +1053,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         const int i = k + 2 + u;
         const unsigned long long* const wp2[2] = {&ps.flagLi[k], &ps.cntA[i * T + k]};
         const unsigned long long wt2[2] = {e, k >= 1 ? done_k : 0ull};
-        if (!block_wait<2>(wp2, wt2, ps, e, a.err)) break;
+        if (!block_wait<2>(wp2, wt2, ps0, e, a.err)) break;
         if (k == 0) {
           tile_load_gram(sW, cx, i, 0);
           const TileRef t1[1] = {{LinvT, k, k, false, sX1}};
@@ -1018,7 +1073,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         const int j = u;
         const unsigned long long* const wp2[2] = {&ps.flagLi[k], &ps.cntB[k * T + j]};
         const unsigned long long wt2[2] = {e, base + (unsigned long long)(k - j)};
-        if (!block_wait<2>(wp2, wt2, ps, e, a.err)) break;
+        if (!block_wait<2>(wp2, wt2, ps0, e, a.err)) break;
         const TileRef t2[2] = {{Linv, k, k, false, sX1}, {Linv, k, j, false, sW}};
         tiles_load_cg<2>(t2, P);
         __syncthreads();
@@ -1042,7 +1097,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         const int j = k + 1 + q, i = j + idx;
         const unsigned long long* const wp3[3] = {&ps.flagL[i * T + k], &ps.flagL[j * T + k], &ps.cntA[i * T + j]};
         const unsigned long long wt3[3] = {e, e, k >= 1 ? done_k : 0ull};
-        if (!block_wait<3>(wp3, wt3, ps, e, a.err)) break;
+        if (!block_wait<3>(wp3, wt3, ps0, e, a.err)) break;
         if (k == 0) {
           tile_load_gram(sW, cx, i, j);
           const TileRef t2[2] = {{A, i, k, false, sX1}, {A, j, k, true, sX2}};
@@ -1064,7 +1119,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         const unsigned long long* const wp3[3] = {&ps.flagL[i * T + k], j < k ? &ps.flagX[k * T + j] : &ps.flagLi[k],
                                                    &ps.cntB[i * T + j]};
         const unsigned long long wt3[3] = {e, e, k > j ? base + (unsigned long long)(k - j) : 0ull};
-        if (!block_wait<3>(wp3, wt3, ps, e, a.err)) break;
+        if (!block_wait<3>(wp3, wt3, ps0, e, a.err)) break;
         if (k == j) {
           tile_zero(sW);
           const TileRef t2[2] = {{A, i, k, false, sX1}, {Linv, k, j, false, sX2}};
@@ -1084,10 +1139,10 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    if (atomicAdd(ps.ticket, 1ull) == (unsigned long long)(gridDim.x - 1)) {
-      *ps.ticket = 0;
-      *ps.next = 0;
-      *ps.epoch = e;
+    if (atomicAdd(ps0.ticket, 1ull) == (unsigned long long)(gridDim.x - 1)) {
+      *ps0.ticket = 0;
+      *ps0.next = 0;
+      *ps0.epoch = e;
     }
   }
 }
@@ -1098,9 +1153,37 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
 __device__ __forceinline__ double elem(const double* M, size_t idx) { return M[idx]; }
 __device__ __forceinline__ double elem(const df2* M, size_t idx) { return df_value(M[idx]); }
 
+// Several chains in one launch (blockIdx.y = chain), as for the shrink kernel;
+// k_dev_rw advances by one slot per chain.
+__device__ __forceinline__ TailArgs tail_chain(TailArgs a, int m) {
+  const size_t p = (size_t)a.p, P = (size_t)a.P, P2 = P * P;
+  const size_t eb = a.df32 ? sizeof(df2) : sizeof(double);
+  a.rng.chain += (uint32_t)m;
+  a.xtz += m * p;
+  a.S += m * P;
+  a.Linv = static_cast<const unsigned char*>(a.Linv) + m * P2 * eb;
+  a.LinvT = static_cast<const unsigned char*>(a.LinvT) + m * P2 * eb;
+  a.v += m * P;
+  a.beta_new += m * p;
+  a.nu_new += m * p;
+  a.lam_new += m * p;
+  a.tau_new += m;
+  a.beta += m * p;
+  a.lam += m * p;
+  a.nu += m * p;
+  a.scal += 2 * m;
+  a.k_dev_rw += m;
+  a.beta_c = static_cast<unsigned char*>(a.beta_c) + (size_t)m * a.ld * (a.beta_c_is_double ? 8 : 4);
+  a.ring_beta += m * (size_t)a.ring_size * p;
+  a.ring_lam += m * (size_t)a.ring_size * p;
+  a.ring_tau += m * (size_t)a.ring_size;
+  return a;
+}
+
 // v_i = sum_{j <= i} Linv[i][j] S_j xtz_j + s_i   (one warp per row)
 template <typename E>
-__global__ void __launch_bounds__(256) tail_w_kernel(TailArgs a) {
+__global__ void __launch_bounds__(256) tail_w_kernel(TailArgs a0) {
+  const TailArgs a = tail_chain(a0, blockIdx.y);
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= a.p) return;
@@ -1121,7 +1204,8 @@ __global__ void __launch_bounds__(256) tail_w_kernel(TailArgs a) {
 
 // beta_j = S_j sum_{i >= j} LinvT[j][i] v_i; nu_j^{-1} (one warp per j)
 template <typename E>
-__global__ void __launch_bounds__(256) tail_beta_kernel(TailArgs a) {
+__global__ void __launch_bounds__(256) tail_beta_kernel(TailArgs a0) {
+  const TailArgs a = tail_chain(a0, blockIdx.y);
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= a.p) return;
@@ -1146,7 +1230,8 @@ __global__ void __launch_bounds__(256) tail_beta_kernel(TailArgs a) {
 }
 
 // Commit (single CTA): xi^{-1}, state, compute-type beta, ring, k.
-__global__ void __launch_bounds__(1024) commit_kernel(TailArgs a) {
+__global__ void __launch_bounds__(1024) commit_kernel(TailArgs a0) {
+  const TailArgs a = tail_chain(a0, blockIdx.y);
   __shared__ int s_ok;
   __shared__ int64_t s_sweep;
   if (threadIdx.x == 0) {
@@ -1248,7 +1333,7 @@ cudaError_t linalg_prepare() {
                               kStepPadBytes);
 }
 
-int chol_persistent_grid(int device) {
+int chol_persistent_grid(int device, int nchains) {
   int coop = 0, sms = 0, per_sm = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
@@ -1257,11 +1342,15 @@ int chol_persistent_grid(int device) {
     return 0;
   }
   if (!coop || sms < 2 || per_sm < 1) return 0;
-  return sms;
+  // one chain: one block per SM (the X-stream shares the SMs); several: every
+  // block that fits, and at least one worker besides the chain blocks
+  if (nchains <= 1) return sms;
+  const int g = sms * per_sm;
+  return g > nchains ? g : 0;
 }
 
-cudaError_t shrink_launch(const ShrinkArgs& a, cudaStream_t s) {
-  shrink_kernel<<<(a.p + kShrinkThreads - 1) / kShrinkThreads, kShrinkThreads, 0, s>>>(a);
+cudaError_t shrink_launch(const ShrinkArgs& a, cudaStream_t s, int nchains) {
+  shrink_kernel<<<dim3((a.p + kShrinkThreads - 1) / kShrinkThreads, nchains), kShrinkThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1324,34 +1413,20 @@ cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches) {
   return cudaGetLastError();
 }
 
-cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s) {
-  const int nb = (a.p * 32 + 255) / 256;
+cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s, int nchains) {
+  const dim3 grid((a.p * 32 + 255) / 256, nchains);
   if (a.df32) {
-    tail_w_kernel<df2><<<nb, 256, 0, s>>>(a);
-    tail_beta_kernel<df2><<<nb, 256, 0, s>>>(a);
+    tail_w_kernel<df2><<<grid, 256, 0, s>>>(a);
+    tail_beta_kernel<df2><<<grid, 256, 0, s>>>(a);
   } else {
-    tail_w_kernel<double><<<nb, 256, 0, s>>>(a);
-    tail_beta_kernel<double><<<nb, 256, 0, s>>>(a);
+    tail_w_kernel<double><<<grid, 256, 0, s>>>(a);
+    tail_beta_kernel<double><<<grid, 256, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
 
-cudaError_t commit_enqueue(const TailArgs& a, cudaStream_t s) {
-  commit_kernel<<<1, 1024, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t tail_enqueue(const TailArgs& a, cudaStream_t s, int* launches) {
-  const int nb = (a.p * 32 + 255) / 256;
-  if (a.df32) {
-    tail_w_kernel<df2><<<nb, 256, 0, s>>>(a);
-    tail_beta_kernel<df2><<<nb, 256, 0, s>>>(a);
-  } else {
-    tail_w_kernel<double><<<nb, 256, 0, s>>>(a);
-    tail_beta_kernel<double><<<nb, 256, 0, s>>>(a);
-  }
-  commit_kernel<<<1, 1024, 0, s>>>(a);
-  if (launches) *launches = 3;
+cudaError_t commit_enqueue(const TailArgs& a, cudaStream_t s, int nchains) {
+  commit_kernel<<<dim3(1, nchains), 1024, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -20,9 +20,10 @@
 // end it writes the partial (p x 32, FP32) and a second kernel sums the
 // partials in a fixed order in FP64.
 //
-// Warp roles (256 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues
-// tcgen05.mma, warp 2 owns the TMEM allocation, warps 4..7 (one per TMEM lane
-// quadrant, thread = tile row) read eta, draw z and write Z^T.  Every wait is
+// Warp roles (384 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues
+// tcgen05.mma, warp 2 owns the TMEM allocation, warps 4..11 read eta, draw z
+// and write Z^T: warp w serves TMEM lane quadrant w % 4 (thread = tile row)
+// and chains 16 (w - 4) / 4 .. +15.  Every wait is
 // bounded (2 s); a wait that runs out sets the timeout bit and all roles wind
 // down through a shared abort flag.
 #include <cuda.h>
@@ -44,7 +45,7 @@ constexpr int kXStages = 4;      // ring stages
 constexpr uint32_t kStageBytes = kTR * kCF * 2;       // 16 KB
 constexpr uint32_t kBChunkBytes = 2 * kKc * kCF * 2;  // 8 KB: 64 rows (hi chains, lo chains) x 128 B
 constexpr uint32_t kZBlock = kKc * 128;               // 4 KB: 32 chains x 64 rows x 2 B
-constexpr int kThreads = 256;
+constexpr int kThreads = 384;  // 4 role warps + 8 epilogue warps
 
 // ---- tcgen05 helpers (shared-memory descriptors, 128-byte swizzle) ---------
 // Descriptor: start address >> 4 in bits 0-13, leading byte offset >> 4 in
@@ -88,6 +89,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
+}
+// 32 lanes x 16 consecutive columns of TMEM into 16 registers per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+// FP32 uniform pair from two Philox words: u = (2m + 1) 2^-53 and 1 - u with
+// m = (hi << 20) | (lo >> 12), each converted once from its exact integer.
+__device__ __forceinline__ void unit_pair_f(uint32_t hi, uint32_t lo, float& u, float& uc) {
+  const unsigned long long m = ((unsigned long long)hi << 20) | (unsigned long long)(lo >> 12);
+  const unsigned long long mc = ((1ull << 52) - 1ull) - m;
+  u = __ull2float_rn(2ull * m + 1ull) * 0x1p-53f;
+  uc = __ull2float_rn(2ull * mc + 1ull) * 0x1p-53f;
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -158,8 +175,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     mbar_init(&sh.bfull, 1);
     mbar_init(&sh.eta_full, 1);
-    mbar_init(&sh.eta_empty, 128);
-    mbar_init(&sh.z_ready, 128);
+    mbar_init(&sh.eta_empty, 256);
+    mbar_init(&sh.z_ready, 256);
     mbar_init(&sh.zt_empty, 1);
     mbar_init(&sh.acc_done, 1);
     sh.abort = 0;
@@ -252,17 +269,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     mma_commit(&sh.acc_done);
   } else if (warp >= 4) {
     // ---------------- epilogue: z draws and Z^T ----------------
-    const int er = tid - 128;  // row within the tile = TMEM lane
-    const uint32_t lane_off = (uint32_t)(32 * (warp - 4)) << 16;
-    const Rng rng{a.rng.k0, a.rng.k1, a.rng.chain, a.rng.problem};
+    const int quad = warp & 3, half = (warp - 4) >> 2;  // TMEM lane quadrant; chains 16 half .. +15
+    const int er = 32 * quad + lane;                      // row within the tile = TMEM lane
+    const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
+    const int m0 = 16 * half;
     const uint32_t sweep = (uint32_t)(*a.k_dev + 1);
     int it = 0;
     for (int64_t t = t0; t < t1; ++t, ++it) {
       if (!xk_wait(&sh.eta_full, it & 1, &sh, a.err)) break;
       tc_fence_after();
-      uint32_t hi[32], lo[32];
-      tmem_ld32(tm_eta + lane_off, hi);
-      tmem_ld32(tm_eta + lane_off + 32, lo);
+      uint32_t hi[16], lo[16];
+      tmem_ld16(tm_eta + lane_off + m0, hi);
+      tmem_ld16(tm_eta + lane_off + 32 + m0, lo);
       tmem_ld_wait();
       tc_fence_before();
       mbar_arrive(&sh.eta_empty);
@@ -272,20 +290,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       // Z^T (both parts) for pass 2, once pass 2 of the previous tile is done with it
       if (!xk_wait(&sh.zt_empty, (it & 1) ^ 1, &sh, a.err)) break;
       const int katom = er >> 6, kr = er & 63;
-#pragma unroll 4
-      for (int m = 0; m < kKc; ++m) {
-        const float eta = __uint_as_float(hi[m]) + __uint_as_float(lo[m]);
+#pragma unroll
+      for (int mm = 0; mm < 16; ++mm) {
+        const int m = m0 + mm;
+        const float eta = __uint_as_float(hi[mm]) + __uint_as_float(lo[mm]);
         const bool on = active && m < a.K;
-        double u = 0.5, uc = 0.5;
+        float u = 0.5f, uc = 0.5f;
         if (on) {
-          const Rng r{rng.k0, rng.k1, rng.chain + (uint32_t)m, rng.problem};
+          const Rng r{a.rng.k0, a.rng.k1, a.rng.chain + (uint32_t)m, a.rng.problem};
           const uint4 wd = r.words((uint32_t)i, sweep, kPurZ);
-          unit_pair(wd.x, wd.y, u, uc);
+          unit_pair_f(wd.x, wd.y, u, uc);
         }
         const float ms = on ? (yi ? eta : -eta) : 0.0f;
-        float zp = tn_main<float>(ms, (float)u, (float)uc);
+        float zp = tn_main<float>(ms, u, uc);
         const bool tail = on && ms < TnMath<float>::kTail;
-        if (tail) zp = tn_tail<float>(ms, (float)u, (float)uc);
+        if (tail) zp = tn_tail<float>(ms, u, uc);
         zp = zp > TnMath<float>::tiny() ? zp : TnMath<float>::tiny();
         float zz = on ? (yi ? zp : -zp) : 0.0f;
         if (on && !isfinite(zz)) {
@@ -302,10 +321,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
       mbar_arrive(&sh.z_ready);
     }
-    // the CTA's X^T Z partial: row = feature 128 g + er, 32 chains
+    // the CTA's X^T Z partial: row = feature 128 g + er, 32 chains; groups split between the halves
     if (xk_wait(&sh.acc_done, 0, &sh, a.err)) {
       tc_fence_after();
-      for (int g = 0; g < ngrp; ++g) {
+      for (int g = half; g < ngrp; g += 2) {
         uint32_t r[32];
         tmem_ld32(tm_xtz + 32 * g + lane_off, r);
         tmem_ld_wait();
