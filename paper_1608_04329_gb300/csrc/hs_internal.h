@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <vector>
 #include <stdint.h>
 
 namespace hs {
@@ -130,6 +132,7 @@ struct CholArgs {
   // P*P and sync_words past the pointers above.
   int nchains;                  // 0 or 1: one chain
   size_t sync_words;
+  const int* order;             // worker task list (chol_task_order), or nullptr: canonical order
 };
 // Enqueues the whole factorization; *launches receives the kernel count.
 cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches);
@@ -140,6 +143,9 @@ size_t chol_sync_words(int P);
 // at once: one per SM for one chain, as many as fit for several), or 0 where
 // cooperative launch is unavailable.
 int chol_persistent_grid(int device, int nchains = 1);
+// Worker task list of the single-launch factorization for T tiles and about
+// `workers` concurrent task slots (a topological order; see linalg.cu).
+std::vector<int> chol_task_order(int T, int workers);
 
 // ---- beta tail, nu/xi, commit ----------------------------------------------
 struct TailArgs {

@@ -79,6 +79,7 @@ struct hs_probit {
   unsigned int* sm_mark = nullptr;          // SM occupancy marks of the X-stream (single launch only)
   int chol_grid = 0;                        // its blocks; 0: one launch per block column
   size_t chol_words = 0;                    // scheduling words per chain
+  int* chol_order = nullptr;                // worker task list of the single-launch factorization
   // K chains sharing X: every per-chain buffer holds K slices (chain m at offset m * size)
   int K = 1;
   int64_t* k_scratch = nullptr;             // K: commits of chains 0..K-2 record the sweep here
@@ -245,6 +246,7 @@ hs::CholArgs chol_args(hs_probit* h, int m) {
   a.k_dev = h->k_dev;
   a.nchains = 1;
   a.sync_words = h->chol_words;
+  a.order = h->chol_order;
   return a;
 }
 
@@ -645,9 +647,14 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   check(h->alloc(&h->v, K * (size_t)h->P * sizeof(double)));
   check(h->alloc(&h->shrink_part, K * shrink_blocks(h) * sizeof(double)));
   check(h->alloc(&h->shrink_ticket, K * sizeof(unsigned int)));
+  std::vector<int> order;
   if (h->chol_grid > 0) {
     check(h->alloc(&h->chol_sync, K * h->chol_words * sizeof(unsigned long long)));
     check(h->alloc(&h->sm_mark, hs::kSmMarks * sizeof(unsigned int)));
+    // two task slots per worker block, shared by the chains
+    const int slots = 2 * (h->chol_grid - h->K) / h->K;
+    order = hs::chol_task_order(h->T, slots > 1 ? slots : 1);
+    if (!order.empty()) check(h->alloc(&h->chol_order, order.size() * sizeof(int)));
   }
   if (h->K == 1) {
     check(h->alloc(&h->partials, (size_t)h->grid * h->ld * hs::partial_elem_bytes(h->x_dtype)));
@@ -680,6 +687,8 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   check(cudaMemsetAsync(h->err, 0, sizeof(int), h->s0));
   check(cudaMemsetAsync(h->hook_err, 0, sizeof(int), h->s0));
   check(cudaMemsetAsync(h->shrink_ticket, 0, K * sizeof(unsigned int), h->s0));
+  if (h->chol_order && e == cudaSuccess)
+    check(cudaMemcpy(h->chol_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
   if (h->chol_sync) {
     check(cudaMemsetAsync(h->chol_sync, 0, K * h->chol_words * sizeof(unsigned long long), h->s0));
     check(cudaMemsetAsync(h->sm_mark, 0, hs::kSmMarks * sizeof(unsigned int), h->s0));

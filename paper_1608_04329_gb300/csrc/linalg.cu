@@ -19,6 +19,10 @@
 //           explicit inverse factor; nu_j^{-1} ~ Exp(1 + lambda_j^{-2}) and
 //           xi^{-1} ~ Exp(1 + tau^{-2}) (Eq. 12, third and sixth lines); and
 //           the commit of the new state, skipped when the error word is set.
+#include <algorithm>
+#include <queue>
+#include <vector>
+
 #include "df32.cuh"
 #include "hs_common.cuh"
 #include "hs_internal.h"
@@ -762,16 +766,7 @@ __host__ __device__ __forceinline__ int nUA(int T, int k) {
 }
 __host__ __device__ __forceinline__ int nUB(int T, int k) { return (T - k - 1) * (k + 1); }
 __host__ __device__ __forceinline__ int nTasks(int T, int k) { return nC(T, k) + k + nUA(T, k) + nUB(T, k); }
-// Worker tasks split in two families: A tasks (C, UA) build L and feed the
-// diagonal chain; B tasks (X, UB) build L^{-1} and are needed only after the
-// factorization.  The list runs in blocks s = 0..T-1+kBLag: block s holds the
-// A tasks of step s, then the B tasks of step s - kBLag, so inverse-factor
-// work fills the gaps behind the factorization instead of delaying it.  Every
-// task still comes after the tasks it reads.
-constexpr int kBLag = 4;
-__host__ __device__ __forceinline__ int nAt(int T, int k) { return k >= 0 && k < T ? nC(T, k) + nUA(T, k) : 0; }
-__host__ __device__ __forceinline__ int nBt(int T, int k) { return k >= 0 && k < T ? k + nUB(T, k) : 0; }
-__host__ __device__ __forceinline__ int nBlock(int T, int s) { return nAt(T, s) + nBt(T, s - kBLag); }
+
 __host__ __device__ inline int total_tasks(int T) {
   int n = 0;
   for (int k = 0; k < T; ++k) n += nTasks(T, k);
@@ -907,6 +902,142 @@ __device__ __forceinline__ void tile_store_cg(df2* M, int P, int ti, int tj, con
   }
 }
 
+// ---- tile work of a 128-thread group ----------------------------------------
+// A worker block runs two independent tile tasks at a time, one per group of
+// four warps (warps 0-3 and 4-7), each with its own tiles and named barrier.
+struct Grp {
+  int t;    // thread index within the group, 0..127
+  int bar;  // named barrier of the group (1 or 2)
+  __device__ __forceinline__ void sync() const { named_bar_sync(bar, 128); }
+  __device__ __forceinline__ bool sync_and(int pred) const {
+    int out;
+    asm volatile(
+        "{\n\t.reg .pred q, r;\n\tsetp.ne.s32 q, %1, 0;\n\tbar.red.and.pred r, %2, 128, q;\n\tselp.s32 %0, 1, 0, r;\n\t}"
+        : "=r"(out)
+        : "r"(pred), "r"(bar)
+        : "memory");
+    return out != 0;
+  }
+};
+
+template <int NT>
+__device__ __forceinline__ void gload_cg(const Grp& g, const TileRef (&t)[NT], int P) {
+  float4 v[NT][4];
+#pragma unroll
+  for (int n = 0; n < NT; ++n)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int e = g.t + h * 128, r = e >> 4, c = (e & 15) * 2;
+      v[n][h] = __ldcg(reinterpret_cast<const float4*>(t[n].M + (size_t)(t[n].ti * NB + r) * P + t[n].tj * NB + c));
+    }
+#pragma unroll
+  for (int n = 0; n < NT; ++n)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int e = g.t + h * 128, r = e >> 4, c = (e & 15) * 2;
+      const df2 x0{v[n][h].x, v[n][h].y}, x1{v[n][h].z, v[n][h].w};
+      if (t[n].transposed) {
+        t[n].dst[c][r] = x0;
+        t[n].dst[c + 1][r] = x1;
+      } else {
+        t[n].dst[r][c] = x0;
+        t[n].dst[r][c + 1] = x1;
+      }
+    }
+}
+__device__ __forceinline__ void gload_gram(const Grp& g, df2 (*T)[NB + 1], const DFCtx& cx, int ti, int tj) {
+  for (int e = g.t; e < NB * NB; e += 128) {
+    const int r = e >> 5, c = e & 31;
+    const int gr = ti * NB + r, gc = tj * NB + c;
+    T[r][c] = (gc <= gr) ? scaled_gram(cx, gr, gc) : scaled_gram(cx, gc, gr);
+  }
+}
+__device__ __forceinline__ void gzero(const Grp& g, df2 (*T)[NB + 1]) {
+  for (int e = g.t; e < NB * NB; e += 128) T[e >> 5][e & 31] = df2{0.0f, 0.0f};
+}
+__device__ __forceinline__ void gstore_cg(const Grp& g, df2* M, int P, int ti, int tj, const df2 (*T)[NB + 1],
+                                          bool transposed) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const int e = g.t + h * 128, r = e >> 4, c = (e & 15) * 2;
+    const df2 x0 = transposed ? T[c][r] : T[r][c];
+    const df2 x1 = transposed ? T[c + 1][r] : T[r][c + 1];
+    __stcg(reinterpret_cast<float4*>(M + (size_t)(ti * NB + r) * P + tj * NB + c), make_float4(x0.hi, x0.lo, x1.hi, x1.lo));
+  }
+}
+// C = As Bt (set) or C -= As Bt (sub), Bt[q][c]; thread: rows ty + 8i, columns tx, tx + 16.
+template <bool kSub>
+__device__ __forceinline__ void gmma(const Grp& g, df2 (*C)[NB + 1], const df2 (*As)[NB + 1], const df2 (*Bt)[NB + 1]) {
+  const int tx = g.t & 15, ty = g.t >> 4;
+  float h[4][2], l[4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) h[i][j] = l[i][j] = 0.0f;
+#pragma unroll 2
+  for (int q = 0; q < NB; ++q) {
+    df2 av[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) av[i] = As[ty + 8 * i][q];
+    const df2 b0 = Bt[q][tx], b1 = Bt[q][tx + 16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      df_fma(h[i][0], l[i][0], av[i], b0);
+      df_fma(h[i][1], l[i][1], av[i], b1);
+    }
+  }
+  g.sync();  // all reads of As/Bt/C done before C is written (C may alias)
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const df2 v = df_renorm(h[i][j], l[i][j]);
+      df2& dst = C[ty + 8 * i][tx + 16 * j];
+      dst = kSub ? df_sub(dst, v) : v;
+    }
+  g.sync();
+}
+// Thread 0 of the group waits for every *p[n] >= target[n] (one relaxed read of
+// all, then an acquire fence); bounded as block_wait.
+template <int N>
+__device__ bool gwait(const Grp& g, const unsigned long long* const (&p)[N], const unsigned long long (&target)[N],
+                      const PSync& ps, unsigned long long e, int* err) {
+  int ok = 1;
+  if (g.t == 0) {
+    unsigned long long v[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) v[n] = ld_relaxed_u64(p[n]);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      if (ok && v[n] < target[n]) {
+        const uint64_t t0 = global_ns();
+        while (ld_relaxed_u64(p[n]) < target[n]) {
+          if (ld_relaxed_u64(ps.abort) >= e) {
+            ok = 0;
+            break;
+          }
+          if (global_ns() - t0 > 2000000000ull) {
+            set_error(err, kErrTimeout);
+            st_release_u64(ps.abort, e);
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  }
+  return g.sync_and(ok);
+}
+__device__ __forceinline__ void gpublish(const Grp& g, unsigned long long* p, unsigned long long v) {
+  g.sync();
+  if (g.t == 0) {
+    __threadfence();
+    st_release_u64(p, v);
+  }
+}
+
 // The buffers of one chain of the launch.
 struct ChainView {
   df2 *A, *Linv, *LinvT;
@@ -920,14 +1051,23 @@ struct ChainView {
         ps(a.sync + (size_t)m * a.sync_words, T) {}
 };
 
+constexpr int kPersistTiles = 6;  // chain: 5 tiles; workers: 3 per group
+constexpr size_t kPersistSmem = kPersistTiles * sizeof(DTile);
+
 __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
-  __shared__ DTile sD, sW, sX1, sX2, sLi;
+  extern __shared__ __align__(16) unsigned char dyn_tiles[];
+  DTile* const tiles = reinterpret_cast<DTile*>(dyn_tiles);
+  DTile& sD = tiles[0];
+  DTile& sW = tiles[1];
+  DTile& sX1 = tiles[2];
+  DTile& sX2 = tiles[3];
+  DTile& sLi = tiles[4];
   __shared__ df2 s_piv[NB], s_rs[NB];
-  __shared__ int s_step0[kMaxTiles + kBLag + 1];
+  __shared__ int s_step0[kMaxTiles + 1];
   __shared__ unsigned long long s_e;
   __shared__ int s_role;  // 0 worker, 1 chain, 2 idle
   __shared__ int s_chain;
-  __shared__ int s_task;
+  __shared__ int s_task[2];
   const int T = a.P / NB;
   const int P = a.P;
   const int nch = a.nchains > 1 ? a.nchains : 1;
@@ -1014,26 +1154,29 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
     }
   } else if (s_role == 0) {
     // ---------------- workers: tasks in list order from a shared counter ----------------
-    const int nblk = T + kBLag;
     if (threadIdx.x == 0) {
       int acc = 0;
-      for (int b = 0; b <= nblk; ++b) {
-        s_step0[b] = acc;
-        if (b < nblk) acc += nBlock(T, b);
+      for (int kk = 0; kk <= T; ++kk) {
+        s_step0[kk] = acc;
+        if (kk < T) acc += nTasks(T, kk);
       }
     }
     __syncthreads();
-    const int total1 = s_step0[nblk];
+    const int total1 = s_step0[T];
     const long long total = (long long)total1 * nch;  // task t: chain t % nch, its list entry t / nch
-    int blk = 0;
+    const int gi = threadIdx.x >> 7;                  // two groups of four warps, one task each
+    const Grp g{(int)(threadIdx.x & 127), 1 + gi};
+    DTile& gW = tiles[3 * gi];
+    DTile& gX1 = tiles[3 * gi + 1];
+    DTile& gX2 = tiles[3 * gi + 2];
     unsigned long long grabbed = 0;
-    if (threadIdx.x == 0) grabbed = atomicAdd(ps0.next, 1ull);
+    if (g.t == 0) grabbed = atomicAdd(ps0.next, 1ull);
     for (;;) {
-      if (threadIdx.x == 0) s_task = grabbed >= (unsigned long long)total ? -1 : (int)grabbed;
-      __syncthreads();
-      const int t = s_task;
+      if (g.t == 0) s_task[gi] = grabbed >= (unsigned long long)total ? -1 : (int)grabbed;
+      g.sync();
+      const int t = s_task[gi];
       if (t < 0) break;
-      if (threadIdx.x == 0) grabbed = atomicAdd(ps0.next, 1ull);  // the following task, early
+      if (g.t == 0) grabbed = atomicAdd(ps0.next, 1ull);  // the following task, early
       const ChainView cv(a, t % nch, T);
       df2* const A = cv.A;
       df2* const Linv = cv.Linv;
@@ -1041,50 +1184,54 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
       const DFCtx& cx = cv.cx;
       const PSync& ps = cv.ps;
       const int tl = t / nch;
-      while (tl >= s_step0[blk + 1]) ++blk;  // a worker's tasks come in increasing order
-      int u = tl - s_step0[blk];
-      const bool a_task = u < nAt(T, blk);
-      const int k = a_task ? blk : blk - kBLag;
-      if (!a_task) u -= nAt(T, blk);
+      const int cid = a.order ? __ldg(a.order + tl) : tl;  // canonical id of the list entry
+      int lo = 0, hi = T - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_step0[mid] <= cid) lo = mid; else hi = mid - 1;
+      }
+      const int k = lo;
+      int u = cid - s_step0[k];
       const unsigned long long done_k = base + (unsigned long long)k;  // A tile after updates 0..k-1
       const int c = nC(T, k), ua = nUA(T, k);
-      if (a_task && u < c) {
+      if (u < c) {
         // C(i,k): L_ik = A_ik L_kk^{-T}, i = k + 2 + u
         const int i = k + 2 + u;
         const unsigned long long* const wp2[2] = {&ps.flagLi[k], &ps.cntA[i * T + k]};
         const unsigned long long wt2[2] = {e, k >= 1 ? done_k : 0ull};
-        if (!block_wait<2>(wp2, wt2, ps0, e, a.err)) break;
+        if (!gwait<2>(g, wp2, wt2, ps0, e, a.err)) break;
         if (k == 0) {
-          tile_load_gram(sW, cx, i, 0);
-          const TileRef t1[1] = {{LinvT, k, k, false, sX1}};
-          tiles_load_cg<1>(t1, P);
+          gload_gram(g, gW, cx, i, 0);
+          const TileRef t1[1] = {{LinvT, k, k, false, gX1}};
+          gload_cg<1>(g, t1, P);
         } else {
-          const TileRef t2[2] = {{A, i, k, false, sW}, {LinvT, k, k, false, sX1}};  // sX1[q][c] = (L_kk^{-1})[c][q]
-          tiles_load_cg<2>(t2, P);
+          const TileRef t2[2] = {{A, i, k, false, gW}, {LinvT, k, k, false, gX1}};  // gX1[q][c] = (L_kk^{-1})[c][q]
+          gload_cg<2>(g, t2, P);
         }
-        __syncthreads();
-        tile_mma<false>(sX2, sW, sX1);
-        tile_store_cg(A, P, i, k, sX2, false);
-        block_publish(&ps.flagL[i * T + k], e);
+        g.sync();
+        gmma<false>(g, gX2, gW, gX1);
+        gstore_cg(g, A, P, i, k, gX2, false);
+        gpublish(g, &ps.flagL[i * T + k], e);
         continue;
       }
-      if (!a_task && u < k) {
+      u -= c;
+      if (u < k) {
         // X(k,j): X_kj = L_kk^{-1} B_kj, j = u; B_kj after its k - j updates
         const int j = u;
         const unsigned long long* const wp2[2] = {&ps.flagLi[k], &ps.cntB[k * T + j]};
         const unsigned long long wt2[2] = {e, base + (unsigned long long)(k - j)};
-        if (!block_wait<2>(wp2, wt2, ps0, e, a.err)) break;
-        const TileRef t2[2] = {{Linv, k, k, false, sX1}, {Linv, k, j, false, sW}};
-        tiles_load_cg<2>(t2, P);
-        __syncthreads();
-        tile_mma<false>(sX2, sX1, sW);
-        tile_store_cg(Linv, P, k, j, sX2, false);
-        tile_store_cg(LinvT, P, j, k, sX2, true);
-        block_publish(&ps.flagX[k * T + j], e);
+        if (!gwait<2>(g, wp2, wt2, ps0, e, a.err)) break;
+        const TileRef t2[2] = {{Linv, k, k, false, gX1}, {Linv, k, j, false, gW}};
+        gload_cg<2>(g, t2, P);
+        g.sync();
+        gmma<false>(g, gX2, gX1, gW);
+        gstore_cg(g, Linv, P, k, j, gX2, false);
+        gstore_cg(g, LinvT, P, j, k, gX2, true);
+        gpublish(g, &ps.flagX[k * T + j], e);
         continue;
       }
-      if (a_task) {
-        u -= c;
+      u -= k;
+      if (u < ua) {
         // UA(i,j,k): A_ij -= L_ik L_jk^T.  The lower triangle of tile rows/cols
         // k+1..T-1 is listed column by column (column k+1, which feeds the
         // diagonal chain, first), without its first entry (k+1, k+1).
@@ -1097,41 +1244,41 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         const int j = k + 1 + q, i = j + idx;
         const unsigned long long* const wp3[3] = {&ps.flagL[i * T + k], &ps.flagL[j * T + k], &ps.cntA[i * T + j]};
         const unsigned long long wt3[3] = {e, e, k >= 1 ? done_k : 0ull};
-        if (!block_wait<3>(wp3, wt3, ps0, e, a.err)) break;
+        if (!gwait<3>(g, wp3, wt3, ps0, e, a.err)) break;
         if (k == 0) {
-          tile_load_gram(sW, cx, i, j);
-          const TileRef t2[2] = {{A, i, k, false, sX1}, {A, j, k, true, sX2}};
-          tiles_load_cg<2>(t2, P);
+          gload_gram(g, gW, cx, i, j);
+          const TileRef t2[2] = {{A, i, k, false, gX1}, {A, j, k, true, gX2}};
+          gload_cg<2>(g, t2, P);
         } else {
-          const TileRef t3[3] = {{A, i, j, false, sW}, {A, i, k, false, sX1}, {A, j, k, true, sX2}};
-          tiles_load_cg<3>(t3, P);
+          const TileRef t3[3] = {{A, i, j, false, gW}, {A, i, k, false, gX1}, {A, j, k, true, gX2}};
+          gload_cg<3>(g, t3, P);
         }
-        __syncthreads();
-        tile_mma<true>(sW, sX1, sX2);
-        tile_store_cg(A, P, i, j, sW, false);
-        block_publish(&ps.cntA[i * T + j], done_k + 1);
+        g.sync();
+        gmma<true>(g, gW, gX1, gX2);
+        gstore_cg(g, A, P, i, j, gW, false);
+        gpublish(g, &ps.cntA[i * T + j], done_k + 1);
         continue;
       }
-      u -= k;
+      u -= ua;
       {
         // UB(i,j,k): B_ij -= L_ik X_kj (X_kk = L_kk^{-1}; B_ik starts at zero)
         const int i = k + 1 + u / (k + 1), j = u % (k + 1);
         const unsigned long long* const wp3[3] = {&ps.flagL[i * T + k], j < k ? &ps.flagX[k * T + j] : &ps.flagLi[k],
                                                    &ps.cntB[i * T + j]};
         const unsigned long long wt3[3] = {e, e, k > j ? base + (unsigned long long)(k - j) : 0ull};
-        if (!block_wait<3>(wp3, wt3, ps0, e, a.err)) break;
+        if (!gwait<3>(g, wp3, wt3, ps0, e, a.err)) break;
         if (k == j) {
-          tile_zero(sW);
-          const TileRef t2[2] = {{A, i, k, false, sX1}, {Linv, k, j, false, sX2}};
-          tiles_load_cg<2>(t2, P);
+          gzero(g, gW);
+          const TileRef t2[2] = {{A, i, k, false, gX1}, {Linv, k, j, false, gX2}};
+          gload_cg<2>(g, t2, P);
         } else {
-          const TileRef t3[3] = {{Linv, i, j, false, sW}, {A, i, k, false, sX1}, {Linv, k, j, false, sX2}};
-          tiles_load_cg<3>(t3, P);
+          const TileRef t3[3] = {{Linv, i, j, false, gW}, {A, i, k, false, gX1}, {Linv, k, j, false, gX2}};
+          gload_cg<3>(g, t3, P);
         }
-        __syncthreads();
-        tile_mma<true>(sW, sX1, sX2);
-        tile_store_cg(Linv, P, i, j, sW, false);
-        block_publish(&ps.cntB[i * T + j], base + (unsigned long long)(k - j + 1));
+        g.sync();
+        gmma<true>(g, gW, gX1, gX2);
+        gstore_cg(g, Linv, P, i, j, gW, false);
+        gpublish(g, &ps.cntB[i * T + j], base + (unsigned long long)(k - j + 1));
       }
     }
   }
@@ -1329,15 +1476,18 @@ cudaError_t linalg_prepare() {
                                          (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
   }
-  return cudaFuncSetAttribute((const void*)step_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kStepPadBytes);
+  cudaError_t e = cudaFuncSetAttribute((const void*)step_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kStepPadBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute((const void*)chol_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kPersistSmem);
 }
 
 int chol_persistent_grid(int device, int nchains) {
   int coop = 0, sms = 0, per_sm = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_persistent_kernel, 256, 0) != cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_persistent_kernel, 256, kPersistSmem) != cudaSuccess) {
     (void)cudaGetLastError();
     return 0;
   }
@@ -1359,6 +1509,191 @@ size_t chol_sync_words(int P) {
   return kSyncHeader + 4 * T * T + T;
 }
 
+// ---- the worker task list of the single-launch factorization -------------
+// Canonical task ids: step k's tasks are numbered from s0[k] in the order
+// C(i,k) (i = k+2..T-1), X(k,j) (j < k), UA(i,j,k) (lower triangle of tile
+// rows/cols k+1..T-1 column by column without (k+1,k+1)), UB(i,j,k) (row by
+// row).  The list is the start order of a simulated schedule (list
+// scheduling): W workers take the ready task with the longest remaining path
+// (bottom level) whenever they are free, beside one processor that runs the
+// diagonal chain's two nodes per step (L_kk^{-1}; then L_{k+1,k} and the next
+// diagonal update).  The start order is a topological order of the whole graph
+// including the chain, which is what the kernel's wait-free progress argument
+// needs; it is checked here and replaced by the canonical order if the check
+// fails.
+namespace {
+struct HostIds {
+  int T;
+  std::vector<int> s0;
+  explicit HostIds(int T_) : T(T_), s0(T_ + 1, 0) {
+    for (int k = 0; k < T; ++k) s0[k + 1] = s0[k] + nTasks(T, k);
+  }
+  int C(int i, int k) const { return s0[k] + (i - k - 2); }
+  int X(int k, int j) const { return s0[k] + nC(T, k) + j; }
+  int UA(int i, int j, int k) const {
+    const int m = T - k - 1, q = j - k - 1;
+    return s0[k] + nC(T, k) + k + q * m - q * (q - 1) / 2 + (i - j) - 1;
+  }
+  int UB(int i, int j, int k) const { return s0[k] + nC(T, k) + k + nUA(T, k) + (i - k - 1) * (k + 1) + j; }
+  // kind 0 C, 1 X, 2 UA, 3 UB
+  void decode(int t, int& kind, int& i, int& j, int& k) const {
+    int lo = 0, hi = T - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s0[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    k = lo;
+    int u = t - s0[k];
+    const int c = nC(T, k), ua = nUA(T, k);
+    if (u < c) { kind = 0; i = k + 2 + u; j = k; return; }
+    u -= c;
+    if (u < k) { kind = 1; i = k; j = u; return; }
+    u -= k;
+    if (u < ua) {
+      const int m = T - k - 1;
+      int idx = u + 1, q = 0;
+      while (idx >= m - q) { idx -= m - q; ++q; }
+      kind = 2; j = k + 1 + q; i = j + idx; return;
+    }
+    u -= ua;
+    kind = 3; i = k + 1 + u / (k + 1); j = u % (k + 1);
+  }
+};
+}  // namespace
+
+std::vector<int> chol_task_order(int T, int workers) {
+  const HostIds id(T);
+  const int n = id.s0[T];
+  std::vector<int> canonical(n);
+  for (int t = 0; t < n; ++t) canonical[t] = t;
+  if (n == 0 || workers < 1) return canonical;
+  const int N = n + 2 * T;  // chain nodes: n + 2k (L_kk^{-1}), n + 2k + 1 (L_{k+1,k}, next diagonal)
+  auto Li = [&](int k) { return n + 2 * k; };
+  auto Ln = [&](int k) { return n + 2 * k + 1; };
+  std::vector<std::vector<int>> deps(N);
+  for (int t = 0; t < n; ++t) {
+    int kind, i, j, k;
+    id.decode(t, kind, i, j, k);
+    auto& d = deps[t];
+    if (kind == 0) {
+      d.push_back(Li(k));
+      if (k >= 1) d.push_back(id.UA(i, k, k - 1));
+    } else if (kind == 1) {
+      d.push_back(Li(k));
+      d.push_back(id.UB(k, j, k - 1));
+    } else if (kind == 2) {
+      d.push_back(i == k + 1 ? Ln(k) : id.C(i, k));
+      if (j != i) d.push_back(j == k + 1 ? Ln(k) : id.C(j, k));
+      if (k >= 1) d.push_back(id.UA(i, j, k - 1));
+    } else {
+      d.push_back(i == k + 1 ? Ln(k) : id.C(i, k));
+      d.push_back(j < k ? id.X(k, j) : Li(k));
+      if (k > j) d.push_back(id.UB(i, j, k - 1));
+    }
+  }
+  for (int k = 0; k < T; ++k) {
+    if (k >= 1) deps[Li(k)].push_back(Ln(k - 1));
+    if (k >= 2) deps[Li(k)].push_back(id.UA(k, k, k - 2));
+    if (k + 1 < T) {
+      deps[Ln(k)].push_back(Li(k));
+      if (k >= 1) {
+        deps[Ln(k)].push_back(id.UA(k + 1, k, k - 1));
+        deps[Ln(k)].push_back(id.UA(k + 1, k + 1, k - 1));
+      }
+    }
+  }
+  // durations (us, measured on GB300): diagonal tile 10, panel tile and next diagonal 6, tile task 6
+  std::vector<double> dur(N, 6.0);
+  for (int k = 0; k < T; ++k) {
+    dur[Li(k)] = 10.0;
+    dur[Ln(k)] = 6.0;
+  }
+  std::vector<std::vector<int>> succ(N);
+  for (int v = 0; v < N; ++v)
+    for (int d : deps[v]) {
+      if (d < 0 || d >= N) return canonical;
+      succ[d].push_back(v);
+    }
+  // bottom levels in reverse topological order
+  std::vector<int> cnt(N), topo;
+  topo.reserve(N);
+  std::vector<int> stack;
+  for (int v = 0; v < N; ++v) {
+    cnt[v] = (int)deps[v].size();
+    if (cnt[v] == 0) stack.push_back(v);
+  }
+  while (!stack.empty()) {
+    const int v = stack.back();
+    stack.pop_back();
+    topo.push_back(v);
+    for (int w : succ[v])
+      if (--cnt[w] == 0) stack.push_back(w);
+  }
+  if ((int)topo.size() != N) return canonical;
+  std::vector<double> bl(N, 0.0);
+  for (int x = N - 1; x >= 0; --x) {
+    const int v = topo[x];
+    double m = 0.0;
+    for (int w : succ[v]) m = std::max(m, bl[w]);
+    bl[v] = dur[v] + m;
+  }
+  // event simulation
+  std::vector<int> rem(N);
+  for (int v = 0; v < N; ++v) rem[v] = (int)deps[v].size();
+  using RQ = std::pair<double, int>;  // (-bottom level, id): largest bottom level first, then smallest id
+  std::priority_queue<RQ, std::vector<RQ>, std::greater<RQ>> ready;
+  std::priority_queue<int, std::vector<int>, std::greater<int>> chain_ready;
+  using EV = std::pair<double, int>;
+  std::priority_queue<EV, std::vector<EV>, std::greater<EV>> ev;
+  for (int v = 0; v < N; ++v)
+    if (rem[v] == 0) {
+      if (v >= n) chain_ready.push(v); else ready.push({-bl[v], v});
+    }
+  std::vector<int> out;
+  out.reserve(n);
+  std::vector<double> start(N, -1.0);
+  double now = 0.0;
+  int free_w = workers;
+  bool chain_busy = false;
+  for (;;) {
+    while (free_w > 0 && !ready.empty()) {
+      const int v = ready.top().second;
+      ready.pop();
+      start[v] = now;
+      out.push_back(v);
+      --free_w;
+      ev.push({now + dur[v], v});
+    }
+    if (!chain_busy && !chain_ready.empty()) {
+      const int v = chain_ready.top();
+      chain_ready.pop();
+      start[v] = now;
+      chain_busy = true;
+      ev.push({now + dur[v], v});
+    }
+    if (ev.empty()) break;
+    now = ev.top().first;
+    const int v = ev.top().second;
+    ev.pop();
+    if (v >= n) chain_busy = false; else ++free_w;
+    for (int w : succ[v])
+      if (--rem[w] == 0) {
+        if (w >= n) chain_ready.push(w); else ready.push({-bl[w], w});
+      }
+  }
+  if ((int)out.size() != n) return canonical;
+  // check: a permutation, and every node starts no earlier than its inputs
+  std::vector<char> seen(n, 0);
+  for (int v : out) {
+    if (v < 0 || v >= n || seen[v]) return canonical;
+    seen[v] = 1;
+  }
+  for (int v = 0; v < N; ++v)
+    for (int d : deps[v])
+      if (!(start[d] >= 0.0 && start[v] >= start[d] + dur[d] - 1e-9)) return canonical;
+  return out;
+}
+
 int chol_launch_count(int P, int arith, int persistent_grid) {
   const int T = P / NB;
   if (arith == HS_CHOL_DF32) return persistent_grid > 0 ? 1 : T;
@@ -1372,7 +1707,7 @@ cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)a.persistent_grid);
     cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = kPersistSmem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
