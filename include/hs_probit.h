@@ -84,7 +84,7 @@ typedef struct hs_probit_config {
   void* stream;        /* cudaStream_t for the sweep; NULL: library-owned stream */
   const float* x_scales; /* HS_X_FP8E4M3 only: p column scales (host or device) */
   int32_t chol_sched;  /* HS_SCHED_*; ignored for HS_CHOL_F64 */
-  int32_t num_chains;  /* K independent chains sharing X (1..32; > 1 needs HS_X_BF16 and p <= 1152) */
+  int32_t num_chains;  /* K independent chains sharing X (1..32; > 1 needs HS_X_BF16 and p <= 1536) */
   int32_t reserved[6];
 } hs_probit_config;
 

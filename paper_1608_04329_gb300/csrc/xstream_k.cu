@@ -8,14 +8,18 @@
 //            z     ~ TN(eta, 1) truncated by y (Eq. 12, first line), branch-free
 //                    inverse CDF on the chain's own Philox counters
 //   pass 2   XtZ  += X_tile^T Z_hi + X_tile^T Z_lo   (p x K, tcgen05, TMEM)
+// with pass 1 of the next tile issued before pass 2 of this one (eta has two
+// TMEM buffers), so the tensor cores and the loads keep running while the
+// epilogue draws z.
 // where beta (FP64) is split into two BF16 parts B_hi + B_lo and so is z, so
 // that the products carry about 16 significant bits of beta and z; X itself
 // is exact in BF16 and the tensor cores accumulate in FP32.
 //
 // Data movement: X tiles arrive by TMA (box 64 features x 128 rows, 128-byte
-// swizzle) in a ring of 4 stages; pass 2 reads the same tile again, which the
-// 129 MB L2 still holds, so HBM sees X once per sweep.  B^T (both parts, all
-// features) stays in shared memory for the whole launch.  Each CTA owns a
+// swizzle) in a ring of 8 stages of 24 KB; in pass 1 each stage also receives
+// the matching 8 KB chunk of B^T (both parts, pre-swizzled in global memory,
+// L2-resident) by a bulk copy.  Pass 2 reads the same tile again, which the
+// 129 MB L2 still holds, so HBM sees X once per sweep.  Each CTA owns a
 // contiguous range of row tiles and keeps its X^T Z partial in TMEM; at the
 // end it writes the partial (p x 32, FP32) and a second kernel sums the
 // partials in a fixed order in FP64.
@@ -41,9 +45,10 @@ namespace {
 constexpr int kKc = 32;          // chains per launch (padded)
 constexpr int kTR = 128;         // rows per tile (MMA M of pass 1; K of pass 2)
 constexpr int kCF = 64;          // features per chunk (one 128-byte swizzle row)
-constexpr int kXStages = 4;      // ring stages
-constexpr uint32_t kStageBytes = kTR * kCF * 2;       // 16 KB
-constexpr uint32_t kBChunkBytes = 2 * kKc * kCF * 2;  // 8 KB: 64 rows (hi chains, lo chains) x 128 B
+constexpr int kXStages = 8;      // ring stages (even: pass 2 takes them in pairs)
+constexpr uint32_t kXChunkBytes = kTR * kCF * 2;      // 16 KB: 128 rows x 64 features of X
+constexpr uint32_t kBChunkBytes = 2 * kKc * kCF * 2;  // 8 KB: 64 rows (hi chains, lo chains) x 128 B of B^T
+constexpr uint32_t kStageBytes = kXChunkBytes + kBChunkBytes;  // 24 KB: X chunk, then (pass 1) its B^T chunk
 constexpr uint32_t kZBlock = kKc * 128;               // 4 KB: 32 chains x 64 rows x 2 B
 constexpr int kThreads = 384;  // 4 role warps + 8 epilogue warps
 
@@ -125,9 +130,44 @@ __host__ __device__ __forceinline__ uint32_t sw128_off(int n, int k) {
          (byte & 15u);
 }
 
+// ---- the latent draw of the batched form --------------------------------------
+// Phi^{-1}(p) for 0 < p <= 1/2: Wichura (1988), Applied Statistics 37,
+// Algorithm AS 241, PPND7 (rational approximations, about 7 significant
+// digits; 1.2e-7 mixed relative error against scipy's ndtri for p down to
+// 1e-37).  Both arms are evaluated and selected, so lanes do not diverge.
+__device__ __forceinline__ float ppnd7_lower(float p) {
+  const float q = p - 0.5f;
+  const float r1 = 0.180625f - q * q;
+  const float num1 = fmaf(fmaf(fmaf(59.109374720f, r1, 159.29113202f), r1, 50.434271938f), r1, 3.3871327179f);
+  const float den1 = fmaf(fmaf(fmaf(67.187563600f, r1, 78.757757664f), r1, 17.895169469f), r1, 1.0f);
+  const float central = q * __fdividef(num1, den1);
+  const float r = sqrtf(-__logf(p));
+  const bool near = r <= 5.0f;
+  const float rr = near ? r - 1.6f : r - 5.0f;
+  const float c3 = near ? 0.17023821103f : 0.017337203997f, c2 = near ? 1.3067284816f : 0.42868294337f;
+  const float c1 = near ? 2.7568153900f : 3.0812263860f, c0 = near ? 1.4234372777f : 6.6579051150f;
+  const float d2 = near ? 0.12021132975f : 0.012258202635f, d1 = near ? 0.73700164250f : 0.24197894225f;
+  const float tail = -__fdividef(fmaf(fmaf(fmaf(c3, rr, c2), rr, c1), rr, c0), fmaf(fmaf(d2, rr, d1), rr, 1.0f));
+  return fabsf(q) <= 0.425f ? central : tail;
+}
+// z+ = ms - Phi^{-1}(u Phi(ms)) (Eq. 12, first line; the main arm of
+// tn_main): Phi(ms) and Phi(-ms) come from one erfc of |ms| (the smaller is
+// the tail, the other 1 - tail), and Phi^{-1} is taken on the smaller of q
+// and 1 - q = (1 - u) + u Phi(-ms).
+__device__ __forceinline__ float tn_main_k(float ms, float u, float uc) {
+  const float t = 0.5f * erfcf(fabsf(ms) * 0.70710678118654752f);  // Phi(-|ms|)
+  const float pm = ms < 0.0f ? t : 1.0f - t;
+  const float pc = ms < 0.0f ? 1.0f - t : t;
+  const float q = u * pm;
+  const float qc = fmaf(u, pc, uc);
+  const bool lower = q <= qc;
+  const float w0 = ppnd7_lower(lower ? q : qc);
+  return ms - (lower ? w0 : -w0);
+}
+
 struct XKShared {
   uint64_t full[kXStages], empty[kXStages];
-  uint64_t bfull, eta_full, eta_empty, z_ready, zt_empty, acc_done;
+  uint64_t eta_full[2], eta_empty[2], z_ready, zt_empty, acc_done;
   uint32_t tmem;
   int abort;
 };
@@ -153,9 +193,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ XKShared sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char* base = dyn + ((1024u - (smem_u32(dyn) & 1023u)) & 1023u);  // 1024-byte aligned
-  unsigned char* sB = base;                                           // nch x 8 KB
-  unsigned char* sX = sB + (size_t)a.nch * kBChunkBytes;              // kXStages x 16 KB
-  unsigned char* sZ = sX + (size_t)kXStages * kStageBytes;            // [hi/lo][rows 0-63 | 64-127] x 4 KB
+  unsigned char* sX = base;                                   // kXStages x 24 KB
+  unsigned char* sZ = sX + (size_t)kXStages * kStageBytes;    // [hi/lo][rows 0-63 | 64-127] x 4 KB
   const int64_t ntiles = (a.N + kTR - 1) / kTR;
   const int64_t t0 = ntiles * blockIdx.x / gridDim.x;
   const int64_t t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
@@ -173,9 +212,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&sh.full[s], 1);
       mbar_init(&sh.empty[s], 1);
     }
-    mbar_init(&sh.bfull, 1);
-    mbar_init(&sh.eta_full, 1);
-    mbar_init(&sh.eta_empty, 256);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh.eta_full[b], 1);
+      mbar_init(&sh.eta_empty[b], 256);
+    }
     mbar_init(&sh.z_ready, 256);
     mbar_init(&sh.zt_empty, 1);
     mbar_init(&sh.acc_done, 1);
@@ -190,23 +230,31 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sh.tmem;
-  const uint32_t tm_eta = tmem;        // columns [0, 64): eta' (hi chains, lo chains)
-  const uint32_t tm_xtz = tmem + 64;   // columns [64 + 32 g, 96 + 32 g): X^T Z of feature group g
+  const uint32_t tm_eta = tmem;        // columns [64 b, 64 b + 64): eta' of buffer b (hi chains, lo chains)
+  const uint32_t tm_xtz = tmem + 128;  // columns [128 + 32 g, 160 + 32 g): X^T Z of feature group g
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
-    mbar_arrive_expect_tx(&sh.bfull, (uint32_t)nch * kBChunkBytes);
-    bulk_g2s(sB, a.bsw, (uint32_t)nch * kBChunkBytes, &sh.bfull);
+    // load order (as the MMA issuer consumes): pass 1 of t0; then for each
+    // tile t, pass 1 of t + 1 and pass 2 of t
     uint32_t q = 0;
-    for (int64_t t = t0; t < t1 && !sh.abort; ++t) {
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int c = 0; c < nch; ++c, ++q) {
-          const int s = q % kXStages;
-          if (!xk_wait(&sh.empty[s], ((q / kXStages) & 1) ^ 1, &sh, a.err)) break;
-          mbar_arrive_expect_tx(&sh.full[s], kStageBytes);
-          tma_load_2d(sX + (size_t)s * kStageBytes, &xmap, c * kCF, (int)(t * kTR), &sh.full[s]);
-        }
+    auto load_pass = [&](int64_t t, bool with_b) -> bool {
+      for (int c = 0; c < nch; ++c, ++q) {
+        const int s = q % kXStages;
+        if (!xk_wait(&sh.empty[s], ((q / kXStages) & 1) ^ 1, &sh, a.err)) return false;
+        unsigned char* st = sX + (size_t)s * kStageBytes;
+        mbar_arrive_expect_tx(&sh.full[s], with_b ? kStageBytes : kXChunkBytes);
+        tma_load_2d(st, &xmap, c * kCF, (int)(t * kTR), &sh.full[s]);
+        if (with_b)
+          bulk_g2s(st + kXChunkBytes, static_cast<const unsigned char*>(a.bsw) + (size_t)c * kBChunkBytes,
+                   kBChunkBytes, &sh.full[s]);
       }
+      return true;
+    };
+    bool okp = t0 < t1 ? load_pass(t0, true) : true;
+    for (int64_t t = t0; t < t1 && okp; ++t) {
+      if (t + 1 < t1 && !(okp = load_pass(t + 1, true))) break;
+      okp = load_pass(t, false);
     }
     // drain: every issued load must land before the CTA may exit
     const uint32_t nd = q < (uint32_t)kXStages ? q : (uint32_t)kXStages;
@@ -214,33 +262,37 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t qq = q - d;
       mbar_wait(&sh.full[qq % kXStages], (qq / kXStages) & 1, 2000000000ull);
     }
-    mbar_wait(&sh.bfull, 0, 2000000000ull);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
     const uint32_t id_eta = idesc_bf16(kTR, 2 * kKc, 0, 0);   // M 128 rows, N 64 (hi, lo), both K-major
     const uint32_t id_xtz = idesc_bf16(128, kKc, 1, 0);       // M 128 features (MN-major A), N 32 chains
-    bool ok = xk_wait(&sh.bfull, 0, &sh, a.err);
-    tc_fence_after();
+    bool ok = true;
     uint32_t q = 0;
-    int it = 0;
-    for (int64_t t = t0; t < t1 && ok; ++t, ++it) {
-      // pass 1: eta' of the tile (the epilogue must have read the previous one)
-      if (!(ok = xk_wait(&sh.eta_empty, (it & 1) ^ 1, &sh, a.err))) break;
+    // pass 1 of tile number n (within this CTA) into eta buffer n % 2
+    auto pass1 = [&](int n) -> bool {
+      const int b = n & 1;
+      if (!xk_wait(&sh.eta_empty[b], ((n >> 1) & 1) ^ 1, &sh, a.err)) return false;  // the epilogue read it
       tc_fence_after();
       for (int c = 0; c < nch; ++c, ++q) {
         const int s = q % kXStages;
-        if (!(ok = xk_wait(&sh.full[s], (q / kXStages) & 1, &sh, a.err))) break;
+        if (!xk_wait(&sh.full[s], (q / kXStages) & 1, &sh, a.err)) return false;
         tc_fence_after();
         const uint32_t xa = smem_u32(sX + (size_t)s * kStageBytes);
-        const uint32_t ba = smem_u32(sB + (size_t)c * kBChunkBytes);
+        const uint32_t ba = xa + kXChunkBytes;
 #pragma unroll
         for (int kk = 0; kk < kCF / 16; ++kk)
-          mma_bf16(tm_eta, sw128_desc(xa + kk * 32, 16, 1024), sw128_desc(ba + kk * 32, 16, 1024), id_eta,
+          mma_bf16(tm_eta + 64 * b, sw128_desc(xa + kk * 32, 16, 1024), sw128_desc(ba + kk * 32, 16, 1024), id_eta,
                    (c > 0 || kk > 0) ? 1 : 0);
         mma_commit(&sh.empty[s]);
       }
-      if (!ok) break;
-      mma_commit(&sh.eta_full);
+      mma_commit(&sh.eta_full[b]);
+      return true;
+    };
+    const int ntl = (int)(t1 - t0);
+    if (ok && ntl > 0) ok = pass1(0);
+    for (int it = 0; it < ntl && ok; ++it) {
+      // pass 1 of the next tile runs while the epilogue draws z of this one
+      if (it + 1 < ntl && !(ok = pass1(it + 1))) break;
       // pass 2: X^T Z once the epilogue has written Z^T of this tile
       if (!(ok = xk_wait(&sh.z_ready, it & 1, &sh, a.err))) break;
       tc_fence_after();
@@ -253,6 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int kk = 0; kk < kTR / 16; ++kk) {
           const uint64_t ad = sw128_desc(xa + kk * 2048, kStageBytes, 1024);  // rows 16kk.., features of both stages
+          // (the second 64-feature atom of A is the next stage's X chunk, kStageBytes further)
 #pragma unroll
           for (int hl = 0; hl < 2; ++hl) {
             const uint32_t za = smem_u32(sZ + (size_t)(hl * 2 + kk / 4) * kZBlock) + (kk % 4) * 32;
@@ -276,14 +329,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t sweep = (uint32_t)(*a.k_dev + 1);
     int it = 0;
     for (int64_t t = t0; t < t1; ++t, ++it) {
-      if (!xk_wait(&sh.eta_full, it & 1, &sh, a.err)) break;
+      const int eb = it & 1;  // eta buffer of this tile
+      if (!xk_wait(&sh.eta_full[eb], (it >> 1) & 1, &sh, a.err)) break;
       tc_fence_after();
       uint32_t hi[16], lo[16];
-      tmem_ld16(tm_eta + lane_off + m0, hi);
-      tmem_ld16(tm_eta + lane_off + 32 + m0, lo);
+      tmem_ld16(tm_eta + 64 * eb + lane_off + m0, hi);
+      tmem_ld16(tm_eta + 64 * eb + lane_off + 32 + m0, lo);
       tmem_ld_wait();
       tc_fence_before();
-      mbar_arrive(&sh.eta_empty);
+      mbar_arrive(&sh.eta_empty[eb]);
       const int64_t i = t * kTR + er;
       const bool active = i < a.N;
       const int yi = active ? a.y[i] : 1;
@@ -302,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           unit_pair_f(wd.x, wd.y, u, uc);
         }
         const float ms = on ? (yi ? eta : -eta) : 0.0f;
-        float zp = tn_main<float>(ms, u, uc);
+        float zp = tn_main_k(ms, u, uc);
         const bool tail = on && ms < TnMath<float>::kTail;
         if (tail) zp = tn_tail<float>(ms, u, uc);
         zp = zp > TnMath<float>::tiny() ? zp : TnMath<float>::tiny();
@@ -384,13 +438,14 @@ int xstream_k_chunks(int p) {
 }
 
 size_t xstream_k_smem_bytes(int p) {
-  return 1024 + (size_t)xstream_k_chunks(p) * kBChunkBytes + (size_t)kXStages * kStageBytes + 4 * (size_t)kZBlock;
+  (void)p;
+  return 1024 + (size_t)kXStages * kStageBytes + 4 * (size_t)kZBlock;
 }
 
 bool xstream_k_supported(int p) {
   const int nch = xstream_k_chunks(p);
-  // TMEM: 64 columns of eta' + 32 per 128-feature group; shared memory as above
-  return p >= 1 && 64 + 32 * (nch / 2) <= 512 && xstream_k_smem_bytes(p) <= 227 * 1024;
+  // TMEM: two eta' buffers of 64 columns + 32 per 128-feature group
+  return p >= 1 && 128 + 32 * (nch / 2) <= 512 && xstream_k_smem_bytes(p) <= 227 * 1024;
 }
 
 cudaError_t xstream_k_prepare(int p) {
