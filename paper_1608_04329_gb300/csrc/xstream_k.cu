@@ -113,13 +113,25 @@ __device__ __forceinline__ void unit_pair_f(uint32_t hi, uint32_t lo, float& u, 
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// 2-D TMA load of one box into shared memory, completing on an mbarrier.
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+// 2-D TMA load of one box into shared memory, completing on an mbarrier, with
+// an L2 eviction-priority policy (createpolicy).
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                            uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-          "r"(smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
       : "memory");
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
 
 // Byte offset of element (row n, column k < 64) in a 128-byte-swizzled K-major
@@ -238,13 +250,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     // load order (as the MMA issuer consumes): pass 1 of t0; then for each
     // tile t, pass 1 of t + 1 and pass 2 of t
     uint32_t q = 0;
+    // pass 1 keeps the tile in L2 for pass 2 (which reads it for the last time)
+    const uint64_t pol_keep = l2_policy_evict_last(), pol_done = l2_policy_evict_first();
     auto load_pass = [&](int64_t t, bool with_b) -> bool {
       for (int c = 0; c < nch; ++c, ++q) {
         const int s = q % kXStages;
         if (!xk_wait(&sh.empty[s], ((q / kXStages) & 1) ^ 1, &sh, a.err)) return false;
         unsigned char* st = sX + (size_t)s * kStageBytes;
         mbar_arrive_expect_tx(&sh.full[s], with_b ? kStageBytes : kXChunkBytes);
-        tma_load_2d(st, &xmap, c * kCF, (int)(t * kTR), &sh.full[s]);
+        tma_load_2d(st, &xmap, c * kCF, (int)(t * kTR), &sh.full[s], with_b ? pol_keep : pol_done);
         if (with_b)
           bulk_g2s(st + kXChunkBytes, static_cast<const unsigned char*>(a.bsw) + (size_t)c * kBChunkBytes,
                    kBChunkBytes, &sh.full[s]);
