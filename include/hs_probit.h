@@ -68,6 +68,18 @@ extern "C" {
 #define HS_SCHED_SINGLE   2  /* one cooperative launch, tiles scheduled by data readiness;
                                 init fails with HS_EUNSUPPORTED where the device lacks it */
 
+/* ---- how beta is drawn from the factor -----------------------------------
+ * beta = S L~^{-T} (L~^{-1} S X^T z + s) either way (Sect. 5, beta update);
+ * the two forms round differently (agreement to about 1e-12 relative). */
+#define HS_BETA_AUTO     0  /* HS_BETA_SUBST for several chains on the single-launch
+                                schedule, else HS_BETA_INVERSE */
+#define HS_BETA_INVERSE  1  /* the factorization also forms L~^{-1}; beta by two
+                                parallel matrix-vector products */
+#define HS_BETA_SUBST    2  /* factor only (half the tile products); beta by block
+                                forward and back substitution, one block per chain;
+                                needs HS_CHOL_DF32 on the single-launch schedule,
+                                else init fails with HS_EUNSUPPORTED */
+
 typedef struct hs_probit hs_probit;  /* opaque handle */
 
 typedef struct hs_probit_config {
@@ -85,7 +97,8 @@ typedef struct hs_probit_config {
   const float* x_scales; /* HS_X_FP8E4M3 only: p column scales (host or device) */
   int32_t chol_sched;  /* HS_SCHED_*; ignored for HS_CHOL_F64 */
   int32_t num_chains;  /* K independent chains sharing X (1..32; > 1 needs HS_X_BF16 and p <= 1536) */
-  int32_t reserved[6];
+  int32_t beta_solve;  /* HS_BETA_* */
+  int32_t reserved[5];
 } hs_probit_config;
 
 /* Values of one sampler state (Eq. 12 variables).  Arrays are host memory of

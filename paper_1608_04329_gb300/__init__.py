@@ -23,11 +23,12 @@ import numpy as np
 
 __all__ = ["HSProbit", "HSProbitError", "load_library", "library_path", "STATUS",
            "X_F64", "X_F32", "X_BF16", "X_FP8E4M3", "CHOL_F64", "CHOL_DF32",
-           "SCHED_AUTO", "SCHED_COLUMNS", "SCHED_SINGLE"]
+           "SCHED_AUTO", "SCHED_COLUMNS", "SCHED_SINGLE", "BETA_AUTO", "BETA_INVERSE", "BETA_SUBST"]
 
 X_F64, X_F32, X_BF16, X_FP8E4M3 = 0, 1, 2, 3
 CHOL_F64, CHOL_DF32 = 0, 1
 SCHED_AUTO, SCHED_COLUMNS, SCHED_SINGLE = 0, 1, 2
+BETA_AUTO, BETA_INVERSE, BETA_SUBST = 0, 1, 2
 STATUS = {0: "HS_OK", -1: "HS_EINVAL", -2: "HS_ENOMEM", -3: "HS_ECUDA", -4: "HS_ENOTPD",
           -5: "HS_ENONFINITE", -6: "HS_ETIMEOUT", -7: "HS_ESTATE", -8: "HS_EUNSUPPORTED"}
 KERNEL_GROUPS = {"xstream": 0, "reduce": 1, "shrink": 2, "cholesky": 3, "tail": 4, "gram": 5}
@@ -50,7 +51,8 @@ class _Config(ctypes.Structure):
                 ("ring_size", ctypes.c_int32), ("debug", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("chol_arith", ctypes.c_int32), ("device", ctypes.c_int32), ("chain", ctypes.c_uint32),
                 ("problem", ctypes.c_uint32), ("stream", ctypes.c_void_p), ("x_scales", ctypes.c_void_p),
-                ("chol_sched", ctypes.c_int32), ("num_chains", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("chol_sched", ctypes.c_int32), ("num_chains", ctypes.c_int32), ("beta_solve", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class _StateView(ctypes.Structure):
@@ -150,7 +152,7 @@ class HSProbit:
     def __init__(self, X, y, seed: int = 0, *, scales=None, thin: int = 1, ring_size: int = 1024,
                  debug: bool = False, use_graph: bool = False, chol_arith: int = CHOL_DF32, chain: int = 0,
                  problem: int = 0, stream=None, device: int = 0, x_dtype: int | None = None,
-                 chol_sched: int = SCHED_AUTO, num_chains: int = 1):
+                 chol_sched: int = SCHED_AUTO, num_chains: int = 1, beta_solve: int = BETA_AUTO):
         self._lib = load_library()
         self._h = None
         is_dev = hasattr(X, "is_cuda") and bool(X.is_cuda)
@@ -179,6 +181,7 @@ class HSProbit:
         cfg.chol_arith = chol_arith
         cfg.chol_sched = chol_sched
         cfg.num_chains = num_chains
+        cfg.beta_solve = beta_solve
         cfg.device = device
         cfg.chain = chain
         cfg.problem = problem

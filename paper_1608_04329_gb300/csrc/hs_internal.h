@@ -119,8 +119,9 @@ struct CholArgs {
   const double* lam_new;  // p
   const double* tau_new;  // 1
   void* A;                // P x P workspace (double, or FP32 pairs); lower part becomes L~
-  void* Linv;             // P x P; lower part becomes L~^{-1}
-  void* LinvT;            // P x P; upper part becomes L~^{-T}
+  void* Linv;             // P x P; lower part becomes L~^{-1} (diagonal tiles only when !inverse)
+  void* LinvT;            // P x P; upper part becomes L~^{-T} (when !inverse: diagonal tiles
+                          // L~_kk^{-T}, off-diagonal tiles (k, i) the transposed factor L~_ik^T)
   int* err;
   int arith;              // HS_CHOL_*
   unsigned long long* sync;  // HS_CHOL_DF32 single-launch schedule: readiness words (chol_sync_words)
@@ -133,6 +134,7 @@ struct CholArgs {
   int nchains;                  // 0 or 1: one chain
   size_t sync_words;
   const int* order;             // worker task list (chol_task_order), or nullptr: canonical order
+  int inverse;                  // single-launch schedule: 1 forms all of L~^{-1}; 0 only its diagonal tiles
 };
 // Enqueues the whole factorization; *launches receives the kernel count.
 cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches);
@@ -145,7 +147,7 @@ size_t chol_sync_words(int P);
 int chol_persistent_grid(int device, int nchains = 1);
 // Worker task list of the single-launch factorization for T tiles and about
 // `workers` concurrent task slots (a topological order; see linalg.cu).
-std::vector<int> chol_task_order(int T, int workers);
+std::vector<int> chol_task_order(int T, int workers, bool inverse);
 
 // ---- beta tail, nu/xi, commit ----------------------------------------------
 struct TailArgs {
@@ -157,7 +159,12 @@ struct TailArgs {
   const void* Linv;        // P x P lower (double, or FP32 pairs when df32)
   const void* LinvT;       // P x P upper (same storage)
   int df32;
-  double* v;               // P scratch: L^{-1} X^T z + s
+  // solve != 0 (FP32 pairs, factorization with inverse == 0): beta by block
+  // substitution with the factor's tiles, L~_ik in L (tile (i, k), i > k),
+  // L~_ik^T in LinvT (tile (k, i)) and L~_kk^{-1} in Linv (tile (k, k))
+  int solve;
+  const void* L;           // P x P factor tiles (CholArgs::A)
+  double* v;               // P scratch: L^{-1} X^T z + s (substitution form: s)
   double* beta_new;        // p
   double* nu_new;          // p
   const double* lam_new;   // p
@@ -181,6 +188,9 @@ struct TailArgs {
 // chain's commit must follow every chain's draws).
 cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s, int nchains = 1);
 cudaError_t commit_enqueue(const TailArgs& a, cudaStream_t s, int nchains = 1);
+// Substitution form only (TailArgs::solve): the s_j and nu_j^{-1} draws, which
+// must precede tail_draw_enqueue and follow the shrink kernel; no-op otherwise.
+cudaError_t tail_noise_enqueue(const TailArgs& a, cudaStream_t s, int nchains = 1);
 
 // beta_c = (compute type)(beta * colscale), pads zero.
 cudaError_t beta_c_launch(const double* beta, const float* colscale, int p, int ld, void* beta_c,

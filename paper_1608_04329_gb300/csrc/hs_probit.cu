@@ -61,7 +61,7 @@ struct hs_probit {
   hs::RngKey rng{};
   cudaStream_t s0 = nullptr, s1 = nullptr;
   bool own_s0 = false;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_shrink = nullptr;
   std::vector<void*> allocs;
 
   void* X = nullptr;
@@ -102,6 +102,7 @@ struct hs_probit {
   int64_t k_host = 0;
   std::vector<int64_t> drained;  // per chain: draws (index k/thin) already handed out
   int64_t launches = 0;
+  bool chol_inverse = true;  // the factorization forms L~^{-1} (HS_BETA_INVERSE)
 
   bool graph_ready = false;
   cudaGraph_t graph = nullptr;
@@ -247,6 +248,7 @@ hs::CholArgs chol_args(hs_probit* h, int m) {
   a.nchains = 1;
   a.sync_words = h->chol_words;
   a.order = h->chol_order;
+  a.inverse = h->chol_inverse ? 1 : 0;
   return a;
 }
 
@@ -263,6 +265,8 @@ hs::TailArgs tail_args(hs_probit* h, int m) {
   a.Linv = h->Linv + m * P2;
   a.LinvT = h->LinvT + m * P2;
   a.df32 = (h->cfg.chol_arith == HS_CHOL_DF32);
+  a.solve = h->chol_inverse ? 0 : 1;
+  a.L = h->A + m * P2;
   a.v = h->v + (size_t)m * h->P;
   a.beta_new = h->beta_new + m * p;
   a.nu_new = h->nu_new + m * p;
@@ -323,6 +327,7 @@ cudaError_t enqueue_sweep(hs_probit* h) {
     ProfSpan sp(h, 2, h->s1);
     if ((e = hs::shrink_launch(shrink_args(h, 0), h->s1, h->K)) != cudaSuccess) return e;
   }
+  if (!h->chol_inverse && (e = cudaEventRecord(h->ev_shrink, h->s1)) != cudaSuccess) return e;
   {
     ProfSpan sp(h, 3, h->s1);
     if (h->K > 1 && h->chol_grid > 0) {
@@ -358,6 +363,11 @@ cudaError_t enqueue_sweep(hs_probit* h) {
       ProfSpan sp(h, 1, h->s0);
       if ((e = hs::xstream_k_reduce(xa, h->kgrid, h->xtz, h->p, h->s0)) != cudaSuccess) return e;
     }
+  }
+  if (!h->chol_inverse) {
+    // the substitution form's s and nu draws need lambda^{-2} only: beside the factorization
+    if ((e = cudaStreamWaitEvent(h->s0, h->ev_shrink, 0)) != cudaSuccess) return e;
+    if ((e = hs::tail_noise_enqueue(tail_args(h, 0), h->s0, h->K)) != cudaSuccess) return e;
   }
   if ((e = cudaStreamWaitEvent(h->s0, h->ev_join, 0)) != cudaSuccess) return e;
   {
@@ -455,6 +465,7 @@ void destroy(hs_probit* h) {
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_shrink) cudaEventDestroy(h->ev_shrink);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->h_k) cudaFreeHost(h->h_k);
@@ -522,7 +533,8 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   if (!X || !y || N < 2 || p < 1 || p > kMaxP || cfg.thin < 1 || cfg.ring_size < 1 ||
       cfg.chain >= (1u << 24) || (cfg.x_dtype < HS_X_F64 || cfg.x_dtype > HS_X_FP8E4M3) ||
       (cfg.chol_arith != HS_CHOL_F64 && cfg.chol_arith != HS_CHOL_DF32) || N > (int64_t)0xFFFFFFFF ||
-      cfg.chol_sched < HS_SCHED_AUTO || cfg.chol_sched > HS_SCHED_SINGLE) {
+      cfg.chol_sched < HS_SCHED_AUTO || cfg.chol_sched > HS_SCHED_SINGLE || cfg.beta_solve < HS_BETA_AUTO ||
+      cfg.beta_solve > HS_BETA_SUBST) {
     fail(HS_EINVAL);
     return nullptr;
   }
@@ -605,6 +617,14 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
       return nullptr;
     }
   }
+  // beta by substitution needs the single-launch schedule's inverse-free mode
+  if (e == cudaSuccess && cfg.beta_solve == HS_BETA_SUBST && h->chol_grid == 0) {
+    destroy(h);
+    fail(HS_EUNSUPPORTED);
+    return nullptr;
+  }
+  h->chol_inverse = !(h->chol_grid > 0 && (cfg.beta_solve == HS_BETA_SUBST ||
+                                          (cfg.beta_solve == HS_BETA_AUTO && h->K > 1)));
   if (cfg.stream) {
     h->s0 = static_cast<cudaStream_t>(cfg.stream);
   } else {
@@ -614,6 +634,7 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   check(cudaStreamCreateWithFlags(&h->s1, cudaStreamNonBlocking));
   check(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   check(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  check(cudaEventCreateWithFlags(&h->ev_shrink, cudaEventDisableTiming));
   const size_t P2 = (size_t)h->P * h->P;
   const size_t pd = (size_t)p * sizeof(double);
   const size_t K = (size_t)h->K;
@@ -653,7 +674,7 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
     check(h->alloc(&h->sm_mark, hs::kSmMarks * sizeof(unsigned int)));
     // two task slots per worker block, shared by the chains
     const int slots = 2 * (h->chol_grid - h->K) / h->K;
-    order = hs::chol_task_order(h->T, slots > 1 ? slots : 1);
+    order = hs::chol_task_order(h->T, slots > 1 ? slots : 1, h->chol_inverse);
     if (!order.empty()) check(h->alloc(&h->chol_order, order.size() * sizeof(int)));
   }
   if (h->K == 1) {
@@ -729,7 +750,8 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   // per chain: shrink, the factorization, two draws, commit; then the X-stream and its reduce
   const int64_t chol_l = hs::chol_launch_count(h->P, h->cfg.chol_arith, h->chol_grid);
   // shrink, factorization (one launch for every chain when single-launch), two draws, commits
-  h->launches = 1 + ((h->K > 1 && h->chol_grid > 0) ? chol_l : h->K * chol_l) + 2 + (h->K > 1 ? 2 : 1) +
+  h->launches = 1 + ((h->K > 1 && h->chol_grid > 0) ? chol_l : h->K * chol_l) + 2 +
+                (h->K > 1 ? 2 : 1) +
                 (h->K == 1 ? 2 : 3);
   return h;
 }

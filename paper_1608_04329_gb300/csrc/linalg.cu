@@ -740,6 +740,10 @@ __global__ void __launch_bounds__(256) step_df_kernel(CholArgs a, int k) {
 //   X(k,j)   X_kj = L_kk^{-1} B_kj                   j < k
 //   UA(i,j,k) A_ij -= L_ik L_jk^T   k < j <= i, except the diagonal tile's last update
 //   UB(i,j,k) B_ij -= L_ik X_kj     i > k, j <= k
+// Without the inverse factor (CholArgs::inverse == 0) the X and UB tasks are
+// left out, so the launch does half the tile products; the chain still forms
+// every L_kk^{-1}, and the C tasks and the chain also store L_ik^T at tile
+// (k, i) of LinvT, for the block substitutions of the tail.
 // Readiness lives in per-tile words tagged with the sweep number e: a flag
 // holds e once its tile is published; an update counter holds e*64 + n after
 // n updates (values of earlier sweeps are smaller, so nothing is reset).
@@ -765,12 +769,9 @@ __host__ __device__ __forceinline__ int nUA(int T, int k) {
   return m > 0 ? m * (m + 1) / 2 - 1 : 0;  // without the diagonal tile (k+1, k+1)
 }
 __host__ __device__ __forceinline__ int nUB(int T, int k) { return (T - k - 1) * (k + 1); }
-__host__ __device__ __forceinline__ int nTasks(int T, int k) { return nC(T, k) + k + nUA(T, k) + nUB(T, k); }
-
-__host__ __device__ inline int total_tasks(int T) {
-  int n = 0;
-  for (int k = 0; k < T; ++k) n += nTasks(T, k);
-  return n;
+// inv: the inverse factor is formed (X and UB tasks); otherwise only C and UA
+__host__ __device__ __forceinline__ int nTasks(int T, int k, bool inv) {
+  return nC(T, k) + nUA(T, k) + (inv ? k + nUB(T, k) : 0);
 }
 struct PSync {
   unsigned long long *epoch, *ticket, *abort, *claim, *start, *chain_sm, *next;
@@ -1071,6 +1072,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
   const int T = a.P / NB;
   const int P = a.P;
   const int nch = a.nchains > 1 ? a.nchains : 1;
+  const bool inv = a.inverse != 0;
   const PSync ps0(a.sync, T);  // chain 0's words also hold the launch-wide header
   unsigned int smid;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
@@ -1147,6 +1149,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
       __syncthreads();
       tile_mma<false>(sLi, sW, sX1);  // L_{k+1,k} = A_{k+1,k} L_kk^{-T}
       tile_store_cg(A, P, k + 1, k, sLi, false);
+      if (!inv) tile_store_cg(LinvT, P, k, k + 1, sLi, true);
       block_publish(&ps.flagL[(k + 1) * T + k], e);
       for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) sX2[t & 31][t >> 5] = sLi[t >> 5][t & 31];
       __syncthreads();
@@ -1158,7 +1161,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
       int acc = 0;
       for (int kk = 0; kk <= T; ++kk) {
         s_step0[kk] = acc;
-        if (kk < T) acc += nTasks(T, kk);
+        if (kk < T) acc += nTasks(T, kk, inv);
       }
     }
     __syncthreads();
@@ -1211,11 +1214,12 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         g.sync();
         gmma<false>(g, gX2, gW, gX1);
         gstore_cg(g, A, P, i, k, gX2, false);
+        if (!inv) gstore_cg(g, LinvT, P, k, i, gX2, true);
         gpublish(g, &ps.flagL[i * T + k], e);
         continue;
       }
       u -= c;
-      if (u < k) {
+      if (inv && u < k) {
         // X(k,j): X_kj = L_kk^{-1} B_kj, j = u; B_kj after its k - j updates
         const int j = u;
         const unsigned long long* const wp2[2] = {&ps.flagLi[k], &ps.cntB[k * T + j]};
@@ -1230,7 +1234,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         gpublish(g, &ps.flagX[k * T + j], e);
         continue;
       }
-      u -= k;
+      if (inv) u -= k;
       if (u < ua) {
         // UA(i,j,k): A_ij -= L_ik L_jk^T.  The lower triangle of tile rows/cols
         // k+1..T-1 is listed column by column (column k+1, which feeds the
@@ -1310,6 +1314,7 @@ __device__ __forceinline__ TailArgs tail_chain(TailArgs a, int m) {
   a.S += m * P;
   a.Linv = static_cast<const unsigned char*>(a.Linv) + m * P2 * eb;
   a.LinvT = static_cast<const unsigned char*>(a.LinvT) + m * P2 * eb;
+  if (a.L) a.L = static_cast<const unsigned char*>(a.L) + m * P2 * eb;
   a.v += m * P;
   a.beta_new += m * p;
   a.nu_new += m * p;
@@ -1374,6 +1379,140 @@ __global__ void __launch_bounds__(256) tail_beta_kernel(TailArgs a0) {
     unit_pair(w.x, w.y, u, uc);
     a.nu_new[j] = -log(u) / (1.0 + a.lam_new[j]);
   }
+}
+
+// beta by block substitution, for the factorization without the inverse
+// factor (Sect. 5, beta update, steps iv to viii: the same two triangular
+// systems the explicit inverse is applied to):
+//   b = S X^T z;  L~ y = b:    y_k = L~_kk^{-1} (b_k - sum_{j<k} L~_kj y_j)
+//   v = y + s;    L~^T x = v:  x_k = L~_kk^{-T} (v_k - sum_{i>k} L~_ik^T x_i)
+//   beta = S x   (s and the nu_j^{-1} draws: tail_noise_kernel, earlier).
+// One block per chain (blockIdx.x), FP32 pairs.  The right-hand side lives in
+// shared memory and is updated column-panel by column-panel right after each
+// diagonal tile is solved; the panel reads are coalesced (forward through the
+// transposed factor tiles, backward through the factor's own rows).  Rows
+// past p (padding) carry zero.  blockDim.x must be kSolveThreads.
+constexpr int kSolveThreads = 512;
+__device__ __forceinline__ float4 diag_tile_fetch(const df2* Li, int P, int k) {
+  const int rr = threadIdx.x >> 4, cc = (threadIdx.x & 15) * 2;
+  return __ldg(reinterpret_cast<const float4*>(Li + (size_t)(k * NB + rr) * P + k * NB + cc));
+}
+__device__ __forceinline__ void diag_tile_put(df2 (*D)[NB + 1], float4 v) {
+  const int rr = threadIdx.x >> 4, cc = (threadIdx.x & 15) * 2;
+  D[rr][cc] = df2{v.x, v.y};
+  D[rr][cc + 1] = df2{v.z, v.w};
+}
+// r_i -= sum_c M[c][i] y_c for i in [i0, i1), M rows P apart (one panel of 32
+// rows).  Two rows per thread and pass, all 64 loads issued before the sums,
+// so that each pass pays one memory latency.
+__device__ __forceinline__ void panel_update(df2* r, const df2* M, int P, int i0, int i1, const df2* y) {
+  for (int i = i0 + (int)threadIdx.x; i < i1; i += 2 * kSolveThreads) {
+    const int i2 = i + kSolveThreads;
+    const bool two = i2 < i1;
+    float2 m0[NB], m1[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      m0[c] = __ldg(reinterpret_cast<const float2*>(M + (size_t)c * P + i));
+      m1[c] = two ? __ldg(reinterpret_cast<const float2*>(M + (size_t)c * P + i2)) : make_float2(0.f, 0.f);
+    }
+    float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      const df2 yc = y[c];
+      df_fma(h0, l0, df2{m0[c].x, m0[c].y}, yc);
+      df_fma(h1, l1, df2{m1[c].x, m1[c].y}, yc);
+    }
+    r[i] = df_sub(r[i], df_renorm(h0, l0));
+    if (two) r[i2] = df_sub(r[i2], df_renorm(h1, l1));
+  }
+}
+
+__global__ void __launch_bounds__(kSolveThreads, 1) tail_solve_kernel(TailArgs a0) {
+  const TailArgs a = tail_chain(a0, blockIdx.x);
+  extern __shared__ __align__(16) unsigned char solve_dyn[];
+  df2* const r = reinterpret_cast<df2*>(solve_dyn);  // b, then v, then x
+  __shared__ DTile sD[2];                             // diagonal inverse tiles, double buffered
+  __shared__ df2 s_part[4][NB];
+  __shared__ df2 s_y[NB];
+  const int P = a.P, p = a.p, T = P / NB, tid = threadIdx.x;
+  const df2* const L = static_cast<const df2*>(a.L);
+  const df2* const LT = static_cast<const df2*>(a.LinvT);
+  const df2* const Li = static_cast<const df2*>(a.Linv);
+  for (int i = tid; i < P; i += kSolveThreads) r[i] = i < p ? df_split(a.S[i] * a.xtz[i]) : df2{0.0f, 0.0f};
+  diag_tile_put(sD[0], diag_tile_fetch(Li, P, 0));
+  __syncthreads();
+  // ---- forward: L~ y = b; v = y + s ----
+  for (int k = 0; k < T; ++k) {
+    const df2(*D)[NB + 1] = sD[k & 1];
+    const float4 nxt = k + 1 < T ? diag_tile_fetch(Li, P, k + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < 4 * NB) {  // y_c = sum_{q <= c} (L~_kk^{-1})[c][q] r_q, in four partial sums
+      const int c = tid & 31, q0 = (tid >> 5) * 8;
+      float h = 0.0f, l = 0.0f;
+#pragma unroll
+      for (int q = q0; q < q0 + 8; ++q) df_fma(h, l, D[c][q], r[k * NB + q]);
+      s_part[tid >> 5][c] = df_renorm(h, l);
+    }
+    __syncthreads();
+    if (tid < NB) {
+      const int i = k * NB + tid;
+      const df2 y = df_add(df_add(s_part[0][tid], s_part[1][tid]), df_add(s_part[2][tid], s_part[3][tid]));
+      s_y[tid] = y;
+      r[i] = i < p ? df_split(df_value(y) + a.v[i]) : df2{0.0f, 0.0f};
+    }
+    __syncthreads();
+    // rows below tile k: L~_ik[i][c] is row k*NB + c, column i, of the transposed tiles
+    panel_update(r, LT + (size_t)k * NB * P, P, (k + 1) * NB, P, s_y);
+    if (k + 1 < T) diag_tile_put(sD[(k + 1) & 1], nxt);
+    __syncthreads();
+  }
+  // ---- backward: L~^T x = v (sD[(T-1) & 1] still holds tile T-1) ----
+  for (int k = T - 1; k >= 0; --k) {
+    const df2(*D)[NB + 1] = sD[k & 1];
+    const float4 nxt = k > 0 ? diag_tile_fetch(Li, P, k - 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < 4 * NB) {  // x_c = sum_{q >= c} (L~_kk^{-1})[q][c] r_q
+      const int c = tid & 31, q0 = (tid >> 5) * 8;
+      float h = 0.0f, l = 0.0f;
+#pragma unroll
+      for (int q = q0; q < q0 + 8; ++q) df_fma(h, l, D[q][c], r[k * NB + q]);
+      s_part[tid >> 5][c] = df_renorm(h, l);
+    }
+    __syncthreads();
+    if (tid < NB) {
+      const int i = k * NB + tid;
+      const df2 x = i < p ? df_add(df_add(s_part[0][tid], s_part[1][tid]), df_add(s_part[2][tid], s_part[3][tid]))
+                          : df2{0.0f, 0.0f};
+      s_y[tid] = x;
+      r[i] = x;
+    }
+    __syncthreads();
+    // rows above tile k: L~_kj[c][j] is row k*NB + c, column j, of the factor
+    panel_update(r, L + (size_t)k * NB * P, P, 0, k * NB, s_y);
+    if (k > 0) diag_tile_put(sD[(k - 1) & 1], nxt);
+    __syncthreads();
+  }
+  for (int j = tid; j < p; j += kSolveThreads) {
+    const double bj = a.S[j] * df_value(r[j]);
+    a.beta_new[j] = bj;
+    if (!isfinite(bj) && *(volatile int*)a.err == 0) set_error(a.err, kErrNonFinite);
+  }
+}
+
+// The draws the substitution form needs, apart from the factor: s_j (into v)
+// and nu_j^{-1}.  They depend only on the counters and lambda^{-2}, so they
+// run beside the factorization.  One thread per j, chains on blockIdx.y.
+__global__ void __launch_bounds__(256) tail_noise_kernel(TailArgs a0) {
+  const TailArgs a = tail_chain(a0, blockIdx.y);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.p) return;
+  const uint32_t sweep = (uint32_t)(*a.k_dev + 1);
+  const Rng rng{a.rng.k0, a.rng.k1, a.rng.chain, a.rng.problem};
+  const uint4 w = rng.words((uint32_t)j, sweep, kPurBeta);
+  double u, uc;
+  unit_pair(w.x, w.y, u, uc);
+  a.v[j] = std_normal_from_unit(u, uc);
+  const uint4 wn = rng.words((uint32_t)j, sweep, kPurNu);
+  unit_pair(wn.x, wn.y, u, uc);
+  a.nu_new[j] = -log(u) / (1.0 + a.lam_new[j]);
 }
 
 // Commit (single CTA): xi^{-1}, state, compute-type beta, ring, k.
@@ -1468,6 +1607,8 @@ cudaError_t linalg_prepare() {
                        (const void*)tail_beta_kernel<double>,
                        (const void*)tail_w_kernel<df2>,
                        (const void*)tail_beta_kernel<df2>,
+                       (const void*)tail_solve_kernel,
+                       (const void*)tail_noise_kernel,
                        (const void*)commit_kernel,
                        (const void*)beta_c_kernel,
                        (const void*)wait_timeout_kernel};
@@ -1478,6 +1619,9 @@ cudaError_t linalg_prepare() {
   }
   cudaError_t e = cudaFuncSetAttribute((const void*)step_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kStepPadBytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute((const void*)tail_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kMaxTiles * NB * (int)sizeof(df2));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute((const void*)chol_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kPersistSmem);
@@ -1524,15 +1668,16 @@ size_t chol_sync_words(int P) {
 namespace {
 struct HostIds {
   int T;
+  bool inv;
   std::vector<int> s0;
-  explicit HostIds(int T_) : T(T_), s0(T_ + 1, 0) {
-    for (int k = 0; k < T; ++k) s0[k + 1] = s0[k] + nTasks(T, k);
+  HostIds(int T_, bool inv_) : T(T_), inv(inv_), s0(T_ + 1, 0) {
+    for (int k = 0; k < T; ++k) s0[k + 1] = s0[k] + nTasks(T, k, inv);
   }
   int C(int i, int k) const { return s0[k] + (i - k - 2); }
   int X(int k, int j) const { return s0[k] + nC(T, k) + j; }
   int UA(int i, int j, int k) const {
     const int m = T - k - 1, q = j - k - 1;
-    return s0[k] + nC(T, k) + k + q * m - q * (q - 1) / 2 + (i - j) - 1;
+    return s0[k] + nC(T, k) + (inv ? k : 0) + q * m - q * (q - 1) / 2 + (i - j) - 1;
   }
   int UB(int i, int j, int k) const { return s0[k] + nC(T, k) + k + nUA(T, k) + (i - k - 1) * (k + 1) + j; }
   // kind 0 C, 1 X, 2 UA, 3 UB
@@ -1547,8 +1692,10 @@ struct HostIds {
     const int c = nC(T, k), ua = nUA(T, k);
     if (u < c) { kind = 0; i = k + 2 + u; j = k; return; }
     u -= c;
-    if (u < k) { kind = 1; i = k; j = u; return; }
-    u -= k;
+    if (inv) {
+      if (u < k) { kind = 1; i = k; j = u; return; }
+      u -= k;
+    }
     if (u < ua) {
       const int m = T - k - 1;
       int idx = u + 1, q = 0;
@@ -1561,8 +1708,8 @@ struct HostIds {
 };
 }  // namespace
 
-std::vector<int> chol_task_order(int T, int workers) {
-  const HostIds id(T);
+std::vector<int> chol_task_order(int T, int workers, bool inverse) {
+  const HostIds id(T, inverse);
   const int n = id.s0[T];
   std::vector<int> canonical(n);
   for (int t = 0; t < n; ++t) canonical[t] = t;
@@ -1750,13 +1897,22 @@ cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches) {
 
 cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s, int nchains) {
   const dim3 grid((a.p * 32 + 255) / 256, nchains);
-  if (a.df32) {
+  if (a.solve) {
+    if (!a.df32 || !a.L) return cudaErrorInvalidValue;
+    tail_solve_kernel<<<nchains, kSolveThreads, (size_t)a.P * sizeof(df2), s>>>(a);
+  } else if (a.df32) {
     tail_w_kernel<df2><<<grid, 256, 0, s>>>(a);
     tail_beta_kernel<df2><<<grid, 256, 0, s>>>(a);
   } else {
     tail_w_kernel<double><<<grid, 256, 0, s>>>(a);
     tail_beta_kernel<double><<<grid, 256, 0, s>>>(a);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t tail_noise_enqueue(const TailArgs& a, cudaStream_t s, int nchains) {
+  if (!a.solve) return cudaSuccess;
+  tail_noise_kernel<<<dim3((a.p + 255) / 256, nchains), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -77,6 +77,22 @@ def test_batched_chains_match_oracle(pkg, N, p, K):
         assert_batched_close(got[m], ref, X, st.beta)
 
 
+@pytest.mark.parametrize("N,p,K", [(3001, 200, 5), (4099, 1100, 3)])
+def test_batched_inverse_and_substitution_agree(pkg, N, p, K):
+    """The two ways of applying the factor (explicit inverse products, block
+    substitution) give the same transition up to rounding: z, X^T z and the
+    exact variables identical, beta to 1e-12."""
+    d = problem(N, p, 5, "bf16", seed=p)
+    states = [random_state(p, k=4, seed=200 + m) for m in range(K)]
+    a = _batched_transitions(pkg, d, states, seed=5, beta_solve=pkg.BETA_INVERSE)
+    b = _batched_transitions(pkg, d, states, seed=5, beta_solve=pkg.BETA_SUBST)
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga["z"], gb["z"]) and np.array_equal(ga["xtz"], gb["xtz"])
+        assert np.array_equal(ga["lambda_inv2"], gb["lambda_inv2"]) and ga["tau_inv2"] == gb["tau_inv2"]
+        db = np.linalg.norm(ga["beta"] - gb["beta"]) / np.linalg.norm(ga["beta"])
+        assert db <= 1e-12, db
+
+
 def test_batched_graph_equals_eager_and_chains_differ(pkg):
     d = problem(5000, 300, 5, "bf16", seed=3)
     outs = []

@@ -41,6 +41,18 @@ def test_ragged_shapes_fp64(pkg, N, p, chol):
     assert_transition_close(got, ref, 1e-10)
 
 
+@pytest.mark.parametrize("N,p", [(37, 3), (1001, 33), (5003, 257), (3001, 600), (999, 1100), (2, 1)])
+def test_beta_by_substitution_fp64(pkg, N, p):
+    """beta by block forward and back substitution with the factor (the
+    factorization without the inverse factor), FP64 X: same bar as the
+    explicit-inverse form."""
+    d = problem(N, p, min(3, p), "f64", seed=N + 2 * p)
+    st = random_state(p, k=5, seed=p + 1)
+    got = gpu_transition(pkg, d, st, seed=17, chol_arith=1, chol_sched=pkg.SCHED_SINGLE, beta_solve=pkg.BETA_SUBST)
+    ref = oracle_transition(d, st, seed=17)
+    assert_transition_close(got, ref, 1e-10)
+
+
 @pytest.mark.parametrize("dt,N,p", [("f32", 20003, 200), ("f32", 4099, 1100), ("bf16", 9001, 300),
                                     ("fp8", 7001, 130), ("f32", 3, 2)])
 def test_fp32_accumulation_paths(pkg, dt, N, p):
