@@ -904,6 +904,11 @@ __device__ __forceinline__ void tile_store_cg(df2* M, int P, int ti, int tj, con
 }
 
 // ---- tile work of a 128-thread group ----------------------------------------
+// rows of tile row i inside the p x p matrix (the rest is padding)
+__device__ __forceinline__ int tile_rows(int p, int i) {
+  const int r = p - i * NB;
+  return r < NB ? r : NB;
+}
 // A worker block runs two independent tile tasks at a time, one per group of
 // four warps (warps 0-3 and 4-7), each with its own tiles and named barrier.
 struct Grp {
@@ -967,24 +972,42 @@ __device__ __forceinline__ void gstore_cg(const Grp& g, df2* M, int P, int ti, i
   }
 }
 // C = As Bt (set) or C -= As Bt (sub), Bt[q][c]; thread: rows ty + 8i, columns tx, tx + 16.
+// Rows r >= rows of As are padding past p, zero in every operand the tasks
+// pass here, so their products are zero and are skipped (C keeps those rows,
+// or gets zeros when set).
 template <bool kSub>
-__device__ __forceinline__ void gmma(const Grp& g, df2 (*C)[NB + 1], const df2 (*As)[NB + 1], const df2 (*Bt)[NB + 1]) {
+__device__ __forceinline__ void gmma(const Grp& g, df2 (*C)[NB + 1], const df2 (*As)[NB + 1], const df2 (*Bt)[NB + 1],
+                                     int rows = NB) {
   const int tx = g.t & 15, ty = g.t >> 4;
+  const int ni = rows > ty ? (rows - ty + 7) >> 3 : 0;  // this thread's rows ty + 8i below rows
   float h[4][2], l[4][2];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) h[i][j] = l[i][j] = 0.0f;
+  if (ni >= 4) {
 #pragma unroll 2
-  for (int q = 0; q < NB; ++q) {
-    df2 av[4];
+    for (int q = 0; q < NB; ++q) {
+      df2 av[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) av[i] = As[ty + 8 * i][q];
-    const df2 b0 = Bt[q][tx], b1 = Bt[q][tx + 16];
+      for (int i = 0; i < 4; ++i) av[i] = As[ty + 8 * i][q];
+      const df2 b0 = Bt[q][tx], b1 = Bt[q][tx + 16];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      df_fma(h[i][0], l[i][0], av[i], b0);
-      df_fma(h[i][1], l[i][1], av[i], b1);
+      for (int i = 0; i < 4; ++i) {
+        df_fma(h[i][0], l[i][0], av[i], b0);
+        df_fma(h[i][1], l[i][1], av[i], b1);
+      }
+    }
+  } else {
+    for (int q = 0; q < NB; ++q) {
+      const df2 b0 = Bt[q][tx], b1 = Bt[q][tx + 16];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (i < ni) {
+          const df2 av = As[ty + 8 * i][q];
+          df_fma(h[i][0], l[i][0], av, b0);
+          df_fma(h[i][1], l[i][1], av, b1);
+        }
     }
   }
   g.sync();  // all reads of As/Bt/C done before C is written (C may alias)
@@ -1212,7 +1235,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
           gload_cg<2>(g, t2, P);
         }
         g.sync();
-        gmma<false>(g, gX2, gW, gX1);
+        gmma<false>(g, gX2, gW, gX1, tile_rows(cx.p, i));
         gstore_cg(g, A, P, i, k, gX2, false);
         if (!inv) gstore_cg(g, LinvT, P, k, i, gX2, true);
         gpublish(g, &ps.flagL[i * T + k], e);
@@ -1228,7 +1251,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         const TileRef t2[2] = {{Linv, k, k, false, gX1}, {Linv, k, j, false, gW}};
         gload_cg<2>(g, t2, P);
         g.sync();
-        gmma<false>(g, gX2, gX1, gW);
+        gmma<false>(g, gX2, gX1, gW, tile_rows(cx.p, k));
         gstore_cg(g, Linv, P, k, j, gX2, false);
         gstore_cg(g, LinvT, P, j, k, gX2, true);
         gpublish(g, &ps.flagX[k * T + j], e);
@@ -1258,7 +1281,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
           gload_cg<3>(g, t3, P);
         }
         g.sync();
-        gmma<true>(g, gW, gX1, gX2);
+        gmma<true>(g, gW, gX1, gX2, tile_rows(cx.p, i));
         gstore_cg(g, A, P, i, j, gW, false);
         gpublish(g, &ps.cntA[i * T + j], done_k + 1);
         continue;
@@ -1280,7 +1303,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
           gload_cg<3>(g, t3, P);
         }
         g.sync();
-        gmma<true>(g, gW, gX1, gX2);
+        gmma<true>(g, gW, gX1, gX2, tile_rows(cx.p, i));
         gstore_cg(g, Linv, P, i, j, gW, false);
         gpublish(g, &ps.cntB[i * T + j], base + (unsigned long long)(k - j + 1));
       }
