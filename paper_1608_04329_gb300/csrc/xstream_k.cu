@@ -24,10 +24,11 @@
 // end it writes the partial (p x 32, FP32) and a second kernel sums the
 // partials in a fixed order in FP64.
 //
-// Warp roles (384 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues
-// tcgen05.mma, warp 2 owns the TMEM allocation, warps 4..11 read eta, draw z
+// Warp roles (640 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues
+// tcgen05.mma, warp 2 owns the TMEM allocation, warps 4..19 read eta, draw z
 // and write Z^T: warp w serves TMEM lane quadrant w % 4 (thread = tile row)
-// and chains 16 (w - 4) / 4 .. +15.  Every wait is
+// and chains 8 (w - 4) / 4 .. +7 (four warps per SM sub-partition hide the
+// latency of the draw's dependent arithmetic).  Every wait is
 // bounded (2 s); a wait that runs out sets the timeout bit and all roles wind
 // down through a shared abort flag.
 #include <cuda.h>
@@ -50,7 +51,11 @@ constexpr uint32_t kXChunkBytes = kTR * kCF * 2;      // 16 KB: 128 rows x 64 fe
 constexpr uint32_t kBChunkBytes = 2 * kKc * kCF * 2;  // 8 KB: 64 rows (hi chains, lo chains) x 128 B of B^T
 constexpr uint32_t kStageBytes = kXChunkBytes + kBChunkBytes;  // 24 KB: X chunk, then (pass 1) its B^T chunk
 constexpr uint32_t kZBlock = kKc * 128;               // 4 KB: 32 chains x 64 rows x 2 B
-constexpr int kThreads = 384;  // 4 role warps + 8 epilogue warps
+constexpr int kEpiWarps = 16;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kEpiChains = kKc / (kEpiWarps / 4);  // chains per epilogue warp
+constexpr int kThreads = 128 + kEpiThreads;     // 4 role warps + the epilogue warps
+static_assert(kEpiChains == 8, "the epilogue reads eta with 8-column TMEM loads");
 
 // ---- tcgen05 helpers (shared-memory descriptors, 128-byte swizzle) ---------
 // Descriptor: start address >> 4 in bits 0-13, leading byte offset >> 4 in
@@ -94,6 +99,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
+}
+// 32 lanes x 8 consecutive columns of TMEM into 8 registers per thread.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 // 32 lanes x 16 consecutive columns of TMEM into 16 registers per thread.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -226,9 +237,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh.eta_full[b], 1);
-      mbar_init(&sh.eta_empty[b], 256);
+      mbar_init(&sh.eta_empty[b], kEpiThreads);
     }
-    mbar_init(&sh.z_ready, 256);
+    mbar_init(&sh.z_ready, kEpiThreads);
     mbar_init(&sh.zt_empty, 1);
     mbar_init(&sh.acc_done, 1);
     sh.abort = 0;
@@ -336,19 +347,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     mma_commit(&sh.acc_done);
   } else if (warp >= 4) {
     // ---------------- epilogue: z draws and Z^T ----------------
-    const int quad = warp & 3, half = (warp - 4) >> 2;  // TMEM lane quadrant; chains 16 half .. +15
+    const int quad = warp & 3, part = (warp - 4) >> 2;  // TMEM lane quadrant; chains kEpiChains part ..
     const int er = 32 * quad + lane;                      // row within the tile = TMEM lane
     const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
-    const int m0 = 16 * half;
+    const int m0 = kEpiChains * part;
     const uint32_t sweep = (uint32_t)(*a.k_dev + 1);
     int it = 0;
     for (int64_t t = t0; t < t1; ++t, ++it) {
       const int eb = it & 1;  // eta buffer of this tile
       if (!xk_wait(&sh.eta_full[eb], (it >> 1) & 1, &sh, a.err)) break;
       tc_fence_after();
-      uint32_t hi[16], lo[16];
-      tmem_ld16(tm_eta + 64 * eb + lane_off + m0, hi);
-      tmem_ld16(tm_eta + 64 * eb + lane_off + 32 + m0, lo);
+      uint32_t hi[kEpiChains], lo[kEpiChains];
+      tmem_ld8(tm_eta + 64 * eb + lane_off + m0, hi);
+      tmem_ld8(tm_eta + 64 * eb + lane_off + 32 + m0, lo);
       tmem_ld_wait();
       tc_fence_before();
       mbar_arrive(&sh.eta_empty[eb]);
@@ -359,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!xk_wait(&sh.zt_empty, (it & 1) ^ 1, &sh, a.err)) break;
       const int katom = er >> 6, kr = er & 63;
 #pragma unroll
-      for (int mm = 0; mm < 16; ++mm) {
+      for (int mm = 0; mm < kEpiChains; ++mm) {
         const int m = m0 + mm;
         const float eta = __uint_as_float(hi[mm]) + __uint_as_float(lo[mm]);
         const bool on = active && m < a.K;
@@ -389,10 +400,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
       mbar_arrive(&sh.z_ready);
     }
-    // the CTA's X^T Z partial: row = feature 128 g + er, 32 chains; groups split between the halves
+    // the CTA's X^T Z partial: row = feature 128 g + er, 32 chains; groups split between the parts
     if (xk_wait(&sh.acc_done, 0, &sh, a.err)) {
       tc_fence_after();
-      for (int g = half; g < ngrp; g += 2) {
+      for (int g = part; g < ngrp; g += kEpiWarps / 4) {
         uint32_t r[32];
         tmem_ld32(tm_xtz + 32 * g + lane_off, r);
         tmem_ld_wait();
