@@ -133,7 +133,7 @@ struct CholArgs {
   // P*P and sync_words past the pointers above.
   int nchains;                  // 0 or 1: one chain
   size_t sync_words;
-  const int* order;             // worker task list (chol_task_order), or nullptr: canonical order
+  const int* order;             // worker task list (chol_task_codes), or nullptr: canonical order
   int inverse;                  // single-launch schedule: 1 forms all of L~^{-1}; 0 only its diagonal tiles
 };
 // Enqueues the whole factorization; *launches receives the kernel count.
@@ -148,6 +148,9 @@ int chol_persistent_grid(int device, int nchains = 1);
 // Worker task list of the single-launch factorization for T tiles and about
 // `workers` concurrent task slots (a topological order; see linalg.cu).
 std::vector<int> chol_task_order(int T, int workers, bool inverse);
+// The same list with each entry decoded for the kernel: kind (0 C, 1 X, 2 UA,
+// 3 UB) | k << 2 | i << 10 | j << 18 (T <= 256).
+std::vector<int> chol_task_codes(int T, int workers, bool inverse);
 
 // ---- beta tail, nu/xi, commit ----------------------------------------------
 struct TailArgs {

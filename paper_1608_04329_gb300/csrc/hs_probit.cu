@@ -674,7 +674,7 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
     check(h->alloc(&h->sm_mark, hs::kSmMarks * sizeof(unsigned int)));
     // two task slots per worker block, shared by the chains
     const int slots = 2 * (h->chol_grid - h->K) / h->K;
-    order = hs::chol_task_order(h->T, slots > 1 ? slots : 1, h->chol_inverse);
+    order = hs::chol_task_codes(h->T, slots > 1 ? slots : 1, h->chol_inverse);
     if (!order.empty()) check(h->alloc(&h->chol_order, order.size() * sizeof(int)));
   }
   if (h->K == 1) {

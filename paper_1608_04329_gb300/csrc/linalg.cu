@@ -1210,19 +1210,57 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
       const DFCtx& cx = cv.cx;
       const PSync& ps = cv.ps;
       const int tl = t / nch;
-      const int cid = a.order ? __ldg(a.order + tl) : tl;  // canonical id of the list entry
-      int lo = 0, hi = T - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_step0[mid] <= cid) lo = mid; else hi = mid - 1;
+      int kind, i, j, k;
+      if (a.order) {
+        // list entry, decoded on the host: kind | k << 2 | i << 10 | j << 18
+        const int code = __ldg(a.order + tl);
+        kind = code & 3;
+        k = (code >> 2) & 0xFF;
+        i = (code >> 10) & 0xFF;
+        j = (code >> 18) & 0xFF;
+      } else {
+        // canonical order: step k's C, X, UA, UB tasks from s_step0[k]
+        int lo = 0, hi = T - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_step0[mid] <= tl) lo = mid; else hi = mid - 1;
+        }
+        k = lo;
+        int u = tl - s_step0[k];
+        const int c = nC(T, k), ua = nUA(T, k);
+        if (u < c) {
+          kind = 0;
+          i = k + 2 + u;
+          j = k;
+        } else if (inv && u - c < k) {
+          kind = 1;
+          i = k;
+          j = u - c;
+        } else {
+          u -= c + (inv ? k : 0);
+          if (u < ua) {
+            // the lower triangle of tile rows/cols k+1..T-1, column by column
+            // (column k+1, which feeds the diagonal chain, first), without (k+1, k+1)
+            const int m = T - k - 1;
+            int idx = u + 1, q = 0;
+            while (idx >= m - q) {
+              idx -= m - q;
+              ++q;
+            }
+            kind = 2;
+            j = k + 1 + q;
+            i = j + idx;
+          } else {
+            u -= ua;
+            kind = 3;
+            i = k + 1 + u / (k + 1);
+            j = u % (k + 1);
+          }
+        }
       }
-      const int k = lo;
-      int u = cid - s_step0[k];
       const unsigned long long done_k = base + (unsigned long long)k;  // A tile after updates 0..k-1
-      const int c = nC(T, k), ua = nUA(T, k);
-      if (u < c) {
-        // C(i,k): L_ik = A_ik L_kk^{-T}, i = k + 2 + u
-        const int i = k + 2 + u;
+      if (kind == 0) {
+        // C(i,k): L_ik = A_ik L_kk^{-T}
         const unsigned long long* const wp2[2] = {&ps.flagLi[k], &ps.cntA[i * T + k]};
         const unsigned long long wt2[2] = {e, k >= 1 ? done_k : 0ull};
         if (!gwait<2>(g, wp2, wt2, ps0, e, a.err)) break;
@@ -1241,10 +1279,8 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         gpublish(g, &ps.flagL[i * T + k], e);
         continue;
       }
-      u -= c;
-      if (inv && u < k) {
-        // X(k,j): X_kj = L_kk^{-1} B_kj, j = u; B_kj after its k - j updates
-        const int j = u;
+      if (kind == 1) {
+        // X(k,j): X_kj = L_kk^{-1} B_kj; B_kj after its k - j updates
         const unsigned long long* const wp2[2] = {&ps.flagLi[k], &ps.cntB[k * T + j]};
         const unsigned long long wt2[2] = {e, base + (unsigned long long)(k - j)};
         if (!gwait<2>(g, wp2, wt2, ps0, e, a.err)) break;
@@ -1257,18 +1293,8 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         gpublish(g, &ps.flagX[k * T + j], e);
         continue;
       }
-      if (inv) u -= k;
-      if (u < ua) {
-        // UA(i,j,k): A_ij -= L_ik L_jk^T.  The lower triangle of tile rows/cols
-        // k+1..T-1 is listed column by column (column k+1, which feeds the
-        // diagonal chain, first), without its first entry (k+1, k+1).
-        const int m = T - k - 1;
-        int idx = u + 1, q = 0;
-        while (idx >= m - q) {
-          idx -= m - q;
-          ++q;
-        }
-        const int j = k + 1 + q, i = j + idx;
+      if (kind == 2) {
+        // UA(i,j,k): A_ij -= L_ik L_jk^T
         const unsigned long long* const wp3[3] = {&ps.flagL[i * T + k], &ps.flagL[j * T + k], &ps.cntA[i * T + j]};
         const unsigned long long wt3[3] = {e, e, k >= 1 ? done_k : 0ull};
         if (!gwait<3>(g, wp3, wt3, ps0, e, a.err)) break;
@@ -1286,10 +1312,8 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         gpublish(g, &ps.cntA[i * T + j], done_k + 1);
         continue;
       }
-      u -= ua;
       {
         // UB(i,j,k): B_ij -= L_ik X_kj (X_kk = L_kk^{-1}; B_ik starts at zero)
-        const int i = k + 1 + u / (k + 1), j = u % (k + 1);
         const unsigned long long* const wp3[3] = {&ps.flagL[i * T + k], j < k ? &ps.flagX[k * T + j] : &ps.flagLi[k],
                                                    &ps.cntB[i * T + j]};
         const unsigned long long wt3[3] = {e, e, k > j ? base + (unsigned long long)(k - j) : 0ull};
@@ -1450,10 +1474,20 @@ __device__ __forceinline__ void panel_update(df2* r, const df2* M, int P, int i0
   }
 }
 
+// L2 prefetch of rows [row0, row0 + 32) x columns [col0, col1) of M (128-byte lines; col0 a multiple of 16)
+__device__ __forceinline__ void panel_prefetch(const df2* M, int P, int row0, int col0, int col1) {
+  const int nl = (col1 - col0 + 15) >> 4;
+  for (int e = threadIdx.x; e < NB * nl; e += kSolveThreads) {
+    const df2* ptr = M + (size_t)(row0 + e / nl) * P + col0 + (e % nl) * 16;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+  }
+}
+
 __global__ void __launch_bounds__(kSolveThreads, 1) tail_solve_kernel(TailArgs a0) {
   const TailArgs a = tail_chain(a0, blockIdx.x);
   extern __shared__ __align__(16) unsigned char solve_dyn[];
   df2* const r = reinterpret_cast<df2*>(solve_dyn);  // b, then v, then x
+  double* const sv = reinterpret_cast<double*>(r + a0.P);  // s (the noise), rows < p
   __shared__ DTile sD[2];                             // diagonal inverse tiles, double buffered
   __shared__ df2 s_part[4][NB];
   __shared__ df2 s_y[NB];
@@ -1461,13 +1495,20 @@ __global__ void __launch_bounds__(kSolveThreads, 1) tail_solve_kernel(TailArgs a
   const df2* const L = static_cast<const df2*>(a.L);
   const df2* const LT = static_cast<const df2*>(a.LinvT);
   const df2* const Li = static_cast<const df2*>(a.Linv);
-  for (int i = tid; i < P; i += kSolveThreads) r[i] = i < p ? df_split(a.S[i] * a.xtz[i]) : df2{0.0f, 0.0f};
+  for (int i = tid; i < P; i += kSolveThreads) {
+    r[i] = i < p ? df_split(a.S[i] * a.xtz[i]) : df2{0.0f, 0.0f};
+    sv[i] = i < p ? a.v[i] : 0.0;
+  }
   diag_tile_put(sD[0], diag_tile_fetch(Li, P, 0));
+  if (T > 1) panel_prefetch(LT, P, NB, 2 * NB, P);
   __syncthreads();
   // ---- forward: L~ y = b; v = y + s ----
   for (int k = 0; k < T; ++k) {
     const df2(*D)[NB + 1] = sD[k & 1];
     const float4 nxt = k + 1 < T ? diag_tile_fetch(Li, P, k + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    // panels two steps ahead into L2 (the backward pass's first two at the end)
+    if (k + 2 < T) panel_prefetch(LT, P, (k + 2) * NB, (k + 3) * NB, P);
+    else if (k + 2 - T < 2 && T - 1 - (k + 2 - T) >= 1) panel_prefetch(L, P, (2 * T - 3 - k) * NB, 0, (2 * T - 3 - k) * NB);
     if (tid < 4 * NB) {  // y_c = sum_{q <= c} (L~_kk^{-1})[c][q] r_q, in four partial sums
       const int c = tid & 31, q0 = (tid >> 5) * 8;
       float h = 0.0f, l = 0.0f;
@@ -1480,7 +1521,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) tail_solve_kernel(TailArgs a
       const int i = k * NB + tid;
       const df2 y = df_add(df_add(s_part[0][tid], s_part[1][tid]), df_add(s_part[2][tid], s_part[3][tid]));
       s_y[tid] = y;
-      r[i] = i < p ? df_split(df_value(y) + a.v[i]) : df2{0.0f, 0.0f};
+      r[i] = i < p ? df_split(df_value(y) + sv[i]) : df2{0.0f, 0.0f};
     }
     __syncthreads();
     // rows below tile k: L~_ik[i][c] is row k*NB + c, column i, of the transposed tiles
@@ -1492,6 +1533,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) tail_solve_kernel(TailArgs a
   for (int k = T - 1; k >= 0; --k) {
     const df2(*D)[NB + 1] = sD[k & 1];
     const float4 nxt = k > 0 ? diag_tile_fetch(Li, P, k - 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k >= 3) panel_prefetch(L, P, (k - 2) * NB, 0, (k - 2) * NB);
     if (tid < 4 * NB) {  // x_c = sum_{q >= c} (L~_kk^{-1})[q][c] r_q
       const int c = tid & 31, q0 = (tid >> 5) * 8;
       float h = 0.0f, l = 0.0f;
@@ -1644,7 +1686,7 @@ cudaError_t linalg_prepare() {
                                        kStepPadBytes);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute((const void*)tail_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kMaxTiles * NB * (int)sizeof(df2));
+                           kMaxTiles * NB * (int)(sizeof(df2) + sizeof(double)));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute((const void*)chol_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kPersistSmem);
@@ -1864,6 +1906,17 @@ std::vector<int> chol_task_order(int T, int workers, bool inverse) {
   return out;
 }
 
+std::vector<int> chol_task_codes(int T, int workers, bool inverse) {
+  const HostIds id(T, inverse);
+  std::vector<int> order = chol_task_order(T, workers, inverse);
+  for (int& t : order) {
+    int kind, i, j, k;
+    id.decode(t, kind, i, j, k);
+    t = kind | (k << 2) | (i << 10) | (j << 18);
+  }
+  return order;
+}
+
 int chol_launch_count(int P, int arith, int persistent_grid) {
   const int T = P / NB;
   if (arith == HS_CHOL_DF32) return persistent_grid > 0 ? 1 : T;
@@ -1922,7 +1975,7 @@ cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s, int nchains) {
   const dim3 grid((a.p * 32 + 255) / 256, nchains);
   if (a.solve) {
     if (!a.df32 || !a.L) return cudaErrorInvalidValue;
-    tail_solve_kernel<<<nchains, kSolveThreads, (size_t)a.P * sizeof(df2), s>>>(a);
+    tail_solve_kernel<<<nchains, kSolveThreads, (size_t)a.P * (sizeof(df2) + sizeof(double)), s>>>(a);
   } else if (a.df32) {
     tail_w_kernel<df2><<<grid, 256, 0, s>>>(a);
     tail_beta_kernel<df2><<<grid, 256, 0, s>>>(a);

@@ -445,14 +445,26 @@ __global__ void bsw_prep_kernel(const double* __restrict__ beta, int64_t beta_st
 }
 
 // X^T z of chain m, feature j: fixed-order FP64 sum over the CTAs' partials.
+// Thread (j, m): lanes run over the 32 chains of one feature, so each CTA's
+// partial row is read as one 128-byte line; four accumulators (CTA index
+// mod 4) are added in a fixed order at the end.
 __global__ void reduce_k_kernel(const float* __restrict__ part, int grid, int fpad, int p, int K,
                                 double* __restrict__ xtz, int64_t xtz_stride) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= p * K) return;
-  const int m = e / p, j = e % p;
-  double s = 0.0;
-  for (int c = 0; c < grid; ++c) s += (double)part[((size_t)c * fpad + j) * kKc + m];
-  xtz[(int64_t)m * xtz_stride + j] = s;
+  const int j = e / kKc, m = e % kKc;
+  if (j >= p) return;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const float* col = part + (size_t)j * kKc + m;
+  const size_t cs = (size_t)fpad * kKc;
+  int c = 0;
+  for (; c + 3 < grid; c += 4) {
+    s0 += (double)__ldg(col + (size_t)c * cs);
+    s1 += (double)__ldg(col + (size_t)(c + 1) * cs);
+    s2 += (double)__ldg(col + (size_t)(c + 2) * cs);
+    s3 += (double)__ldg(col + (size_t)(c + 3) * cs);
+  }
+  for (; c < grid; ++c) s0 += (double)__ldg(col + (size_t)c * cs);
+  if (m < K) xtz[(int64_t)m * xtz_stride + j] = (s0 + s1) + (s2 + s3);
 }
 
 }  // namespace
@@ -527,7 +539,7 @@ cudaError_t xstream_k_enqueue(const void* map, const XKArgs& a, const double* be
 }
 
 cudaError_t xstream_k_reduce(const XKArgs& a, int grid, double* xtz, int64_t xtz_stride, cudaStream_t s) {
-  reduce_k_kernel<<<(a.p * a.K + 255) / 256, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, xtz, xtz_stride);
+  reduce_k_kernel<<<(a.p * kKc + 255) / 256, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, xtz, xtz_stride);
   return cudaGetLastError();
 }
 
