@@ -238,12 +238,30 @@ def run_k_chains(args, wk, pkg, torch, dist, ws, rank, local, chol, one_chain_va
                  "traffic": None, "peak_source": peak_kind,
                  "kernel": "xstream_k (B prep + tensor-core X-stream)", "avg_launch_ms": kavg,
                  "tensor_tflops": 4.0 * wk["N"] * 1024 * 2 * 32 / (kavg / 1e3) / 1e12}
+    # the K factorizations on the CUDA cores: FP32-pair FMAs against the FP32 issue bound
+    kc_ms, kc_n = kgroups["cholesky"]
+    kchol = None
+    if kc_n > 0:
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                mhz, mhz_src = float(json.load(f)["sm_max_mhz"]), "measured"
+        except (OSError, KeyError, ValueError):
+            mhz, mhz_src = 2070.0, "nominal"
+        alu_peak = sms * 128 * mhz * 1e6 / 12.0 / 1e12
+        cavg = kc_ms / kc_n
+        cach = args.k_chains * float(wk["p"]) ** 3 / 6.0 / (cavg / 1e3) / 1e12
+        kchol = {"bound": "alu", "achieved": cach, "peak": alu_peak, "unit": "Tpair-FMA/s", "frac": cach / alu_peak,
+                 "traffic": None, "kernel": "chol_persistent_kernel (K chains, factor only)", "avg_launch_ms": cavg,
+                 "work": "K p^3/6 FP32-pair FMAs per sweep",
+                 "peak_source": f"SMs x 128 FP32 lanes x {mhz_src} max SM clock / 12 FP32 instructions per pair-FMA"}
     kvalue = ws * args.k_chains * args.k_steps / (kms / 1e3)
     return {"value": kvalue, "unit": "chain-sweeps/s", "K": args.k_chains, "x_dtype": "bf16",
             "steps": args.k_steps, "warmup": 3, "ms_per_sweep": kms / args.k_steps,
             "vs_one_chain_fp32": (kvalue / one_chain_value) if one_chain_value else None,
             "kernel_ms_per_sweep": {g: (v[0] / max(v[1], 1)) for g, v in kgroups.items()},
-            "gpu_launches_per_sweep": klaunches, "roofline": kroof, "clocks": clk.summary(),
+            "gpu_launches_per_sweep": klaunches, "roofline": kroof, "factorization_roofline": kchol,
+            "clocks": clk.summary(),
             "workload": wk["name"]}
 
 

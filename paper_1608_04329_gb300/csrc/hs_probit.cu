@@ -61,7 +61,7 @@ struct hs_probit {
   hs::RngKey rng{};
   cudaStream_t s0 = nullptr, s1 = nullptr;
   bool own_s0 = false;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_shrink = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_shrink = nullptr, ev_xs = nullptr;
   std::vector<void*> allocs;
 
   void* X = nullptr;
@@ -328,19 +328,28 @@ cudaError_t enqueue_sweep(hs_probit* h) {
     if ((e = hs::shrink_launch(shrink_args(h, 0), h->s1, h->K)) != cudaSuccess) return e;
   }
   if (!h->chol_inverse && (e = cudaEventRecord(h->ev_shrink, h->s1)) != cudaSuccess) return e;
-  {
-    ProfSpan sp(h, 3, h->s1);
-    if (h->K > 1 && h->chol_grid > 0) {
-      // every chain's factorization in one launch
-      hs::CholArgs ca = chol_args(h, 0);
-      ca.nchains = h->K;
-      if ((e = hs::chol_enqueue(ca, h->s1, nullptr)) != cudaSuccess) return e;
-    } else {
-      for (int m = 0; m < h->K; ++m)
-        if ((e = hs::chol_enqueue(chol_args(h, m), h->s1, nullptr)) != cudaSuccess) return e;
+  // One chain: the factorization runs beside the X-stream (its blocks are
+  // small enough to share the SMs).  Several chains on the single-launch
+  // schedule: both fill the GPU, so the factorization follows the X-stream
+  // explicitly (same total time, and each group's events time only itself).
+  const bool after_xstream = h->K > 1 && h->chol_grid > 0;
+  auto factorize = [&]() -> cudaError_t {
+    cudaError_t ee;
+    {
+      ProfSpan sp(h, 3, h->s1);
+      if (after_xstream) {
+        // every chain's factorization in one launch
+        hs::CholArgs ca = chol_args(h, 0);
+        ca.nchains = h->K;
+        if ((ee = hs::chol_enqueue(ca, h->s1, nullptr)) != cudaSuccess) return ee;
+      } else {
+        for (int m = 0; m < h->K; ++m)
+          if ((ee = hs::chol_enqueue(chol_args(h, m), h->s1, nullptr)) != cudaSuccess) return ee;
+      }
     }
-  }
-  if ((e = cudaEventRecord(h->ev_join, h->s1)) != cudaSuccess) return e;
+    return cudaEventRecord(h->ev_join, h->s1);
+  };
+  if (!after_xstream && (e = factorize()) != cudaSuccess) return e;
   if (h->K == 1) {
     {
       ProfSpan sp(h, 0, h->s0);
@@ -368,6 +377,11 @@ cudaError_t enqueue_sweep(hs_probit* h) {
     // the substitution form's s and nu draws need lambda^{-2} only: beside the factorization
     if ((e = cudaStreamWaitEvent(h->s0, h->ev_shrink, 0)) != cudaSuccess) return e;
     if ((e = hs::tail_noise_enqueue(tail_args(h, 0), h->s0, h->K)) != cudaSuccess) return e;
+  }
+  if (after_xstream) {
+    if ((e = cudaEventRecord(h->ev_xs, h->s0)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->s1, h->ev_xs, 0)) != cudaSuccess) return e;
+    if ((e = factorize()) != cudaSuccess) return e;
   }
   if ((e = cudaStreamWaitEvent(h->s0, h->ev_join, 0)) != cudaSuccess) return e;
   {
@@ -466,6 +480,7 @@ void destroy(hs_probit* h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_shrink) cudaEventDestroy(h->ev_shrink);
+  if (h->ev_xs) cudaEventDestroy(h->ev_xs);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->h_k) cudaFreeHost(h->h_k);
@@ -635,6 +650,7 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
   check(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   check(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   check(cudaEventCreateWithFlags(&h->ev_shrink, cudaEventDisableTiming));
+  check(cudaEventCreateWithFlags(&h->ev_xs, cudaEventDisableTiming));
   const size_t P2 = (size_t)h->P * h->P;
   const size_t pd = (size_t)p * sizeof(double);
   const size_t K = (size_t)h->K;

@@ -115,12 +115,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 // FP32 uniform pair from two Philox words: u = (2m + 1) 2^-53 and 1 - u with
-// m = (hi << 20) | (lo >> 12), each converted once from its exact integer.
+// m = (hi << 20) | (lo >> 12).  With m = hi 2^20 + l (l < 2^20),
+// u = hi 2^-32 + (2l + 1) 2^-53: the second term is exact in FP32 and one FMA
+// adds it to the rounded first, so u is within an ulp of (2m + 1) 2^-53
+// (exactly rounded when hi < 2^24) using 32-bit conversions only; 1 - u is
+// the same with the complemented words (2^52 - 1 - m = ~hi 2^20 + (2^20 - 1 - l)).
 __device__ __forceinline__ void unit_pair_f(uint32_t hi, uint32_t lo, float& u, float& uc) {
-  const unsigned long long m = ((unsigned long long)hi << 20) | (unsigned long long)(lo >> 12);
-  const unsigned long long mc = ((1ull << 52) - 1ull) - m;
-  u = __ull2float_rn(2ull * m + 1ull) * 0x1p-53f;
-  uc = __ull2float_rn(2ull * mc + 1ull) * 0x1p-53f;
+  const uint32_t l = lo >> 12;
+  u = fmaf(__uint2float_rn(2u * l + 1u), 0x1p-53f, __uint2float_rn(hi) * 0x1p-32f);
+  uc = fmaf(__uint2float_rn(2u * (0xFFFFFu - l) + 1u), 0x1p-53f, __uint2float_rn(~hi) * 0x1p-32f);
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -291,6 +294,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- MMA issuer ----------------
     const uint32_t id_eta = idesc_bf16(kTR, 2 * kKc, 0, 0);   // M 128 rows, N 64 (hi, lo), both K-major
     const uint32_t id_xtz = idesc_bf16(128, kKc, 1, 0);       // M 128 features (MN-major A), N 32 chains
+    // Descriptors are built once: moving a descriptor by b bytes adds b >> 4 to
+    // its address field (shared addresses stay below 256 KB, so it cannot carry).
+    // This warp shares its sub-partition with four epilogue warps, so every
+    // instruction it saves shortens the issue loop.
+    const uint64_t dX0 = sw128_desc(smem_u32(sX), 16, 1024);                  // pass 1: X chunk of stage 0
+    const uint64_t dB0 = sw128_desc(smem_u32(sX) + kXChunkBytes, 16, 1024);   // pass 1: B^T chunk of stage 0
+    const uint64_t dA0 = sw128_desc(smem_u32(sX), kStageBytes, 1024);         // pass 2: X pair from stage 0
+    uint64_t dZ[2][8];                                                         // pass 2: Z part hl, rows 16 kk ..
+#pragma unroll
+    for (int hl = 0; hl < 2; ++hl)
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk)
+        dZ[hl][kk] = sw128_desc(smem_u32(sZ + (size_t)(hl * 2 + kk / 4) * kZBlock) + (kk % 4) * 32, 16, 1024);
+    constexpr uint64_t kStageStep = kStageBytes >> 4;
     bool ok = true;
     uint32_t q = 0;
     // pass 1 of tile number n (within this CTA) into eta buffer n % 2
@@ -302,12 +319,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = q % kXStages;
         if (!xk_wait(&sh.full[s], (q / kXStages) & 1, &sh, a.err)) return false;
         tc_fence_after();
-        const uint32_t xa = smem_u32(sX + (size_t)s * kStageBytes);
-        const uint32_t ba = xa + kXChunkBytes;
+        const uint64_t dx = dX0 + kStageStep * s, db = dB0 + kStageStep * s;
 #pragma unroll
         for (int kk = 0; kk < kCF / 16; ++kk)
-          mma_bf16(tm_eta + 64 * b, sw128_desc(xa + kk * 32, 16, 1024), sw128_desc(ba + kk * 32, 16, 1024), id_eta,
-                   (c > 0 || kk > 0) ? 1 : 0);
+          mma_bf16(tm_eta + 64 * b, dx + 2 * kk, db + 2 * kk, id_eta, (c > 0 || kk > 0) ? 1 : 0);
         mma_commit(&sh.empty[s]);
       }
       mma_commit(&sh.eta_full[b]);
@@ -326,16 +341,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!(ok = xk_wait(&sh.full[s0], (q / kXStages) & 1, &sh, a.err))) break;
         if (!(ok = xk_wait(&sh.full[s0 + 1], ((q + 1) / kXStages) & 1, &sh, a.err))) break;
         tc_fence_after();
-        const uint32_t xa = smem_u32(sX + (size_t)s0 * kStageBytes);
+        const uint64_t da = dA0 + kStageStep * s0;
+        const int acc0 = it > 0 ? 1 : 0;
 #pragma unroll
         for (int kk = 0; kk < kTR / 16; ++kk) {
-          const uint64_t ad = sw128_desc(xa + kk * 2048, kStageBytes, 1024);  // rows 16kk.., features of both stages
-          // (the second 64-feature atom of A is the next stage's X chunk, kStageBytes further)
-#pragma unroll
-          for (int hl = 0; hl < 2; ++hl) {
-            const uint32_t za = smem_u32(sZ + (size_t)(hl * 2 + kk / 4) * kZBlock) + (kk % 4) * 32;
-            mma_bf16(tm_xtz + 32 * g, ad, sw128_desc(za, 16, 1024), id_xtz, (it > 0 || kk > 0 || hl > 0) ? 1 : 0);
-          }
+          // rows 16kk.., features of both stages (the second 64-feature atom of A
+          // is the next stage's X chunk, kStageBytes further)
+          const uint64_t ad = da + 128 * kk;
+          mma_bf16(tm_xtz + 32 * g, ad, dZ[0][kk], id_xtz, kk > 0 ? 1 : acc0);
+          mma_bf16(tm_xtz + 32 * g, ad, dZ[1][kk], id_xtz, 1);
         }
         mma_commit(&sh.empty[s0]);
         mma_commit(&sh.empty[s0 + 1]);
@@ -353,8 +367,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int m0 = kEpiChains * part;
     const uint32_t sweep = (uint32_t)(*a.k_dev + 1);
     int it = 0;
+    // y of this thread's row, one tile ahead (its load latency off the draw's path)
+    int y_next = (t0 < t1 && t0 * kTR + er < a.N) ? a.y[t0 * kTR + er] : 1;
     for (int64_t t = t0; t < t1; ++t, ++it) {
       const int eb = it & 1;  // eta buffer of this tile
+      const int yi_t = y_next;
+      if (t + 1 < t1 && (t + 1) * kTR + er < a.N) y_next = a.y[(t + 1) * kTR + er];
       if (!xk_wait(&sh.eta_full[eb], (it >> 1) & 1, &sh, a.err)) break;
       tc_fence_after();
       uint32_t hi[kEpiChains], lo[kEpiChains];
@@ -365,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(&sh.eta_empty[eb]);
       const int64_t i = t * kTR + er;
       const bool active = i < a.N;
-      const int yi = active ? a.y[i] : 1;
+      const int yi = active ? yi_t : 1;
       // Z^T (both parts) for pass 2, once pass 2 of the previous tile is done with it
       if (!xk_wait(&sh.zt_empty, (it & 1) ^ 1, &sh, a.err)) break;
       const int katom = er >> 6, kr = er & 63;
