@@ -1010,7 +1010,8 @@ __device__ __forceinline__ void gmma(const Grp& g, df2 (*C)[NB + 1], const df2 (
         }
     }
   }
-  g.sync();  // all reads of As/Bt/C done before C is written (C may alias)
+  // C is neither As nor Bt, and each thread reads and writes only its own
+  // entries of C, so no barrier is needed before the writes
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -1020,6 +1021,56 @@ __device__ __forceinline__ void gmma(const Grp& g, df2 (*C)[NB + 1], const df2 (
       dst = kSub ? df_sub(dst, v) : v;
     }
   g.sync();
+}
+// The trailing update A_ij -= L_ik L_jk^T of a UA task, with both factor
+// tiles as loaded (not transposed: Ls[c][q] is read along a row, which with
+// the 33-pair row stride touches 16 distinct bank pairs per half-warp) and
+// the result stored from registers straight to tile (ti, tj) of M: no
+// barrier between the products and the store, and W (the tile's old value,
+// read only by its owner thread) is never written in shared memory.
+// Thread: rows ty + 8i, columns tx, tx + 16; rows >= rows are padding.
+__device__ __forceinline__ void gmma_update_store(const Grp& g, const df2 (*W)[NB + 1], const df2 (*As)[NB + 1],
+                                                  const df2 (*Bs)[NB + 1], int rows, df2* M, int P, int ti, int tj) {
+  const int tx = g.t & 15, ty = g.t >> 4;
+  const int ni = rows > ty ? (rows - ty + 7) >> 3 : 0;
+  float h[4][2], l[4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) h[i][j] = l[i][j] = 0.0f;
+  if (ni >= 4) {
+#pragma unroll 2
+    for (int q = 0; q < NB; ++q) {
+      df2 av[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[ty + 8 * i][q];
+      const df2 b0 = Bs[tx][q], b1 = Bs[tx + 16][q];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        df_fma(h[i][0], l[i][0], av[i], b0);
+        df_fma(h[i][1], l[i][1], av[i], b1);
+      }
+    }
+  } else {
+    for (int q = 0; q < NB; ++q) {
+      const df2 b0 = Bs[tx][q], b1 = Bs[tx + 16][q];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (i < ni) {
+          const df2 av = As[ty + 8 * i][q];
+          df_fma(h[i][0], l[i][0], av, b0);
+          df_fma(h[i][1], l[i][1], av, b1);
+        }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = ty + 8 * i, c = tx + 16 * j;
+      const df2 v = df_sub(W[r][c], df_renorm(h[i][j], l[i][j]));
+      __stcg(reinterpret_cast<float2*>(M + (size_t)(ti * NB + r) * P + tj * NB + c), make_float2(v.hi, v.lo));
+    }
 }
 // Thread 0 of the group waits for every *p[n] >= target[n] (one relaxed read of
 // all, then an acquire fence); bounded as block_wait.
@@ -1300,15 +1351,14 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         if (!gwait<3>(g, wp3, wt3, ps0, e, a.err)) break;
         if (k == 0) {
           gload_gram(g, gW, cx, i, j);
-          const TileRef t2[2] = {{A, i, k, false, gX1}, {A, j, k, true, gX2}};
+          const TileRef t2[2] = {{A, i, k, false, gX1}, {A, j, k, false, gX2}};
           gload_cg<2>(g, t2, P);
         } else {
-          const TileRef t3[3] = {{A, i, j, false, gW}, {A, i, k, false, gX1}, {A, j, k, true, gX2}};
+          const TileRef t3[3] = {{A, i, j, false, gW}, {A, i, k, false, gX1}, {A, j, k, false, gX2}};
           gload_cg<3>(g, t3, P);
         }
         g.sync();
-        gmma<true>(g, gW, gX1, gX2, tile_rows(cx.p, i));
-        gstore_cg(g, A, P, i, j, gW, false);
+        gmma_update_store(g, gW, gX1, gX2, tile_rows(cx.p, i), A, P, i, j);
         gpublish(g, &ps.cntA[i * T + j], done_k + 1);
         continue;
       }
