@@ -265,6 +265,37 @@ def run_k_chains(args, wk, pkg, torch, dist, ws, rank, local, chol, one_chain_va
             "workload": wk["name"]}
 
 
+def run_tn_compare(d, pkg, torch, local, reps=20):
+    """The latent draw alone, both samplers, on this workload's mu* = y* x_i beta_true
+    (N draws): time per launch (CUDA events), proposals per draw, and how long a
+    warp runs for its slowest lane (mean over warps of the max attempts / mean)."""
+    X = torch.from_numpy(d["X"]).to(f"cuda:{local}")
+    bt = torch.from_numpy(d["beta_true"]).to(device=X.device, dtype=X.dtype)
+    ys = torch.from_numpy(d["y"]).to(X.device).to(X.dtype) * 2.0 - 1.0
+    mu = (ys * (X @ bt)).float().contiguous()
+    del X
+    out = {"workload": "mu* = y* x_i beta_true of the benchmark data (N draws), FP32, one thread per draw"}
+    for name, meth in (("inverse_cdf", pkg.TN_INVCDF), ("rejection", pkg.TN_REJECTION)):
+        for _ in range(3):
+            z, t = pkg.tn_sample(mu, seed=0, sweep=1, method=meth)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for r in range(reps):
+            z, t = pkg.tn_sample(mu, seed=0, sweep=1 + r, method=meth)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        tt = t.double()
+        n = tt.numel() // 32 * 32
+        warp_max = tt[:n].view(-1, 32).max(dim=1).values.mean().item()
+        out[name] = {"ms_per_launch": ms, "draws_per_s": mu.numel() / (ms / 1e3), "mean_attempts": tt.mean().item(),
+                     "warp_wait_factor": warp_max / tt[:n].mean().item()}
+    out["rejection_over_inverse_cdf_time"] = out["rejection"]["ms_per_launch"] / out["inverse_cdf"]["ms_per_launch"]
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -283,6 +314,7 @@ def main(argv=None):
     ap.add_argument("--k-chains", type=int, default=32,
                     help="also time the batched form: K chains on BF16 X (0: skip)")
     ap.add_argument("--k-steps", type=int, default=20)
+    ap.add_argument("--no-tn", action="store_true", help="skip the standalone sampler comparison")
     args = ap.parse_args(argv)
     wl = WORKLOADS[args.workload]
     dist, rank, ws, local = _dist()
@@ -378,6 +410,10 @@ def main(argv=None):
     if args.k_chains > 1:
         kch = run_k_chains(args, WORKLOADS["c2"], pkg, torch, dist, ws, rank, local, chol, value)
 
+    tnc = None
+    if rank == 0 and not args.no_tn:
+        tnc = run_tn_compare(d, pkg, torch, local)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, done, t, t_gram = cpu_oracle_rate(d, wl, n_sweeps=args.cpu_sweeps)
@@ -399,7 +435,7 @@ def main(argv=None):
                 "clocks": clk.summary(),
                 "kernel_ms_per_sweep": {g: (v[0] / max(v[1], 1)) for g, v in groups.items()},
                 "hbm_roofline_frac_whole_sweep": (bytes_per_launch / (ms / args.steps / 1e3) / 1e9) / 8000.0,
-                "k_chains": kch}
+                "k_chains": kch, "tn_samplers": tnc}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

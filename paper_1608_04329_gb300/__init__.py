@@ -23,12 +23,14 @@ import numpy as np
 
 __all__ = ["HSProbit", "HSProbitError", "load_library", "library_path", "STATUS",
            "X_F64", "X_F32", "X_BF16", "X_FP8E4M3", "CHOL_F64", "CHOL_DF32",
-           "SCHED_AUTO", "SCHED_COLUMNS", "SCHED_SINGLE", "BETA_AUTO", "BETA_INVERSE", "BETA_SUBST"]
+           "SCHED_AUTO", "SCHED_COLUMNS", "SCHED_SINGLE", "BETA_AUTO", "BETA_INVERSE", "BETA_SUBST",
+           "TN_INVCDF", "TN_REJECTION", "tn_sample"]
 
 X_F64, X_F32, X_BF16, X_FP8E4M3 = 0, 1, 2, 3
 CHOL_F64, CHOL_DF32 = 0, 1
 SCHED_AUTO, SCHED_COLUMNS, SCHED_SINGLE = 0, 1, 2
 BETA_AUTO, BETA_INVERSE, BETA_SUBST = 0, 1, 2
+TN_INVCDF, TN_REJECTION = 0, 1
 STATUS = {0: "HS_OK", -1: "HS_EINVAL", -2: "HS_ENOMEM", -3: "HS_ECUDA", -4: "HS_ENOTPD",
           -5: "HS_ENONFINITE", -6: "HS_ETIMEOUT", -7: "HS_ESTATE", -8: "HS_EUNSUPPORTED"}
 KERNEL_GROUPS = {"xstream": 0, "reduce": 1, "shrink": 2, "cholesky": 3, "tail": 4, "gram": 5}
@@ -96,6 +98,8 @@ _PROTOS = {
     "hs_probit_debug_z_chain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "hs_probit_debug_xtz_chain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "hs_probit_free": (None, [ctypes.c_void_p]),
+    "hs_tn_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                    ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "hs_probit_xstream_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
@@ -306,3 +310,25 @@ class HSProbit:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def tn_sample(mu, seed: int = 0, sweep: int = 1, method: int = TN_INVCDF, chain: int = 0, stream=None):
+    """z+ ~ N(mu, 1) restricted to (0, inf) for a CUDA float32 tensor mu, by the
+    inverse CDF or the paper's rejection sampler (``hs_tn_sample``); returns
+    (z, attempts) as CUDA tensors, enqueued on ``stream`` (a torch stream or a
+    raw handle; default: torch's current stream)."""
+    import torch
+    if not (hasattr(mu, "is_cuda") and mu.is_cuda and mu.dtype == torch.float32):
+        raise HSProbitError(-1, "tn_sample: mu must be a CUDA float32 tensor")
+    mu = mu.contiguous()
+    z = torch.empty_like(mu)
+    tries = torch.empty(mu.shape, dtype=torch.int32, device=mu.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(mu.device)
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    st = load_library().hs_tn_sample(ctypes.c_void_p(mu.data_ptr()), mu.numel(), ctypes.c_uint64(seed & (2**64 - 1)),
+                                     chain, sweep, method, ctypes.c_void_p(z.data_ptr()),
+                                     ctypes.c_void_p(tries.data_ptr()), ctypes.c_void_p(handle))
+    if st != 0:
+        raise HSProbitError(st, "hs_tn_sample")
+    return z, tries

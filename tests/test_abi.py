@@ -88,3 +88,12 @@ def test_noalloc_rejects_bad_arguments_on_host(lib):
     assert lib.hs_probit_xstream_noalloc(1, ctypes.c_void_p(16), 5, ctypes.c_void_p(16), 10, 5,
                                          ctypes.c_void_p(16), None, 0, 0, 0, 1, ctypes.c_void_p(16), None,
                                          None) == -1
+
+
+def test_tn_sample_rejects_bad_arguments_on_host(lib):
+    # nothing is launched for these: n < 0, NULL arrays with n > 0, unknown method, chain id too large
+    assert lib.hs_tn_sample(None, -1, 0, 0, 1, 0, None, None, None) == -1
+    assert lib.hs_tn_sample(None, 5, 0, 0, 1, 0, None, None, None) == -1
+    assert lib.hs_tn_sample(None, 0, 0, 0, 1, 7, None, None, None) == -1
+    assert lib.hs_tn_sample(None, 0, 0, 1 << 24, 1, 0, None, None, None) == -1
+    assert lib.hs_tn_sample(None, 0, 0, 0, 1, 1, None, None, None) == 0  # empty input: nothing to do
