@@ -1484,132 +1484,138 @@ __global__ void __launch_bounds__(256) tail_beta_kernel(TailArgs a0) {
 //   b = S X^T z;  L~ y = b:    y_k = L~_kk^{-1} (b_k - sum_{j<k} L~_kj y_j)
 //   v = y + s;    L~^T x = v:  x_k = L~_kk^{-T} (v_k - sum_{i>k} L~_ik^T x_i)
 //   beta = S x   (s and the nu_j^{-1} draws: tail_noise_kernel, earlier).
-// One block per chain (blockIdx.x), FP32 pairs.  The right-hand side lives in
-// shared memory and is updated column-panel by column-panel right after each
-// diagonal tile is solved; the panel reads are coalesced (forward through the
-// transposed factor tiles, backward through the factor's own rows).  Rows
-// past p (padding) carry zero.  blockDim.x must be kSolveThreads.
-constexpr int kSolveThreads = 512;
-__device__ __forceinline__ float4 diag_tile_fetch(const df2* Li, int P, int k) {
-  const int rr = threadIdx.x >> 4, cc = (threadIdx.x & 15) * 2;
-  return __ldg(reinterpret_cast<const float4*>(Li + (size_t)(k * NB + rr) * P + k * NB + cc));
+// One thread-block cluster of kSolveCTAs blocks per chain, FP32 pairs.  Block
+// c of the cluster owns the tile rows t with t % kSolveCTAs == c and keeps
+// their part of the right-hand side in its shared memory.  Step k: the owner
+// of tile k solves the diagonal tile (y_k or x_k), writes the 32 values into
+// every block's shared memory (distributed shared memory) and the cluster
+// synchronizes; then every block updates its own rows below (forward,
+// reading the transposed factor tiles) or above (backward, the factor's own
+// rows) with coalesced reads.  The value buffer alternates between two slots
+// by step, so one cluster barrier per step suffices.  Rows past p (padding)
+// carry zero.  blockDim.x must be kSolveThreads.
+constexpr int kSolveCTAs = 4;
+constexpr int kSolveThreads = 256;
+constexpr int kSolveMaxRows = (kMaxTiles + kSolveCTAs - 1) / kSolveCTAs * NB;  // rows a block can own
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
 }
-__device__ __forceinline__ void diag_tile_put(df2 (*D)[NB + 1], float4 v) {
-  const int rr = threadIdx.x >> 4, cc = (threadIdx.x & 15) * 2;
-  D[rr][cc] = df2{v.x, v.y};
-  D[rr][cc + 1] = df2{v.z, v.w};
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-// r_i -= sum_c M[c][i] y_c for i in [i0, i1), M rows P apart (one panel of 32
-// rows).  Two rows per thread and pass, all 64 loads issued before the sums,
-// so that each pass pays one memory latency.
-__device__ __forceinline__ void panel_update(df2* r, const df2* M, int P, int i0, int i1, const df2* y) {
-  for (int i = i0 + (int)threadIdx.x; i < i1; i += 2 * kSolveThreads) {
-    const int i2 = i + kSolveThreads;
-    const bool two = i2 < i1;
-    float2 m0[NB], m1[NB];
+// *local_ptr in block `cta` of this cluster = v
+__device__ __forceinline__ void st_cluster_df2(df2* local_ptr, uint32_t cta, df2 v) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(local_ptr)), "r"(cta));
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(ra), "f"(v.hi), "f"(v.lo) : "memory");
+}
+// the diagonal tile inverse of tile k: two 16-byte pieces per thread
+__device__ __forceinline__ void diag_tile_fetch2(const df2* Li, int P, int k, float4 (&v)[2]) {
 #pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      m0[c] = __ldg(reinterpret_cast<const float2*>(M + (size_t)c * P + i));
-      m1[c] = two ? __ldg(reinterpret_cast<const float2*>(M + (size_t)c * P + i2)) : make_float2(0.f, 0.f);
-    }
-    float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+  for (int h = 0; h < 2; ++h) {
+    const int e = threadIdx.x + h * kSolveThreads, rr = e >> 4, cc = (e & 15) * 2;
+    v[h] = __ldg(reinterpret_cast<const float4*>(Li + (size_t)(k * NB + rr) * P + k * NB + cc));
+  }
+}
+__device__ __forceinline__ void diag_tile_put2(df2 (*D)[NB + 1], const float4 (&v)[2]) {
 #pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      const df2 yc = y[c];
-      df_fma(h0, l0, df2{m0[c].x, m0[c].y}, yc);
-      df_fma(h1, l1, df2{m1[c].x, m1[c].y}, yc);
-    }
-    r[i] = df_sub(r[i], df_renorm(h0, l0));
-    if (two) r[i2] = df_sub(r[i2], df_renorm(h1, l1));
+  for (int h = 0; h < 2; ++h) {
+    const int e = threadIdx.x + h * kSolveThreads, rr = e >> 4, cc = (e & 15) * 2;
+    D[rr][cc] = df2{v[h].x, v[h].y};
+    D[rr][cc + 1] = df2{v[h].z, v[h].w};
   }
 }
 
-// L2 prefetch of rows [row0, row0 + 32) x columns [col0, col1) of M (128-byte lines; col0 a multiple of 16)
-__device__ __forceinline__ void panel_prefetch(const df2* M, int P, int row0, int col0, int col1) {
-  const int nl = (col1 - col0 + 15) >> 4;
-  for (int e = threadIdx.x; e < NB * nl; e += kSolveThreads) {
-    const df2* ptr = M + (size_t)(row0 + e / nl) * P + col0 + (e % nl) * 16;
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
-  }
-}
-
-__global__ void __launch_bounds__(kSolveThreads, 1) tail_solve_kernel(TailArgs a0) {
-  const TailArgs a = tail_chain(a0, blockIdx.x);
-  extern __shared__ __align__(16) unsigned char solve_dyn[];
-  df2* const r = reinterpret_cast<df2*>(solve_dyn);  // b, then v, then x
-  double* const sv = reinterpret_cast<double*>(r + a0.P);  // s (the noise), rows < p
-  __shared__ DTile sD[2];                             // diagonal inverse tiles, double buffered
+__global__ void __cluster_dims__(kSolveCTAs, 1, 1) __launch_bounds__(kSolveThreads, 1)
+    tail_solve_kernel(TailArgs a0) {
+  const TailArgs a = tail_chain(a0, blockIdx.x / kSolveCTAs);
+  __shared__ df2 r[kSolveMaxRows];       // this block's rows: b, then v, then x
+  __shared__ double sv[kSolveMaxRows];   // s (the noise) of this block's rows
+  __shared__ DTile sD;                   // diagonal inverse tile of the step this block owns
   __shared__ df2 s_part[4][NB];
-  __shared__ df2 s_y[NB];
+  __shared__ df2 s_val[2][NB];           // the solved tile of a step (written by its owner)
   const int P = a.P, p = a.p, T = P / NB, tid = threadIdx.x;
+  const int rank = (int)cluster_ctarank();
+  const int nt = T > rank ? (T - rank + kSolveCTAs - 1) / kSolveCTAs : 0;  // tiles this block owns
   const df2* const L = static_cast<const df2*>(a.L);
   const df2* const LT = static_cast<const df2*>(a.LinvT);
   const df2* const Li = static_cast<const df2*>(a.Linv);
-  for (int i = tid; i < P; i += kSolveThreads) {
-    r[i] = i < p ? df_split(a.S[i] * a.xtz[i]) : df2{0.0f, 0.0f};
-    sv[i] = i < p ? a.v[i] : 0.0;
+  // local row lr <-> tile rank + kSolveCTAs (lr / NB), row lr % NB
+  auto grow = [&](int lr) { return (rank + kSolveCTAs * (lr / NB)) * NB + (lr % NB); };
+  for (int lr = tid; lr < nt * NB; lr += kSolveThreads) {
+    const int i = grow(lr);
+    r[lr] = i < p ? df_split(a.S[i] * a.xtz[i]) : df2{0.0f, 0.0f};
+    sv[lr] = i < p ? a.v[i] : 0.0;
   }
-  diag_tile_put(sD[0], diag_tile_fetch(Li, P, 0));
-  if (T > 1) panel_prefetch(LT, P, NB, 2 * NB, P);
-  __syncthreads();
-  // ---- forward: L~ y = b; v = y + s ----
-  for (int k = 0; k < T; ++k) {
-    const df2(*D)[NB + 1] = sD[k & 1];
-    const float4 nxt = k + 1 < T ? diag_tile_fetch(Li, P, k + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-    // panels two steps ahead into L2 (the backward pass's first two at the end)
-    if (k + 2 < T) panel_prefetch(LT, P, (k + 2) * NB, (k + 3) * NB, P);
-    else if (k + 2 - T < 2 && T - 1 - (k + 2 - T) >= 1) panel_prefetch(L, P, (2 * T - 3 - k) * NB, 0, (2 * T - 3 - k) * NB);
-    if (tid < 4 * NB) {  // y_c = sum_{q <= c} (L~_kk^{-1})[c][q] r_q, in four partial sums
-      const int c = tid & 31, q0 = (tid >> 5) * 8;
-      float h = 0.0f, l = 0.0f;
+  // step st = 0 .. 2T-1: forward tile k = st, then backward tile k = 2T-1-st
+  auto tile_of = [&](int st) { return st < T ? st : 2 * T - 1 - st; };
+  auto next_owned = [&](int st) {
+    for (int s2 = st; s2 < 2 * T; ++s2)
+      if (tile_of(s2) % kSolveCTAs == rank) return s2;
+    return 2 * T;
+  };
+  float4 nxt[2];
+  int nst = next_owned(0);
+  if (nst < 2 * T) diag_tile_fetch2(Li, P, tile_of(nst), nxt);
+  cluster_sync_all();  // every block of the cluster runs before any remote write
+  for (int st = 0; st < 2 * T; ++st) {
+    const bool fwd = st < T;
+    const int k = tile_of(st), buf = st & 1;
+    if (k % kSolveCTAs == rank) {
+      // the owner solves the diagonal tile from its rows of tile k
+      diag_tile_put2(sD, nxt);
+      nst = next_owned(st + 1);
+      if (nst < 2 * T) diag_tile_fetch2(Li, P, tile_of(nst), nxt);
+      __syncthreads();
+      const int lt = k / kSolveCTAs;
+      if (tid < 4 * NB) {
+        const int c = tid & 31, q0 = (tid >> 5) * 8;
+        float h = 0.0f, l = 0.0f;
 #pragma unroll
-      for (int q = q0; q < q0 + 8; ++q) df_fma(h, l, D[c][q], r[k * NB + q]);
-      s_part[tid >> 5][c] = df_renorm(h, l);
-    }
-    __syncthreads();
-    if (tid < NB) {
-      const int i = k * NB + tid;
-      const df2 y = df_add(df_add(s_part[0][tid], s_part[1][tid]), df_add(s_part[2][tid], s_part[3][tid]));
-      s_y[tid] = y;
-      r[i] = i < p ? df_split(df_value(y) + sv[i]) : df2{0.0f, 0.0f};
-    }
-    __syncthreads();
-    // rows below tile k: L~_ik[i][c] is row k*NB + c, column i, of the transposed tiles
-    panel_update(r, LT + (size_t)k * NB * P, P, (k + 1) * NB, P, s_y);
-    if (k + 1 < T) diag_tile_put(sD[(k + 1) & 1], nxt);
-    __syncthreads();
-  }
-  // ---- backward: L~^T x = v (sD[(T-1) & 1] still holds tile T-1) ----
-  for (int k = T - 1; k >= 0; --k) {
-    const df2(*D)[NB + 1] = sD[k & 1];
-    const float4 nxt = k > 0 ? diag_tile_fetch(Li, P, k - 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-    if (k >= 3) panel_prefetch(L, P, (k - 2) * NB, 0, (k - 2) * NB);
-    if (tid < 4 * NB) {  // x_c = sum_{q >= c} (L~_kk^{-1})[q][c] r_q
-      const int c = tid & 31, q0 = (tid >> 5) * 8;
-      float h = 0.0f, l = 0.0f;
+        for (int q = q0; q < q0 + 8; ++q)
+          df_fma(h, l, fwd ? sD[c][q] : sD[q][c], r[lt * NB + q]);  // L~_kk^{-1} or its transpose
+        s_part[tid >> 5][c] = df_renorm(h, l);
+      }
+      __syncthreads();
+      if (tid < NB) {
+        const int i = k * NB + tid;
+        df2 y = df_add(df_add(s_part[0][tid], s_part[1][tid]), df_add(s_part[2][tid], s_part[3][tid]));
+        if (i >= p) y = df2{0.0f, 0.0f};
+        // forward: the rows of tile k become v = y + s; backward: x
+        r[lt * NB + tid] = fwd ? (i < p ? df_split(df_value(y) + sv[lt * NB + tid]) : df2{0.0f, 0.0f}) : y;
 #pragma unroll
-      for (int q = q0; q < q0 + 8; ++q) df_fma(h, l, D[q][c], r[k * NB + q]);
-      s_part[tid >> 5][c] = df_renorm(h, l);
+        for (int c = 0; c < kSolveCTAs; ++c) st_cluster_df2(&s_val[buf][tid], (uint32_t)c, y);
+      }
+    }
+    cluster_sync_all();
+    // this block's rows below tile k (forward) or above it (backward)
+    const df2* const M = (fwd ? LT : L) + (size_t)k * NB * P;
+    for (int lr = tid; lr < nt * NB; lr += kSolveThreads) {
+      const int t = rank + kSolveCTAs * (lr / NB);
+      if (fwd ? t <= k : t >= k) continue;
+      const int i = t * NB + (lr % NB);
+      float hh = 0.0f, ll = 0.0f;
+      float2 m[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) m[c] = __ldg(reinterpret_cast<const float2*>(M + (size_t)c * P + i));
+#pragma unroll
+      for (int c = 0; c < NB; ++c) df_fma(hh, ll, df2{m[c].x, m[c].y}, s_val[buf][c]);
+      r[lr] = df_sub(r[lr], df_renorm(hh, ll));
     }
     __syncthreads();
-    if (tid < NB) {
-      const int i = k * NB + tid;
-      const df2 x = i < p ? df_add(df_add(s_part[0][tid], s_part[1][tid]), df_add(s_part[2][tid], s_part[3][tid]))
-                          : df2{0.0f, 0.0f};
-      s_y[tid] = x;
-      r[i] = x;
+  }
+  for (int lr = tid; lr < nt * NB; lr += kSolveThreads) {
+    const int i = grow(lr);
+    if (i < p) {
+      const double bj = a.S[i] * df_value(r[lr]);
+      a.beta_new[i] = bj;
+      if (!isfinite(bj) && *(volatile int*)a.err == 0) set_error(a.err, kErrNonFinite);
     }
-    __syncthreads();
-    // rows above tile k: L~_kj[c][j] is row k*NB + c, column j, of the factor
-    panel_update(r, L + (size_t)k * NB * P, P, 0, k * NB, s_y);
-    if (k > 0) diag_tile_put(sD[(k - 1) & 1], nxt);
-    __syncthreads();
   }
-  for (int j = tid; j < p; j += kSolveThreads) {
-    const double bj = a.S[j] * df_value(r[j]);
-    a.beta_new[j] = bj;
-    if (!isfinite(bj) && *(volatile int*)a.err == 0) set_error(a.err, kErrNonFinite);
-  }
+  cluster_sync_all();  // no block leaves while another may still write into it
 }
 
 // The draws the substitution form needs, apart from the factor: s_j (into v)
@@ -1734,9 +1740,6 @@ cudaError_t linalg_prepare() {
   }
   cudaError_t e = cudaFuncSetAttribute((const void*)step_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kStepPadBytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute((const void*)tail_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kMaxTiles * NB * (int)(sizeof(df2) + sizeof(double)));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute((const void*)chol_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kPersistSmem);
@@ -2025,7 +2028,8 @@ cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s, int nchains) {
   const dim3 grid((a.p * 32 + 255) / 256, nchains);
   if (a.solve) {
     if (!a.df32 || !a.L) return cudaErrorInvalidValue;
-    tail_solve_kernel<<<nchains, kSolveThreads, (size_t)a.P * (sizeof(df2) + sizeof(double)), s>>>(a);
+    if (a.P > kMaxTiles * NB) return cudaErrorInvalidValue;
+    tail_solve_kernel<<<nchains * kSolveCTAs, kSolveThreads, 0, s>>>(a);
   } else if (a.df32) {
     tail_w_kernel<df2><<<grid, 256, 0, s>>>(a);
     tail_beta_kernel<df2><<<grid, 256, 0, s>>>(a);
