@@ -105,3 +105,15 @@ def test_gram_matches_definition(pkg):
     ref = X.T @ X
     assert np.abs(G - ref).max() <= 1e-12 * np.abs(ref).max()
     assert np.array_equal(G, G.T)
+
+
+def test_fp8_correlated_design_large_p(pkg):
+    """The shape of the large correlated workload at a size the oracle runs in
+    seconds: FP8 e4m3 X with per-column scales, rows from the AR(1) Toeplitz
+    design (rho = 0.5), p = 4000 (125 tiles), 20 nonzeros of magnitude
+    U[0.5, 2]; FP32 accumulation tolerance."""
+    d = problem(20000, 4000, 20, "fp8", seed=4, mag=(0.5, 2.0), design="ar1")
+    st = random_state(4000, k=6, seed=8, scale=0.05)
+    got = gpu_transition(pkg, d, st, seed=41, chol_arith=1)
+    ref = oracle_transition(d, st, seed=41)
+    assert_transition_close(got, ref, 1e-4)
