@@ -43,6 +43,9 @@ WORKLOADS = {
                name="horseshoe-probit sweep of K chains, N=1e6, p=1000, X iid N(0,1) bf16, 10 nonzeros U[1,3]"),
     "c2s": dict(N=200_000, p=1000, nz=10, dt="bf16",
                 name="horseshoe-probit sweep of K chains, N=2e5, p=1000, X iid N(0,1) bf16 (profiling case, 400 MB)"),
+    "c4": dict(N=4_000_000, p=4000, nz=20, dt="fp8", design="ar1", mag=(0.5, 2.0),
+               name="horseshoe-probit sweep, N=4e6, p=4000, X rows N(0, Toeplitz 0.5^|i-j|) fp8 e4m3 with column "
+                    "scales (16 GB), 20 nonzeros U[0.5,2], 1 chain"),
 }
 XSTREAM_SOURCES = ["paper_1608_04329_gb300/csrc/xstream.cu", "paper_1608_04329_gb300/csrc/hs_common.cuh"]
 
@@ -162,7 +165,8 @@ def _traffic(workload: str):
 
 def make_data(wl):
     import hs_synth
-    return hs_synth.make_problem(wl["N"], wl["p"], wl["nz"], wl["dt"], seed=0)
+    return hs_synth.make_problem(wl["N"], wl["p"], wl["nz"], wl["dt"], seed=0, design=wl.get("design", "iid"),
+                                 mag=wl.get("mag", (1.0, 3.0)))
 
 
 def cpu_oracle_rate(d, wl, n_sweeps: int, budget_s: float = 30.0):
@@ -344,7 +348,7 @@ def main(argv=None):
             dist.destroy_process_group()
         return 0
     d = make_data(wl)
-    s = pkg.HSProbit(d["X"], d["y"], seed=0, chain=rank, device=local, use_graph=bool(args.graph),
+    s = pkg.HSProbit(d["X"], d["y"], seed=0, chain=rank, device=local, use_graph=bool(args.graph), scales=d["scales"],
                      chol_arith=chol, ring_size=max(args.steps + args.warmup, 16))
     stream = torch.cuda.ExternalStream(s.stream(), device=local)
     s.sweep(args.warmup)
@@ -391,7 +395,8 @@ def main(argv=None):
         barrier(dist)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2 = pkg.HSProbit(Xh, yh, seed=1, chain=rank, device=local, use_graph=bool(args.graph), chol_arith=chol)
+        s2 = pkg.HSProbit(Xh, yh, seed=1, chain=rank, device=local, use_graph=bool(args.graph), chol_arith=chol,
+                          scales=d["scales"])
         d2h = 0
         for _ in range(args.steps):
             s2.sweep(1)
@@ -411,7 +416,7 @@ def main(argv=None):
         kch = run_k_chains(args, WORKLOADS["c2"], pkg, torch, dist, ws, rank, local, chol, value)
 
     tnc = None
-    if rank == 0 and not args.no_tn:
+    if rank == 0 and not args.no_tn and wl["dt"] in ("f32", "f64"):
         tnc = run_tn_compare(d, pkg, torch, local)
 
     cpu = None
@@ -428,7 +433,7 @@ def main(argv=None):
                 "data": "synthetic",
                 "config": {"workload": wl["name"], "N": wl["N"], "p": wl["p"], "x_dtype": wl["dt"],
                            "chains_per_gpu": 1, "cholesky": args.chol, "graph": bool(args.graph),
-                           "l2": "inputs larger than L2 (X 4 GB), no flush",
+                           "l2": f"inputs larger than L2 (X {d['X'].nbytes / 1e9:.1f} GB), no flush",
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches,
