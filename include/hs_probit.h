@@ -71,8 +71,8 @@ extern "C" {
 /* ---- how beta is drawn from the factor -----------------------------------
  * beta = S L~^{-T} (L~^{-1} S X^T z + s) either way (Sect. 5, beta update);
  * the two forms round differently (agreement to about 1e-12 relative). */
-#define HS_BETA_AUTO     0  /* HS_BETA_SUBST for several chains on the single-launch
-                                schedule, else HS_BETA_INVERSE */
+#define HS_BETA_AUTO     0  /* HS_BETA_SUBST on the single-launch schedule for several
+                                chains or p > 2016, else HS_BETA_INVERSE */
 #define HS_BETA_INVERSE  1  /* the factorization also forms L~^{-1}; beta by two
                                 parallel matrix-vector products */
 #define HS_BETA_SUBST    2  /* factor only (half the tile products); beta by block

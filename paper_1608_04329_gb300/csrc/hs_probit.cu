@@ -638,8 +638,11 @@ hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, cons
     fail(HS_EUNSUPPORTED);
     return nullptr;
   }
+  // AUTO: the factorization is throughput-bound for several chains or a large p
+  // (measured: one chain at p = 4000, N = 5e5: 65 -> 108 sweeps/s with substitution;
+  // at p = 1000 its diagonal chain bounds it and the inverse products win)
   h->chol_inverse = !(h->chol_grid > 0 && (cfg.beta_solve == HS_BETA_SUBST ||
-                                          (cfg.beta_solve == HS_BETA_AUTO && h->K > 1)));
+                                          (cfg.beta_solve == HS_BETA_AUTO && (h->K > 1 || h->T >= 64))));
   if (cfg.stream) {
     h->s0 = static_cast<cudaStream_t>(cfg.stream);
   } else {

@@ -44,7 +44,8 @@ def test_single_launch_factorization_equals_column_launches(pkg, N, p, graph):
     one-launch-per-block-column schedule, so whole chains agree bit for bit."""
     d = problem(N, p, min(4, p), "f32", seed=p)
     a = pkg.HSProbit(d["X"], d["y"], seed=5, use_graph=graph, chol_sched=pkg.SCHED_COLUMNS)
-    b = pkg.HSProbit(d["X"], d["y"], seed=5, use_graph=graph, chol_sched=pkg.SCHED_SINGLE)
+    b = pkg.HSProbit(d["X"], d["y"], seed=5, use_graph=graph, chol_sched=pkg.SCHED_SINGLE,
+                     beta_solve=pkg.BETA_INVERSE)  # the same beta form as the column schedule
     assert a.launches_per_sweep() - b.launches_per_sweep() == (p + 31) // 32 - 1
     a.sweep(4)
     b.sweep(4)
