@@ -9,16 +9,18 @@
 //  chol     A = X^T X + tau^{-2} Lambda^{-2} (Eq. 12 and the definition of Sigma
 //           after it; Sect. 5, beta update, steps ii and iii).  The factor is
 //           taken of the equilibrated matrix A~ = S A S, S = diag(A)^{-1/2},
-//           by a right-looking blocked Cholesky over 32 x 32 tiles, and the
-//           same sweep over the tiles forms L~^{-1} by block forward
-//           substitution on the identity.  L = S^{-1} L~, so
+//           by a right-looking blocked Cholesky over 32 x 32 tiles, and (one
+//           chain, moderate p) the same sweep over the tiles forms L~^{-1} by
+//           block forward substitution on the identity.  L = S^{-1} L~, so
 //           L^{-1} = L~^{-1} S.
 //  tail     w = L^{-1} X^T z, s_j = Phi^{-1}(u_j), beta = L^{-T}(w + s)
 //           (Sect. 5, beta update, steps iv to viii, with the transposes read
 //           so that Cov(beta) = A^{-1}), as two parallel products with the
-//           explicit inverse factor; nu_j^{-1} ~ Exp(1 + lambda_j^{-2}) and
-//           xi^{-1} ~ Exp(1 + tau^{-2}) (Eq. 12, third and sixth lines); and
-//           the commit of the new state, skipped when the error word is set.
+//           explicit inverse factor, or (several chains, large p) by block
+//           forward and back substitution with the factor itself;
+//           nu_j^{-1} ~ Exp(1 + lambda_j^{-2}) and xi^{-1} ~ Exp(1 + tau^{-2})
+//           (Eq. 12, third and sixth lines); and the commit of the new state,
+//           skipped when the error word is set.
 #include <algorithm>
 #include <queue>
 #include <vector>
