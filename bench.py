@@ -48,6 +48,7 @@ WORKLOADS = {
                     "scales (16 GB), 20 nonzeros U[0.5,2], 1 chain"),
 }
 XSTREAM_SOURCES = ["paper_1608_04329_gb300/csrc/xstream.cu", "paper_1608_04329_gb300/csrc/hs_common.cuh"]
+XSTREAM_K_SOURCES = ["paper_1608_04329_gb300/csrc/xstream_k.cu", "paper_1608_04329_gb300/csrc/hs_common.cuh"]
 
 
 def _dist():
@@ -145,17 +146,17 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _traffic(workload: str):
+def _traffic(workload: str, record: str = "xstream_traffic.json", sources=XSTREAM_SOURCES):
     """DRAM bytes per X-stream launch from the committed ncu summary, or None
     when the kernel sources changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "xstream_traffic.json")
+    path = os.path.join(ROOT, "profiles", record)
     try:
         with open(path) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
     h = hashlib.sha256()
-    for s in XSTREAM_SOURCES:
+    for s in sources:
         with open(os.path.join(ROOT, s), "rb") as f:
             h.update(f.read())
     if rec.get("sources_sha256") != h.hexdigest() or rec.get("workload") != workload:
@@ -239,7 +240,8 @@ def run_k_chains(args, wk, pkg, torch, dist, ws, rank, local, chol, one_chain_va
         kavg = kx_ms / kx_n
         kach = kbytes / (kavg / 1e3) / 1e9
         kroof = {"bound": "hbm", "achieved": kach, "peak": peak, "unit": "GB/s", "frac": kach / peak,
-                 "traffic": None, "peak_source": peak_kind,
+                 "traffic": _traffic("c2" if wk["N"] == WORKLOADS["c2"]["N"] else "c2s", "xstream_k_traffic.json",
+                                     XSTREAM_K_SOURCES), "peak_source": peak_kind,
                  "kernel": "xstream_k (B prep + tensor-core X-stream)", "avg_launch_ms": kavg,
                  "tensor_tflops": 4.0 * wk["N"] * 1024 * 2 * 32 / (kavg / 1e3) / 1e12}
     # the K factorizations on the CUDA cores: FP32-pair FMAs against the FP32 issue bound
