@@ -232,6 +232,18 @@ int hs_probit_xstream_noalloc(int x_dtype, const void* X, int64_t ld, const uint
                               uint32_t chain, uint32_t problem, int64_t sweep, double* xtz, double* z,
                               void* stream);
 
+/* The worker task list of the single-launch factorization for T tiles of 32
+ * (host only; no CUDA call): the order the kernel hands out its tile tasks,
+ * one code per task, kind | k << 2 | i << 10 | j << 18 with kind 0 = C(i,k)
+ * (L_ik = A_ik L_kk^{-T}), 1 = X(k,j) (X_kj = L_kk^{-1} B_kj), 2 = UA(i,j,k)
+ * (A_ij -= L_ik L_jk^T), 3 = UB(i,j,k) (B_ij -= L_ik X_kj); inverse = 0 lists
+ * the factor-only form (kinds 0 and 2).  The list is a topological order of
+ * the task graph, found by a list schedule for `workers` concurrent tasks.
+ * Writes min(count, max_codes) codes to the caller's array and returns the
+ * count, or HS_EINVAL (T outside 1..256, workers < 1, inverse not 0 or 1,
+ * max_codes < 0, codes NULL with max_codes > 0). */
+int64_t hs_chol_task_list(int32_t T, int32_t workers, int32_t inverse, int32_t* codes, int64_t max_codes);
+
 /* ---- K chains on one X (Sect. 5 sweep for each chain; batched form) --------
  * A handle made with cfg.num_chains = K > 1 runs K independent chains on the
  * same BF16 X.  Chain m uses chain id cfg.chain + m in its Philox counters, so

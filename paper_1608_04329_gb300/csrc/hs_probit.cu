@@ -981,6 +981,16 @@ int64_t hs_probit_launches_per_sweep(const hs_probit* h) {
   return h->launches;
 }
 
+int64_t hs_chol_task_list(int32_t T, int32_t workers, int32_t inverse, int32_t* codes, int64_t max_codes) {
+  if (T < 1 || T > 256 || workers < 1 || (inverse != 0 && inverse != 1) || max_codes < 0 ||
+      (max_codes > 0 && !codes))
+    return HS_EINVAL;
+  const std::vector<int> list = hs::chol_task_codes(T, workers, inverse != 0);
+  const int64_t n = (int64_t)list.size();
+  for (int64_t t = 0; t < n && t < max_codes; ++t) codes[t] = list[(size_t)t];
+  return n;
+}
+
 int hs_probit_debug_wait_timeout(hs_probit* h, int64_t max_spins) {
   if (!h || max_spins < 0) return HS_EINVAL;
   DeviceGuard dg(h->device);

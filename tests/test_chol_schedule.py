@@ -1,0 +1,91 @@
+"""Host logic of the single-launch factorization (no GPU): the worker task
+list the library hands to the kernel (hs_chol_task_list).  It must hold every
+tile task of the blocked factorization exactly once (with and without the
+inverse factor), and list each task after the worker tasks it reads, which is
+what makes the kernel's bounded waits free of deadlock: a task waits only on
+earlier list entries or on the diagonal chain.
+
+Tasks of step k (tile size 32, T tiles): C(i,k) L_ik = A_ik L_kk^{-T} for
+i >= k+2 (the chain forms L_{k+1,k}); UA(i,j,k) A_ij -= L_ik L_jk^T for
+k < j <= i except (k+1, k+1) (the chain applies that one); with the inverse
+factor also X(k,j) = L_kk^{-1} B_kj for j < k and UB(i,j,k) B_ij -= L_ik X_kj
+for i > k, j <= k.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1608_04329_gb300 import _build
+    import paper_1608_04329_gb300 as pkg
+    _build.build()
+    return pkg.load_library()
+
+
+def _tasks(T, inv):
+    out = set()
+    for k in range(T):
+        out |= {(0, i, k, k) for i in range(k + 2, T)}
+        out |= {(2, i, j, k) for j in range(k + 1, T) for i in range(j, T) if not (i == j == k + 1)}
+        if inv:
+            out |= {(1, k, j, k) for j in range(k)}
+            out |= {(3, i, j, k) for i in range(k + 1, T) for j in range(k + 1)}
+    return out
+
+
+def _deps(task):
+    kind, i, j, k = task
+    d = []
+    if kind == 0:
+        if k >= 1:
+            d.append((2, i, k, k - 1))
+    elif kind == 1:
+        if k >= 1:
+            d.append((3, k, j, k - 1))
+    elif kind == 2:
+        if i >= k + 2:
+            d.append((0, i, k, k))
+        if j >= k + 2 and j != i:
+            d.append((0, j, k, k))
+        if k >= 1:
+            d.append((2, i, j, k - 1))
+    else:
+        if i >= k + 2:
+            d.append((0, i, k, k))
+        if j < k:
+            d.append((1, k, j, k))
+        if k > j:
+            d.append((3, i, j, k - 1))
+    return d
+
+
+@pytest.mark.parametrize("inv", [0, 1])
+@pytest.mark.parametrize("T", [1, 2, 3, 4, 7, 16, 32, 40])
+@pytest.mark.parametrize("workers", [1, 7, 300])
+def test_task_list_is_complete_and_topological(lib, T, inv, workers):
+    n = lib.hs_chol_task_list(T, workers, inv, None, 0)
+    want = _tasks(T, inv)
+    assert n == len(want)
+    codes = np.zeros(max(n, 1), dtype=np.int32)
+    assert lib.hs_chol_task_list(T, workers, inv, codes.ctypes.data, n) == n
+    got = []
+    for c in codes[:n].tolist():
+        kind, k, i, j = c & 3, (c >> 2) & 0xFF, (c >> 10) & 0xFF, (c >> 18) & 0xFF
+        got.append((kind, i, j, k) if kind in (1, 2, 3) else (kind, i, k, k))
+    assert len(set(got)) == n and set(got) == want
+    pos = {t: p for p, t in enumerate(got)}
+    for t in got:
+        for d in _deps(t):
+            assert d in pos, (t, d)
+            assert pos[d] < pos[t], (t, d)
+
+
+def test_task_list_rejects_bad_arguments(lib):
+    assert lib.hs_chol_task_list(0, 4, 1, None, 0) == -1
+    assert lib.hs_chol_task_list(257, 4, 1, None, 0) == -1
+    assert lib.hs_chol_task_list(8, 0, 1, None, 0) == -1
+    assert lib.hs_chol_task_list(8, 4, 2, None, 0) == -1
+    assert lib.hs_chol_task_list(8, 4, 1, None, 5) == -1
