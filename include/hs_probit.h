@@ -48,7 +48,7 @@ extern "C" {
 #define HS_ENONFINITE   -5  /* a non-finite value appeared in X beta, z or beta */
 #define HS_ETIMEOUT     -6  /* a bounded device wait ran out */
 #define HS_ESTATE       -7  /* handle is in an error state; call set_state */
-#define HS_EUNSUPPORTED -8  /* option not supported by this build */
+#define HS_EUNSUPPORTED -8  /* option not supported on this device or with these settings */
 
 /* ---- storage type of X -------------------------------------------------- */
 #define HS_X_F64      0  /* double; the sweep computes X beta and X^T z in FP64 */
