@@ -97,3 +97,23 @@ def test_tn_sample_rejects_bad_arguments_on_host(lib):
     assert lib.hs_tn_sample(None, 0, 0, 0, 1, 7, None, None, None) == -1
     assert lib.hs_tn_sample(None, 0, 0, 1 << 24, 1, 0, None, None, None) == -1
     assert lib.hs_tn_sample(None, 0, 0, 0, 1, 1, None, None, None) == 0  # empty input: nothing to do
+
+
+@pytest.mark.parametrize("field,value,dtype,p,status", [
+    ("num_chains", 33, "bf16", 64, -1),      # more than 32 chains
+    ("num_chains", -1, "bf16", 64, -1),
+    ("num_chains", 4, "f32", 64, -8),        # the batched form needs BF16 X
+    ("num_chains", 4, "bf16", 1537, -8),     # and p <= 1536 (TMEM columns)
+    ("beta_solve", 3, "f32", 64, -1),        # unknown beta form
+    ("chol_sched", 3, "f32", 64, -1),        # unknown schedule
+])
+def test_init_rejects_bad_config_on_host(lib, field, value, dtype, p, status):
+    import paper_1608_04329_gb300 as pkg
+    cfg = pkg._Config()
+    lib.hs_probit_config_default(ctypes.byref(cfg))
+    cfg.x_dtype = {"f32": pkg.X_F32, "bf16": pkg.X_BF16}[dtype]
+    setattr(cfg, field, value)
+    X = np.zeros((4, p), dtype=np.float32 if dtype == "f32" else np.uint16)
+    y = np.zeros(4, dtype=np.uint8)
+    assert not lib.hs_probit_init_ex(ctypes.byref(cfg), X.ctypes.data, y.ctypes.data, 4, p, 0)
+    assert lib.hs_probit_last_error() == status
