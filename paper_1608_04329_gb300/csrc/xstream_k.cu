@@ -387,6 +387,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       // Z^T (both parts) for pass 2, once pass 2 of the previous tile is done with it
       if (!xk_wait(&sh.zt_empty, (it & 1) ^ 1, &sh, a.err)) break;
       const int katom = er >> 6, kr = er & 63;
+      if (m0 >= a.K) {
+        // every chain of this warp is padding (K < 32): zeros, no draws (the branch is warp-uniform)
+#pragma unroll
+        for (int mm = 0; mm < kEpiChains; ++mm) {
+          const uint32_t o = sw128_off(m0 + mm, kr);
+          *reinterpret_cast<uint16_t*>(sZ + (size_t)(0 * 2 + katom) * kZBlock + o) = 0;
+          *reinterpret_cast<uint16_t*>(sZ + (size_t)(1 * 2 + katom) * kZBlock + o) = 0;
+        }
+      } else {
 #pragma unroll
       for (int mm = 0; mm < kEpiChains; ++mm) {
         const int m = m0 + mm;
@@ -414,6 +423,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t o = sw128_off(m, kr);
         *reinterpret_cast<__nv_bfloat16*>(sZ + (size_t)(0 * 2 + katom) * kZBlock + o) = zh;
         *reinterpret_cast<__nv_bfloat16*>(sZ + (size_t)(1 * 2 + katom) * kZBlock + o) = zl;
+      }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
       mbar_arrive(&sh.z_ready);
