@@ -164,8 +164,6 @@ __global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
 __global__ void build_kernel(CholArgs a) {
   double* Ad = static_cast<double*>(a.A);
   double* Ld = static_cast<double*>(a.Linv);
-  double* LTd = static_cast<double*>(a.LinvT);
-  (void)Ad; (void)Ld; (void)LTd;
   const int64_t n = (int64_t)a.P * a.P;
   const double tau = *a.tau_new;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
@@ -234,9 +232,8 @@ __device__ void potrf_trtri_tile(double (*L)[NB + 1], double (*Li)[NB + 1], int*
   __syncthreads();
 }
 
-// Tile products C = As Bs over one 32 x 32 x 32 block; every thread forms
-// rows {ty, ty+16} x cols {tx, tx+16} of C.  As[r][q] and Bs[q][c] are held
-// in the working format of the arithmetic (FP64, or FP32 pairs).
+// Tile products C = As Bs over one 32 x 32 x 32 block for the native FP64
+// factorization; every thread forms rows {ty, ty+16} x cols {tx, tx+16} of C.
 template <int ARITH> struct Work;
 template <> struct Work<HS_CHOL_F64> {
   using E = double;
@@ -257,27 +254,6 @@ template <> struct Work<HS_CHOL_F64> {
     out[0][1] = c01;
     out[1][0] = c10;
     out[1][1] = c11;
-  }
-};
-template <> struct Work<HS_CHOL_DF32> {
-  using E = df2;
-  static __device__ __forceinline__ E from(double x) { return df_split(x); }
-  static __device__ __forceinline__ void mma(const E (*As)[NB + 1], const E (*Bs)[NB + 1], int ty, int tx,
-                                             double out[2][2]) {
-    float h[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, l[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll 4
-    for (int q = 0; q < NB; ++q) {
-      const df2 a0 = As[ty][q], a1 = As[ty + 16][q];
-      const df2 b0 = Bs[q][tx], b1 = Bs[q][tx + 16];
-      df_fma(h[0][0], l[0][0], a0, b0);
-      df_fma(h[0][1], l[0][1], a0, b1);
-      df_fma(h[1][0], l[1][0], a1, b0);
-      df_fma(h[1][1], l[1][1], a1, b1);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) out[i][j] = df_value(h[i][j], l[i][j]);
   }
 };
 
