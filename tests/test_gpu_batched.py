@@ -130,3 +130,27 @@ def test_batched_needs_bf16(pkg):
     d = problem(1000, 20, 2, "f32", seed=1)
     with pytest.raises(pkg.HSProbitError):
         pkg.HSProbit(d["X"], d["y"], num_chains=4)
+
+
+def test_batched_long_run_moments_match_oracle_within_mc_error(pkg):
+    """Long run of the batched form (16 chains, BF16 X) against a long oracle
+    chain on the same stored X: posterior means of beta agree within Monte
+    Carlo error (GPU: between-chain standard error of 16 independent chains;
+    oracle: batch means)."""
+    d = problem(2000, 10, 3, "bf16", seed=22)
+    X = x_f64(d)
+    K, n, burn = 16, 500, 100
+    s = pkg.HSProbit(d["X"], d["y"], seed=3, num_chains=K, ring_size=n)
+    try:
+        s.sweep(n)
+        per_chain = np.stack([s.draws(chain=m)["beta"][burn:].mean(0) for m in range(K)])
+    finally:
+        s.close()
+    mg, sg = per_chain.mean(0), per_chain.std(0, ddof=1) / np.sqrt(K)
+    _, ob, _, _ = oracle.run(oracle.init_state(10), X, d["y"], oracle.gram(X), 5, 4000)
+    ob = ob[500:]
+    nb = 25
+    bmeans = ob[: len(ob) // nb * nb].reshape(nb, -1, ob.shape[1]).mean(1)
+    mo, so = bmeans.mean(0), bmeans.std(0, ddof=1) / np.sqrt(nb)
+    zs = (mg - mo) / np.sqrt(sg ** 2 + so ** 2 + 1e-12)
+    assert np.all(np.abs(zs) < 5.0), (zs, np.abs(mg - mo).max())
