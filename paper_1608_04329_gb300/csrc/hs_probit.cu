@@ -473,8 +473,8 @@ void destroy(hs_probit* h) {
     for (int j = 0; j < 2; ++j)
       if (h->placeholder[i][j]) cudaEventDestroy(h->placeholder[i][j]);
   for (auto& pe : h->pending) {
-    h->ev_pool.push_back(pe.second.first);
-    h->ev_pool.push_back(pe.second.second);
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
   }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -536,8 +536,8 @@ const char* hs_probit_status_string(int status) {
   return "unknown status";
 }
 
-hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, const uint8_t* y, int64_t N,
-                             int64_t p, uint64_t seed) {
+static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, const uint8_t* y, int64_t N,
+                               int64_t p, uint64_t seed) {
   g_last_error = HS_OK;
   hs_probit_config cfg;
   if (cfg_in)
@@ -781,7 +781,19 @@ hs_probit* hs_probit_init(const float* X, const uint8_t* y, int64_t N, int64_t p
   return hs_probit_init_ex(&cfg, X, y, N, p, seed);
 }
 
-int hs_probit_sweep(hs_probit* h, int64_t n_iter) {
+// No C++ exception leaves the C ABI: the host-side containers that can throw
+// std::bad_alloc are caught here and reported as HS_ENOMEM.
+hs_probit* hs_probit_init_ex(const hs_probit_config* cfg_in, const void* X, const uint8_t* y, int64_t N,
+                             int64_t p, uint64_t seed) {
+  try {
+    return init_ex_impl(cfg_in, X, y, N, p, seed);
+  } catch (...) {
+    g_last_error = HS_ENOMEM;
+    return nullptr;
+  }
+}
+
+static int sweep_impl(hs_probit* h, int64_t n_iter) {
   if (!h || n_iter < 0) return HS_EINVAL;
   if (h->sticky != HS_OK) return HS_ESTATE;
   if (n_iter == 0) return HS_OK;
@@ -957,6 +969,14 @@ int hs_probit_info(const hs_probit* h, int64_t* N, int64_t* p, void** stream) {
   return HS_OK;
 }
 
+int hs_probit_sweep(hs_probit* h, int64_t n_iter) {
+  try {
+    return sweep_impl(h, n_iter);
+  } catch (...) {
+    return HS_ENOMEM;
+  }
+}
+
 int hs_probit_set_profiling(hs_probit* h, int on) {
   if (!h) return HS_EINVAL;
   h->profiling = on ? 1 : 0;
@@ -985,10 +1005,14 @@ int64_t hs_chol_task_list(int32_t T, int32_t workers, int32_t inverse, int32_t* 
   if (T < 1 || T > 256 || workers < 1 || (inverse != 0 && inverse != 1) || max_codes < 0 ||
       (max_codes > 0 && !codes))
     return HS_EINVAL;
-  const std::vector<int> list = hs::chol_task_codes(T, workers, inverse != 0);
-  const int64_t n = (int64_t)list.size();
-  for (int64_t t = 0; t < n && t < max_codes; ++t) codes[t] = list[(size_t)t];
-  return n;
+  try {
+    const std::vector<int> list = hs::chol_task_codes(T, workers, inverse != 0);
+    const int64_t n = (int64_t)list.size();
+    for (int64_t t = 0; t < n && t < max_codes; ++t) codes[t] = list[(size_t)t];
+    return n;
+  } catch (...) {
+    return HS_ENOMEM;
+  }
 }
 
 int hs_probit_debug_wait_timeout(hs_probit* h, int64_t max_spins) {
