@@ -9,7 +9,8 @@
 // larger term is known) and the FMA-based TwoProduct (Ogita, Rump & Oishi,
 // "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005); division
 // and square root take one Newton correction of the FP32 quotient or root.
-// Relative error of each operation is a small multiple of 2^-48.
+// Relative error of each operation is a small multiple of 2^-48.  The exact
+// operations are host-callable too, so the CPU tests check these bounds.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,29 +21,29 @@ struct __align__(8) df2 {
   float hi, lo;
 };
 
-__device__ __forceinline__ df2 df_split(double x) {
+__host__ __device__ __forceinline__ df2 df_split(double x) {
   const float hi = (float)x;
   const float lo = (float)(x - (double)hi);
   return {hi, lo};
 }
-__device__ __forceinline__ double df_value(df2 a) { return (double)a.hi + (double)a.lo; }
-__device__ __forceinline__ double df_value(float hi, float lo) { return (double)hi + (double)lo; }
+__host__ __device__ __forceinline__ double df_value(df2 a) { return (double)a.hi + (double)a.lo; }
+__host__ __device__ __forceinline__ double df_value(float hi, float lo) { return (double)hi + (double)lo; }
 
 // Fast2Sum: |a| >= |b| or a == 0.
-__device__ __forceinline__ df2 df_renorm(float a, float b) {
+__host__ __device__ __forceinline__ df2 df_renorm(float a, float b) {
   const float s = a + b;
   return {s, b - (s - a)};
 }
-__device__ __forceinline__ df2 df_add(df2 a, df2 b) {
+__host__ __device__ __forceinline__ df2 df_add(df2 a, df2 b) {
   const float s = a.hi + b.hi;
   const float bb = s - a.hi;
   float e = (a.hi - (s - bb)) + (b.hi - bb);
   e += a.lo + b.lo;
   return df_renorm(s, e);
 }
-__device__ __forceinline__ df2 df_neg(df2 a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ df2 df_sub(df2 a, df2 b) { return df_add(a, df_neg(b)); }
-__device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
+__host__ __device__ __forceinline__ df2 df_neg(df2 a) { return {-a.hi, -a.lo}; }
+__host__ __device__ __forceinline__ df2 df_sub(df2 a, df2 b) { return df_add(a, df_neg(b)); }
+__host__ __device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);
   e = fmaf(a.hi, b.lo, e);
@@ -50,13 +51,13 @@ __device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
   return df_renorm(p, e);
 }
 // 1 / b: FP32 reciprocal q, residual 1 - b q in pair arithmetic, one correction.
-__device__ __forceinline__ df2 df_recip(df2 b) {
+__host__ __device__ __forceinline__ df2 df_recip(df2 b) {
   const float q = 1.0f / b.hi;
   const df2 r = df_sub(df2{1.0f, 0.0f}, df_mul(b, df2{q, 0.0f}));
   return df_renorm(q, r.hi * q);
 }
 // sqrt(a), a > 0: FP32 root s, exact s^2 = p + e, one correction.
-__device__ __forceinline__ df2 df_sqrt(df2 a) {
+__host__ __device__ __forceinline__ df2 df_sqrt(df2 a) {
   const float s = sqrtf(a.hi);
   const float p = s * s;
   const float e = fmaf(s, s, -p);
@@ -86,7 +87,7 @@ __device__ __forceinline__ void df_sqrt_rsqrt_fast(df2 a, df2& sq, df2& rs) {
 
 // (sh, sl) += a * b with a lazily accumulated low word; df_renorm(sh, sl)
 // gives the pair at the end.
-__device__ __forceinline__ void df_fma(float& sh, float& sl, df2 a, df2 b) {
+__host__ __device__ __forceinline__ void df_fma(float& sh, float& sl, df2 a, df2 b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);
   e = fmaf(a.hi, b.lo, e);
