@@ -250,10 +250,12 @@ int64_t hs_chol_task_list(int32_t T, int32_t workers, int32_t inverse, int32_t* 
  * it is the same transition as a one-chain handle with that chain id.  The
  * X-stream of all K chains is one pass over X on the tensor cores (eta = X B
  * and X^T Z as BF16 products, beta and z each split into two BF16 parts,
- * FP32 accumulation); every other step runs per chain.  The sweep count k is
- * shared: hs_probit_sweep advances every chain, and the last set_state call
- * sets k for all of them.  The functions without a chain argument act on
- * chain 0. */
+ * FP32 accumulation); the factorizations of all chains are one launch (on the
+ * single-launch schedule, by default without the inverse factor, beta then
+ * coming from block substitution: see beta_solve), and the other steps run per
+ * chain.  The sweep count k is shared: hs_probit_sweep advances every chain,
+ * and the last set_state call sets k for all of them.  The functions without a
+ * chain argument act on chain 0. */
 
 /* Number of chains of the handle (>= 1), or HS_EINVAL. */
 int hs_probit_num_chains(const hs_probit* h);
