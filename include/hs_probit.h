@@ -209,24 +209,31 @@ int hs_probit_debug_wait_timeout(hs_probit* h, int64_t max_spins);
  *   z_i = y*_i TN+(y*_i x_i beta) with the counters of sweep number `sweep`
  *   (purpose z, `chain`, `problem`, key `seed`), and X^T z.
  * All arguments are device pointers on the current device:
- *   X       N rows of type x_dtype with row stride ld elements; ld * element
- *           size must be a multiple of 16 bytes; columns p..ld-1 must be zero.
+ *   X       N rows of type x_dtype with row stride ld elements, starting on a
+ *           16-byte boundary; ld * element size must be a multiple of 16
+ *           bytes; columns p..ld-1 must be zero.
  *   y       N bytes in {0, 1} (not checked here).
- *   beta_c  ld values, double for HS_X_F64 and float otherwise, equal to
- *           beta_j * x_scales[j] (FP8) or beta_j, zero for j >= p.
- *   x_scales p floats for HS_X_FP8E4M3 (multiplied into X^T z), else NULL.
+ *   beta_c  ld values, double for HS_X_F64 and float otherwise (naturally
+ *           aligned), equal to beta_j * x_scales[j] (FP8) or beta_j, zero
+ *           for j >= p.
+ *   x_scales p floats for HS_X_FP8E4M3 (multiplied into X^T z); must be NULL
+ *           for every other x_dtype.
  *   xtz     output, p doubles.   z  output, N doubles, or NULL.
- *   stream  cudaStream_t or NULL; the call waits for its own work on it.
+ *   stream  cudaStream_t or NULL.
+ * The call is synchronous: it waits for its own work on `stream` and reads
+ * the device error word back, so it cannot be called while `stream` (or the
+ * legacy default stream) is being captured into a CUDA graph.
  * The per-block partial sums live in one fixed device array of 4 MiB
  * (plus a 256-byte header) that every GPU loading the library holds until
  * the process exits: sizes whose partials (one row of ld values per SM)
  * exceed it are rejected with HS_EINVAL, as are p > 8192 and ld > 16384.
- * The first call on a device looks up that array's device address (no
- * allocation); make that first call before any stream capture.  Every call
- * shares the array: calls that overlap on the GPU (other streams, other host
- * threads) race and must be serialized by the caller.  The error word in the
- * array is cleared by each call.  Returns HS_OK, HS_EINVAL, HS_ENONFINITE,
- * HS_ETIMEOUT or HS_ECUDA. */
+ * Every argument check is made on the host before any CUDA call.  The first
+ * call on a device looks up that array's device address (no allocation) and
+ * keeps it for the life of the process, so the entry point must not be used
+ * on a device after cudaDeviceReset.  Every call shares the array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialized by the caller.  The error word in the array is cleared by each
+ * call.  Returns HS_OK, HS_EINVAL, HS_ENONFINITE, HS_ETIMEOUT or HS_ECUDA. */
 int hs_probit_xstream_noalloc(int x_dtype, const void* X, int64_t ld, const uint8_t* y, int64_t N,
                               int64_t p, const void* beta_c, const float* x_scales, uint64_t seed,
                               uint32_t chain, uint32_t problem, int64_t sweep, double* xtz, double* z,

@@ -13,6 +13,7 @@
 // the library, so no call allocates anything.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "hs_internal.h"
@@ -38,7 +39,9 @@ __global__ void noalloc_header_kernel(int* err, int64_t* sweeps_done, int64_t va
 }
 
 // Device address of the scratch array on the current device (set up once
-// per device, with that device current).
+// per device, with that device current).  The address is kept for the life
+// of the process; after cudaDeviceReset it would be stale, so a caller that
+// resets a device must not use this entry point on it again.
 int scratch_for_device(int dev, unsigned char** ptr, int* num_sms) {
   if (dev < 0 || dev >= kMaxDevices) return HS_EINVAL;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
@@ -80,10 +83,19 @@ extern "C" int hs_probit_xstream_noalloc(int x_dtype, const void* X, int64_t ld,
                                          void* stream) {
   using namespace hs;
   const int eb = elem_bytes(x_dtype);
+  // Every check below is on the host and comes before any CUDA call.  The
+  // bulk copies read rows of X from 16-byte boundaries, so X must start on
+  // one; beta_c, xtz and z are read or written as whole doubles (floats for
+  // beta_c of the narrow types).  (ld * eb) / 16 > 2048: more 16-byte slices
+  // per row than the kernel takes.
+  const uintptr_t bc_align = x_dtype == HS_X_F64 ? 8 : 4;
   if (eb == 0 || !X || !y || !beta_c || !xtz || N < 1 || p < 1 || p > 8192 || ld < p || sweep < 1 ||
       sweep > (int64_t)0xFFFFFFFF || N > (int64_t)0xFFFFFFFF || chain >= (1u << 24) || (ld * eb) % 16 != 0 ||
-      (x_dtype == HS_X_FP8E4M3 && !x_scales) || ld > 16384 || (ld * eb) / 16 > 2048)
-    return HS_EINVAL;  // (ld * eb) / 16 > 2048: more 16-byte slices per row than the kernel takes
+      (x_dtype == HS_X_FP8E4M3) != (x_scales != nullptr) || ld > 16384 || (ld * eb) / 16 > 2048 ||
+      (reinterpret_cast<uintptr_t>(X) & 15u) != 0 || (reinterpret_cast<uintptr_t>(beta_c) & (bc_align - 1)) != 0 ||
+      (reinterpret_cast<uintptr_t>(xtz) & 7u) != 0 || (reinterpret_cast<uintptr_t>(z) & 7u) != 0 ||
+      (x_scales && (reinterpret_cast<uintptr_t>(x_scales) & 3u) != 0))
+    return HS_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HS_ECUDA;
   unsigned char* scratch = nullptr;

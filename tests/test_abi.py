@@ -81,13 +81,39 @@ def test_init_rejects_fp64_rows_beyond_the_kernel(lib):
     assert lib.hs_probit_last_error() == -1
 
 
+def _no_cuda_device():
+    try:
+        import torch
+        return not torch.cuda.is_available()
+    except ImportError:
+        return True
+
+
+# The addresses below are host-side stand-ins that no kernel may ever be given;
+# the test runs only where there is no GPU, so even a check that regressed
+# could not launch a kernel on them.
+@pytest.mark.skipif(not _no_cuda_device(), reason="host-only argument checks; a GPU is present")
 def test_noalloc_rejects_bad_arguments_on_host(lib):
-    # NULL buffers and a row stride that is not a multiple of 16 bytes are
-    # rejected before any CUDA call.
+    # NULL buffers, a row stride that is not a multiple of 16 bytes, an X that
+    # does not start on a 16-byte boundary, misaligned beta_c / xtz / z, and
+    # column scales given for a type without them are all rejected before any
+    # CUDA call.
+    v = ctypes.c_void_p
     assert lib.hs_probit_xstream_noalloc(1, None, 8, None, 10, 8, None, None, 0, 0, 0, 1, None, None, None) == -1
-    assert lib.hs_probit_xstream_noalloc(1, ctypes.c_void_p(16), 5, ctypes.c_void_p(16), 10, 5,
-                                         ctypes.c_void_p(16), None, 0, 0, 0, 1, ctypes.c_void_p(16), None,
+    assert lib.hs_probit_xstream_noalloc(1, v(4096), 5, v(4096), 10, 5, v(4096), None, 0, 0, 0, 1, v(4096), None,
                                          None) == -1
+    assert lib.hs_probit_xstream_noalloc(1, v(4096 + 4), 8, v(4096), 10, 8, v(4096), None, 0, 0, 0, 1, v(4096),
+                                         None, None) == -1
+    assert lib.hs_probit_xstream_noalloc(0, v(4096), 8, v(4096), 10, 8, v(4096 + 4), None, 0, 0, 0, 1, v(4096),
+                                         None, None) == -1
+    assert lib.hs_probit_xstream_noalloc(1, v(4096), 8, v(4096), 10, 8, v(4096), None, 0, 0, 0, 1, v(4096 + 4),
+                                         None, None) == -1
+    assert lib.hs_probit_xstream_noalloc(1, v(4096), 8, v(4096), 10, 8, v(4096), None, 0, 0, 0, 1, v(4096),
+                                         v(4096 + 4), None) == -1
+    assert lib.hs_probit_xstream_noalloc(1, v(4096), 8, v(4096), 10, 8, v(4096), v(4096), 0, 0, 0, 1, v(4096),
+                                         None, None) == -1
+    assert lib.hs_probit_xstream_noalloc(3, v(4096), 16, v(4096), 10, 16, v(4096), None, 0, 0, 0, 1, v(4096),
+                                         None, None) == -1
 
 
 def test_tn_sample_rejects_bad_arguments_on_host(lib):
