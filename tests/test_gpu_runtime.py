@@ -155,24 +155,40 @@ def test_device_inputs_and_bad_device_y(pkg, data):
     assert ei.value.status == -1
 
 
+def _batch_means(v, nb=25):
+    """Mean over the draws (rows of v) and its batch-means standard error."""
+    m = v[: len(v) // nb * nb].reshape(nb, -1, v.shape[1]).mean(1)
+    return m.mean(0), m.std(0, ddof=1) / np.sqrt(nb)
+
+
+def _moment_zscores(a, b):
+    """z-scores of the differences of the posterior means and of the posterior
+    variances of two chains' draws (rows), with batch-means errors; the
+    variance of each chain is the batch mean of (v - mean of v)^2."""
+    ma, sa = _batch_means(a)
+    mb, sb = _batch_means(b)
+    va, sva = _batch_means((a - a.mean(0)) ** 2)
+    vb, svb = _batch_means((b - b.mean(0)) ** 2)
+    zm = (ma - mb) / np.sqrt(sa ** 2 + sb ** 2 + 1e-12)
+    zv = (va - vb) / np.sqrt(sva ** 2 + svb ** 2 + 1e-24)
+    return zm, zv
+
+
 def test_long_run_moments_match_oracle_within_mc_error(pkg):
-    """Different seeds: posterior means of beta from the GPU chain and the
-    oracle chain agree within Monte Carlo error (batch means)."""
+    """Different seeds: posterior means and variances of beta (and of
+    log lambda^{-2} and log tau^{-2}) from the GPU chain and the oracle chain
+    agree within Monte Carlo error (batch means, 5 standard errors)."""
     d = problem(2000, 10, 3, "f64", seed=21)
     n, burn = 3000, 500
     s = pkg.HSProbit(d["X"], d["y"], seed=1, ring_size=n)
     s.sweep(n)
-    gb = s.draws()["beta"][burn:]
-    _, ob, _, _ = oracle.run(oracle.init_state(10), d["X"], d["y"], oracle.gram(d["X"]), 2, n)
-    ob = ob[burn:]
-
-    def bm(v, nb=25):
-        m = v[: len(v) // nb * nb].reshape(nb, -1, v.shape[1]).mean(1)
-        return m.mean(0), m.std(0, ddof=1) / np.sqrt(nb)
-    mg, sg = bm(gb)
-    mo, so = bm(ob)
-    zs = (mg - mo) / np.sqrt(sg ** 2 + so ** 2 + 1e-12)
-    assert np.all(np.abs(zs) < 5.0), zs
+    g = s.draws()
+    _, ob, ol, ot = oracle.run(oracle.init_state(10), d["X"], d["y"], oracle.gram(d["X"]), 2, n)
+    gv = np.column_stack([g["beta"], np.log(g["lambda_inv2"]), np.log(g["tau_inv2"])])[burn:]
+    ov = np.column_stack([ob, np.log(ol), np.log(ot)])[burn:]
+    zm, zv = _moment_zscores(gv, ov)
+    assert np.all(np.abs(zm) < 5.0), ("means", zm)
+    assert np.all(np.abs(zv) < 5.0), ("variances", zv)
 
 
 def test_profiling_in_graph_and_eager_modes(pkg, data):
