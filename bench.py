@@ -91,22 +91,32 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []          # (arrival time, line)
+        self.window = None       # (t0, t1) of the timed region, host monotonic clock
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region starts only once samples are flowing (nvidia-smi takes a moment to start)
+            t_end = time.monotonic() + 3.0
+            while not self.lines and time.monotonic() < t_end and self.proc.poll() is None:
+                time.sleep(0.005)
         except (FileNotFoundError, OSError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark(self, start: bool):
+        """Host time of the start (start=True) or end of the timed region."""
+        now = time.monotonic()
+        self.window = (now, None) if start else (self.window[0] if self.window else now, now)
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -119,7 +129,17 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if self.window and self.window[1] is not None:
+            # samples that arrived during the timed region (plus one sampling period after it)
+            inside = [ln for t, ln in lines if self.window[0] <= t <= self.window[1] + 0.025]
+            if not inside:
+                after = [ln for t, ln in lines if t >= self.window[0]]
+                inside = after[:1]
+            lines = inside
+        else:
+            lines = [ln for _, ln in lines]
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -155,13 +175,71 @@ def _traffic(workload: str, record: str = "xstream_traffic.json", sources=XSTREA
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    h = hashlib.sha256()
-    for s in sources:
-        with open(os.path.join(ROOT, s), "rb") as f:
-            h.update(f.read())
-    if rec.get("sources_sha256") != h.hexdigest() or rec.get("workload") != workload:
+    if rec.get("sources_sha256") != sources_sha256(sources) or rec.get("workload") != workload:
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+# DRAM-traffic records of the X-stream kernels (profiles/*_traffic.json):
+# captured at the profiling size, scaled by rows to the full workload.
+TRAFFIC_RECORDS = {
+    "c1s": dict(record="xstream_traffic.json", sources=XSTREAM_SOURCES, kernel_regex="xstream_kernel",
+                full="c1", row_bytes=lambda p: 4 * p + 1),
+    "c2s": dict(record="xstream_k_traffic.json", sources=XSTREAM_K_SOURCES, kernel_regex="xstream_k_kernel",
+                full="c2", row_bytes=lambda p: 2 * p + 1),
+}
+
+
+def sources_sha256(sources) -> str:
+    h = hashlib.sha256()
+    for src in sources:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _ncu_bytes(value: str, unit: str) -> float:
+    scale = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12}[unit.strip().lower()]
+    return float(value.replace(",", "")) * scale
+
+
+def write_traffic_record(csv_path: str, workload: str, command: str) -> dict:
+    """Turn an ncu CSV (dram__bytes_read.sum and dram__bytes_write.sum of the
+    X-stream kernel at the profiling size) into the committed traffic record:
+    bytes of the last captured launch, scaled by rows to the full workload,
+    tagged with the hash of the kernel's sources."""
+    import csv
+    import re
+    spec = TRAFFIC_RECORDS[workload]
+    wl, full = WORKLOADS[workload], WORKLOADS[spec["full"]]
+    launches = {}
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(f) if r]
+    head = next(i for i, r in enumerate(rows) if "Metric Name" in r)
+    cols = rows[head]
+    ik, im, iu, iv, iid = (cols.index("Kernel Name"), cols.index("Metric Name"), cols.index("Metric Unit"),
+                           cols.index("Metric Value"), cols.index("ID"))
+    for r in rows[head + 1:]:
+        if len(r) <= iv or not re.search(spec["kernel_regex"], r[ik]):
+            continue
+        if r[im] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            launches.setdefault(int(r[iid]), {})[r[im]] = _ncu_bytes(r[iv], r[iu])
+    if not launches:
+        raise SystemExit(f"no launch of {spec['kernel_regex']} with DRAM counters in {csv_path}")
+    last = launches[max(launches)]
+    rd, wr = last["dram__bytes_read.sum"], last["dram__bytes_write.sum"]
+    scale = full["N"] / wl["N"]
+    rec = {"kernel": spec["kernel_regex"], "workload": spec["full"],
+           "dram_bytes_per_launch": int(round((rd + wr) * scale)),
+           "captured_on": f"N={wl['N']}, p={wl['p']} {wl['dt']} (X larger than L2); scaled by rows to N={full['N']}",
+           "captured_read_bytes": rd, "captured_write_bytes": wr,
+           "algorithmic_bytes_per_launch": full["N"] * spec["row_bytes"](full["p"]),
+           "sources": spec["sources"], "sources_sha256": sources_sha256(spec["sources"]), "command": command}
+    rec["traffic_over_algorithmic"] = rec["dram_bytes_per_launch"] / rec["algorithmic_bytes_per_launch"]
+    with open(os.path.join(ROOT, "profiles", spec["record"]), "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    return rec
 
 
 def make_data(wl):
@@ -170,15 +248,25 @@ def make_data(wl):
                                  mag=wl.get("mag", (1.0, 3.0)))
 
 
-def cpu_oracle_rate(d, wl, n_sweeps: int, budget_s: float = 30.0):
-    """Oracle sweeps/s on the host (full workload, first n_sweeps sweeps)."""
+def run_config(wl, args, ws, x_nbytes):
+    """The ``config`` object of the bench line (the same for both arms)."""
+    return {"workload": wl["name"], "N": wl["N"], "p": wl["p"], "x_dtype": wl["dt"],
+            "chains_per_gpu": 1, "cholesky": args.chol, "graph": bool(args.graph),
+            "l2": f"inputs larger than L2 (X {x_nbytes / 1e9:.1f} GB), no flush",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
+
+
+def cpu_oracle_rate(d, wl, n_sweeps: int, budget_s: float = 30.0, warmup: int = 1):
+    """Oracle sweeps/s on the host (full workload, first n_sweeps sweeps after
+    ``warmup`` untimed ones)."""
     import oracle
     X = oracle.fmt.stored_to_f64(d["X"], d["x_dtype"], d["scales"])
     t0 = time.perf_counter()
     G = oracle.gram(X)
     t_gram = time.perf_counter() - t0
     st = oracle.init_state(wl["p"])
-    st = oracle.sweep_once(st, X, d["y"], G, 0)  # warm-up
+    for _ in range(max(warmup, 1)):
+        st = oracle.sweep_once(st, X, d["y"], G, 0)  # warm-up
     done, t = 0, 0.0
     while done < n_sweeps and t < budget_s:
         t1 = time.perf_counter()
@@ -193,14 +281,14 @@ def run_reference(args, wl, dist, rank):
         return 0
     d = make_data(wl)
     n = args.steps
-    rate, done, t, t_gram = cpu_oracle_rate(d, wl, n_sweeps=n, budget_s=args.ref_budget)
+    rate, done, t, t_gram = cpu_oracle_rate(d, wl, n_sweeps=n, budget_s=args.ref_budget, warmup=args.warmup)
     cores = os.cpu_count()
     sample = (f"{done} oracle sweeps of the full workload (of {n} requested; capped at "
-              f"{args.ref_budget:.0f} s), after an untimed Gram ({t_gram:.1f} s) and one warm-up sweep")
+              f"{args.ref_budget:.0f} s), after an untimed Gram ({t_gram:.1f} s) and {args.warmup} warm-up sweeps")
     line = {"metric": METRIC, "value": rate, "unit": "sweeps/s", "n_gpus": 0, "steps": done,
-            "warmup": 1, "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["name"], "N": wl["N"], "p": wl["p"], "x_dtype": wl["dt"]},
+            "config": run_config(wl, args, 1, d["X"].nbytes),
             "impl": "reference",
             "cpu_baseline": {"value": rate, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
@@ -223,10 +311,12 @@ def run_k_chains(args, wk, pkg, torch, dist, ws, rank, local, chol, one_chain_va
     k0 = torch.cuda.Event(enable_timing=True)
     k1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        clk.mark(True)
         k0.record(streamk)
         sk.sweep(args.k_steps)
         k1.record(streamk)
         torch.cuda.synchronize()
+        clk.mark(False)
     barrier(dist)
     kms = max_over_ranks(dist, k0.elapsed_time(k1))
     kgroups = {g: sk.kernel_time(g) for g in ("xstream", "reduce", "shrink", "cholesky", "tail")}
@@ -321,7 +411,13 @@ def main(argv=None):
                     help="also time the batched form: K chains on BF16 X (0: skip)")
     ap.add_argument("--k-steps", type=int, default=20)
     ap.add_argument("--no-tn", action="store_true", help="skip the standalone sampler comparison")
+    ap.add_argument("--traffic-from", default=None, metavar="CSV",
+                    help="write profiles/<kernel>_traffic.json from an ncu CSV of --workload c1s or c2s and exit")
+    ap.add_argument("--traffic-command", default="", help="the ncu command that made the CSV (recorded)")
     args = ap.parse_args(argv)
+    if args.traffic_from:
+        print(json.dumps(write_traffic_record(args.traffic_from, args.workload, args.traffic_command)))
+        return 0
     wl = WORKLOADS[args.workload]
     dist, rank, ws, local = _dist()
     if args.impl == "reference":
@@ -362,10 +458,12 @@ def main(argv=None):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        clk.mark(True)
         e0.record(stream)
         s.sweep(args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
+        clk.mark(False)
     barrier(dist)
     ms_local = e0.elapsed_time(e1)
     ms = max_over_ranks(dist, ms_local)
@@ -433,10 +531,7 @@ def main(argv=None):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if wl["dt"] != "f64" else "f64",
                 "data": "synthetic",
-                "config": {"workload": wl["name"], "N": wl["N"], "p": wl["p"], "x_dtype": wl["dt"],
-                           "chains_per_gpu": 1, "cholesky": args.chol, "graph": bool(args.graph),
-                           "l2": f"inputs larger than L2 (X {d['X'].nbytes / 1e9:.1f} GB), no flush",
-                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+                "config": run_config(wl, args, ws, d["X"].nbytes),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches,
                 "clocks": clk.summary(),
