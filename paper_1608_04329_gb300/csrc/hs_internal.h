@@ -17,6 +17,18 @@ enum : int {
   kErrGamma = 8,       // Cheng's sampler found no acceptance in its round cap
   kErrBadY = 16,       // a y value outside {0, 1}
 };
+// A bounded wait that runs out also ORs 1 << (kErrSiteShift + site) into the
+// word, naming where it gave up (hs_probit_debug_error_word).
+constexpr int kErrSiteShift = 8;
+enum : int {
+  kSiteChainStart = 0,   // factorization: the chain's first diagonal tile of a block column
+  kSiteChainStep = 1,    // factorization: the chain's tiles of the next step
+  kSiteTask = 2,         // factorization: a worker task's inputs
+  kSiteTrailLoad = 3,    // trailing updates: a free stage for the loads
+  kSiteTrailMma = 4,     // trailing updates: loaded digits or a free accumulator
+  kSiteTrailEpi = 5,     // trailing updates: finished classes
+  kSiteStartRole = 6,    // factorization: the chain's SM mark
+};
 
 // Philox key and the fixed parts of the counter.
 struct RngKey {
@@ -84,9 +96,13 @@ int partial_elem_bytes(int x_dtype);
 cudaError_t reduce_partials_launch(int x_dtype, const void* partials, int grid, int ld, int p,
                                    const float* colscale, double* xtz, cudaStream_t s);
 
-// G = X^T X (p x p, FP64, row-major, full), X as stored (scaled for FP8).
-cudaError_t gram_launch(int x_dtype, const void* X, int64_t N, int ld, int p,
-                        const float* colscale, double* G, cudaStream_t s);
+// G = X^T X (p x p, FP64, row-major, full), X as stored (scaled for FP8), on
+// the tensor cores with exact digit products (gram_tc.cu).  workspace:
+// gram_workspace_bytes(N, p, num_sms) bytes of device memory, free after the
+// call's work completes.  A bounded wait that runs out sets kErrTimeout in err.
+size_t gram_workspace_bytes(int64_t N, int p, int num_sms);
+cudaError_t gram_launch(int x_dtype, const void* X, int64_t N, int ld, int p, const float* colscale, double* G,
+                        void* workspace, int num_sms, int* err, cudaStream_t s);
 
 // y must be 0/1: sets kErrBadY in err otherwise.
 cudaError_t check_y_launch(const uint8_t* y, int64_t N, int* err, cudaStream_t s);
@@ -135,6 +151,13 @@ struct CholArgs {
   size_t sync_words;
   const int* order;             // worker task list (chol_task_codes), or nullptr: canonical order
   int inverse;                  // single-launch schedule: 1 forms all of L~^{-1}; 0 only its diagonal tiles
+  // Block-column launches (the trailing updates run on the tensor cores,
+  // chol_trail_launch): this launch factors tile columns [k0, k1) only, runs
+  // the ntasks entries of order, and writes the six BF16 digit planes of every
+  // factor tile it forms below row tile k1 (digits: nchains x 6 planes of P x P).
+  int k0, k1;                   // 0, 0: the whole matrix in one launch
+  int ntasks;                   // > 0: entries of order (block-column launches)
+  void* digits;                 // or nullptr
 };
 // Enqueues the whole factorization; *launches receives the kernel count.
 cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches);
@@ -151,6 +174,31 @@ std::vector<int> chol_task_order(int T, int workers, bool inverse);
 // The same list with each entry decoded for the kernel: kind (0 C, 1 X, 2 UA,
 // 3 UB) | k << 2 | i << 10 | j << 18 (T <= 256).
 std::vector<int> chol_task_codes(int T, int workers, bool inverse);
+
+// Task list of one block-column launch (tile columns [k0, k1) of T): C(i, k) and
+// the updates UA(i, j, k) with j < k1, as codes kind | k << 2 | i << 10 | j << 18.
+std::vector<int> chol_block_task_codes(int T, int k0, int k1);
+
+// ---- trailing updates on the tensor cores (chol_trail.cu) -------------------
+struct TrailArgs {
+  int p, P, nchains;
+  int b;                        // block column (tiles 4b .. 4b+3)
+  int col_lo, col_hi;           // output tile columns [col_lo, col_hi) of this launch
+  void* A;                      // nchains x P x P FP32 pairs (tiles of A~ and of L~)
+  const void* G2;               // P x P FP32 pairs of the Gram matrix (first block column only)
+  const double* S;              // nchains x P equilibration
+  const double* lam_new;        // nchains x p
+  const double* tau_new;        // nchains
+  unsigned long long* sync;     // readiness words (chol_sync_words per chain); [0] holds the launch epoch
+  size_t sync_words;
+  int* err;
+};
+size_t chol_trail_smem_bytes();
+cudaError_t chol_trail_prepare();
+int chol_trail_make_maps(const void* digits, int P, int nchains, void* mapA, void* mapB);
+int chol_trail_items(int P, int b, int col_lo, int col_hi, int nchains);
+cudaError_t chol_trail_launch(const void* mapA, const void* mapB, const TrailArgs& a, int grid, cudaStream_t s);
+cudaError_t gram_pairs_launch(const double* G, int p, int P, void* G2, cudaStream_t s);
 
 // ---- beta tail, nu/xi, commit ----------------------------------------------
 struct TailArgs {

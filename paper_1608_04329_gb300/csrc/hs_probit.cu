@@ -11,6 +11,7 @@
 // beta tail joins both.  The DAG can be captured once as a CUDA graph.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -80,6 +81,15 @@ struct hs_probit {
   int chol_grid = 0;                        // its blocks; 0: one launch per block column
   size_t chol_words = 0;                    // scheduling words per chain
   int* chol_order = nullptr;                // worker task list of the single-launch factorization
+  // HS_SCHED_TENSOR: block-column launches and tensor-core trailing updates
+  bool tensor_sched = false;
+  void* digits = nullptr;                   // K x 6 digit planes of P x P BF16
+  void* G2 = nullptr;                       // P x P FP32 pairs of the Gram matrix
+  int* blk_order = nullptr;                 // the block columns' task lists, one after another
+  std::vector<int> blk_off, blk_len;
+  int trail_grid = 0;
+  alignas(64) unsigned char tmapA[128];     // tensor maps of the digit planes (128- and 64-row boxes)
+  alignas(64) unsigned char tmapB[128];
   // K chains sharing X: every per-chain buffer holds K slices (chain m at offset m * size)
   int K = 1;
   int64_t* k_scratch = nullptr;             // K: commits of chains 0..K-2 record the sweep here
@@ -99,6 +109,7 @@ struct hs_probit {
   int64_t* h_k = nullptr;    // pinned
 
   int sticky = HS_OK;
+  int last_err_word = 0;     // device error word seen by the last synchronization
   int64_t k_host = 0;
   std::vector<int64_t> drained;  // per chain: draws (index k/thin) already handed out
   int64_t launches = 0;
@@ -337,7 +348,36 @@ cudaError_t enqueue_sweep(hs_probit* h) {
     cudaError_t ee;
     {
       ProfSpan sp(h, 3, h->s1);
-      if (after_xstream) {
+      if (h->tensor_sched) {
+        // block column b: its tile tasks (one launch), then the rank-128 update
+        // of everything to its right on the tensor cores (one launch)
+        hs::CholArgs ca = chol_args(h, 0);
+        ca.nchains = h->K;
+        ca.digits = h->digits;
+        hs::TrailArgs ta{};
+        ta.p = h->p;
+        ta.P = h->P;
+        ta.nchains = h->K;
+        ta.col_lo = 0;
+        ta.col_hi = h->T;
+        ta.A = h->A;
+        ta.G2 = h->G2;
+        ta.S = h->S;
+        ta.lam_new = h->lam_new;
+        ta.tau_new = h->tau_new;
+        ta.sync = h->chol_sync;
+        ta.sync_words = h->chol_words;
+        ta.err = h->err;
+        for (int b = 0; b < (int)h->blk_off.size(); ++b) {
+          ca.k0 = 4 * b;
+          ca.k1 = std::min(4 * b + 4, h->T);
+          ca.order = h->blk_order + h->blk_off[b];
+          ca.ntasks = h->blk_len[b];
+          if ((ee = hs::chol_enqueue(ca, h->s1, nullptr)) != cudaSuccess) return ee;
+          ta.b = b;
+          if ((ee = hs::chol_trail_launch(h->tmapA, h->tmapB, ta, h->trail_grid, h->s1)) != cudaSuccess) return ee;
+        }
+      } else if (after_xstream) {
         // every chain's factorization in one launch
         hs::CholArgs ca = chol_args(h, 0);
         ca.nchains = h->K;
@@ -496,6 +536,7 @@ int sync_and_check(hs_probit* h) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->s0);
   if (e != cudaSuccess) return cuda_status(e);
   h->k_host = *h->h_k;
+  h->last_err_word = *h->h_err;
   if (*h->h_err) return status_from_err_bits(*h->h_err);
   return HS_OK;
 }
@@ -548,7 +589,7 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   if (!X || !y || N < 2 || p < 1 || p > kMaxP || cfg.thin < 1 || cfg.ring_size < 1 ||
       cfg.chain >= (1u << 24) || (cfg.x_dtype < HS_X_F64 || cfg.x_dtype > HS_X_FP8E4M3) ||
       (cfg.chol_arith != HS_CHOL_F64 && cfg.chol_arith != HS_CHOL_DF32) || N > (int64_t)0xFFFFFFFF ||
-      cfg.chol_sched < HS_SCHED_AUTO || cfg.chol_sched > HS_SCHED_SINGLE || cfg.beta_solve < HS_BETA_AUTO ||
+      cfg.chol_sched < HS_SCHED_AUTO || cfg.chol_sched > HS_SCHED_TENSOR || cfg.beta_solve < HS_BETA_AUTO ||
       cfg.beta_solve > HS_BETA_SUBST) {
     fail(HS_EINVAL);
     return nullptr;
@@ -626,7 +667,7 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   check(hs::linalg_prepare());
   if (e == cudaSuccess && cfg.chol_arith == HS_CHOL_DF32 && cfg.chol_sched != HS_SCHED_COLUMNS) {
     h->chol_grid = hs::chol_persistent_grid(h->device, Kc);
-    if (h->chol_grid == 0 && cfg.chol_sched == HS_SCHED_SINGLE) {
+    if (h->chol_grid == 0 && (cfg.chol_sched == HS_SCHED_SINGLE || cfg.chol_sched == HS_SCHED_TENSOR)) {
       destroy(h);
       fail(HS_EUNSUPPORTED);
       return nullptr;
@@ -643,6 +684,19 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   // at p = 1000 its diagonal chain bounds it and the inverse products win)
   h->chol_inverse = !(h->chol_grid > 0 && (cfg.beta_solve == HS_BETA_SUBST ||
                                           (cfg.beta_solve == HS_BETA_AUTO && (h->K > 1 || h->T >= 64))));
+  // the tensor-core trailing updates: where the factorization is throughput-bound
+  // (several chains, or a large p), factor only
+  h->tensor_sched = h->chol_grid > 0 && cfg.chol_arith == HS_CHOL_DF32 &&
+                    (cfg.chol_sched == HS_SCHED_TENSOR ||
+                     (cfg.chol_sched == HS_SCHED_AUTO && !h->chol_inverse && (h->K > 1 || h->T >= 64)));
+  if (h->tensor_sched && h->chol_inverse) {
+    if (cfg.beta_solve == HS_BETA_INVERSE) {
+      destroy(h);
+      fail(HS_EUNSUPPORTED);
+      return nullptr;
+    }
+    h->chol_inverse = false;
+  }
   if (cfg.stream) {
     h->s0 = static_cast<cudaStream_t>(cfg.stream);
   } else {
@@ -696,6 +750,24 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
     order = hs::chol_task_codes(h->T, slots > 1 ? slots : 1, h->chol_inverse);
     if (!order.empty()) check(h->alloc(&h->chol_order, order.size() * sizeof(int)));
   }
+  if (h->tensor_sched) {
+    check(hs::chol_trail_prepare());
+    check(h->alloc(&h->digits, K * 6 * P2 * sizeof(uint16_t)));
+    check(h->alloc(&h->G2, P2 * 2 * sizeof(float)));
+    std::vector<int> all;
+    for (int b = 0; 4 * b < h->T; ++b) {
+      const std::vector<int> c = hs::chol_block_task_codes(h->T, 4 * b, std::min(4 * b + 4, h->T));
+      h->blk_off.push_back((int)all.size());
+      h->blk_len.push_back((int)c.size());
+      all.insert(all.end(), c.begin(), c.end());
+    }
+    check(h->alloc(&h->blk_order, std::max<size_t>(all.size(), 1) * sizeof(int)));
+    if (e == cudaSuccess && !all.empty())
+      check(cudaMemcpy(h->blk_order, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (e == cudaSuccess && hs::chol_trail_make_maps(h->digits, h->P, h->K, h->tmapA, h->tmapB) != 0)
+      e = cudaErrorInvalidValue;
+    h->trail_grid = num_sms > 0 ? num_sms : 1;
+  }
   if (h->K == 1) {
     check(h->alloc(&h->partials, (size_t)h->grid * h->ld * hs::partial_elem_bytes(h->x_dtype)));
   } else {
@@ -747,18 +819,28 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
     check(cudaMemsetAsync(h->beta_c, 0, K * bc_bytes, h->s0));
     check(cudaStreamSynchronize(h->s0));  // host staging buffers go out of scope
   }
-  // ---- one-time Gram matrix (Sect. 5, beta update, step i) ----
+  // ---- one-time Gram matrix (Sect. 5, beta update, step i), tensor cores ----
+  void* gram_ws = nullptr;
+  check(cudaMalloc(&gram_ws, hs::gram_workspace_bytes(N, h->p, num_sms > 0 ? num_sms : 1)));
   {
     ProfSpan sp(h, 5, h->s0);
-    check(hs::gram_launch(h->x_dtype, h->X, N, h->ld, h->p, h->colscale, h->G, h->s0));
+    check(hs::gram_launch(h->x_dtype, h->X, N, h->ld, h->p, h->colscale, h->G, gram_ws, num_sms > 0 ? num_sms : 1,
+                          h->err, h->s0));
   }
+  if (h->tensor_sched) check(hs::gram_pairs_launch(h->G, h->p, h->P, h->G2, h->s0));
   if (e == cudaSuccess) {
     const int st = sync_and_check(h);
+    cudaFree(gram_ws);
+    gram_ws = nullptr;
     if (st != HS_OK) {
       destroy(h);
       fail(st);
       return nullptr;
     }
+  }
+  if (gram_ws) {
+    cudaStreamSynchronize(h->s0);
+    cudaFree(gram_ws);
   }
   if (e != cudaSuccess) {
     int st = cuda_status(e);
@@ -767,7 +849,12 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
     return nullptr;
   }
   // per chain: shrink, the factorization, two draws, commit; then the X-stream and its reduce
-  const int64_t chol_l = hs::chol_launch_count(h->P, h->cfg.chol_arith, h->chol_grid);
+  int64_t chol_l = hs::chol_launch_count(h->P, h->cfg.chol_arith, h->chol_grid);
+  if (h->tensor_sched) {
+    chol_l = 0;
+    for (int b = 0; b < (int)h->blk_off.size(); ++b)
+      chol_l += 1 + (hs::chol_trail_items(h->P, b, 0, h->T, h->K) > 0 ? 1 : 0);
+  }
   // shrink, factorization (one launch for every chain when single-launch), two draws, commits
   h->launches = 1 + ((h->K > 1 && h->chol_grid > 0) ? chol_l : h->K * chol_l) + 2 +
                 (h->K > 1 ? 2 : 1) +
@@ -1007,6 +1094,38 @@ int64_t hs_chol_task_list(int32_t T, int32_t workers, int32_t inverse, int32_t* 
     return HS_EINVAL;
   try {
     const std::vector<int> list = hs::chol_task_codes(T, workers, inverse != 0);
+    const int64_t n = (int64_t)list.size();
+    for (int64_t t = 0; t < n && t < max_codes; ++t) codes[t] = list[(size_t)t];
+    return n;
+  } catch (...) {
+    return HS_ENOMEM;
+  }
+}
+
+int hs_probit_debug_factor(hs_probit* h, int chain, double* L_out) {
+  if (!h || !L_out || chain < 0 || chain >= h->K) return HS_EINVAL;
+  if (h->cfg.chol_arith != HS_CHOL_DF32) return HS_EUNSUPPORTED;
+  DeviceGuard dg(h->device);
+  if (cudaStreamSynchronize(h->s0) != cudaSuccess || cudaStreamSynchronize(h->s1) != cudaSuccess) return HS_ECUDA;
+  const size_t P2 = (size_t)h->P * h->P;
+  std::vector<float> pairs(2 * P2);
+  if (cudaMemcpy(pairs.data(), h->A + chain * P2, P2 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HS_ECUDA;
+  for (size_t e = 0; e < P2; ++e) L_out[e] = (double)pairs[2 * e] + (double)pairs[2 * e + 1];
+  return HS_OK;
+}
+
+int hs_probit_debug_error_word(const hs_probit* h, int* word) {
+  if (!h || !word) return HS_EINVAL;
+  *word = h->last_err_word;
+  return HS_OK;
+}
+
+int64_t hs_chol_block_task_list(int32_t T, int32_t k0, int32_t k1, int32_t* codes, int64_t max_codes) {
+  if (T < 1 || T > 256 || k0 < 0 || k1 <= k0 || k1 > T || max_codes < 0 || (max_codes > 0 && !codes))
+    return HS_EINVAL;
+  try {
+    const std::vector<int> list = hs::chol_block_task_codes(T, k0, k1);
     const int64_t n = (int64_t)list.size();
     for (int64_t t = 0; t < n && t < max_codes; ++t) codes[t] = list[(size_t)t];
     return n;

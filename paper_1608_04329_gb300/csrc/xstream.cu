@@ -198,6 +198,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- producer ----------------
     if (lane == 0) {
       const unsigned char* X = static_cast<const unsigned char*>(a.X);
+      // X is read once per sweep: keep the factorization's tiles (running
+      // beside this kernel) in L2 instead
+      const uint64_t policy = l2_evict_first_policy();
       int64_t it = 0;
       for (int64_t t = t0; t < t1; ++t, ++it) {
         const int s = (int)(it % nstage);
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int rows = (int)min((int64_t)R, a.N - t * R);
         const uint32_t bytes = (uint32_t)(rows * row_bytes);
         mbar_arrive_expect_tx(&full[s], bytes);
-        bulk_g2s(smem + (size_t)s * stage_bytes, X + (size_t)t * R * row_bytes, bytes, &full[s]);
+        bulk_g2s_hint(smem + (size_t)s * stage_bytes, X + (size_t)t * R * row_bytes, bytes, &full[s], policy);
       }
       s_issued = it;
     }
@@ -404,87 +407,36 @@ int grid_dtype(int ld, int64_t N, int num_sms) {
 }
 
 // ---- second stage: fixed-order FP64 sum of the per-CTA partials -------------
+// Block of 32 columns x 8 groups: thread (g, c) adds the partial rows
+// g, g + 8, g + 16, ... of its column, then group 0 adds the 8 group sums in
+// order, so the sum is the same every sweep and the loads of a column are in
+// flight 8 at a time.
+constexpr int kRedCols = 32, kRedGroups = 8;
 template <typename CT>
-__global__ void reduce_partials_kernel(const CT* __restrict__ part, int grid, int ld, int p,
-                                       const float* __restrict__ colscale, double* __restrict__ xtz) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= p) return;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int c = 0;
-  for (; c + 4 <= grid; c += 4) {
-    s0 += (double)part[(size_t)(c + 0) * ld + j];
-    s1 += (double)part[(size_t)(c + 1) * ld + j];
-    s2 += (double)part[(size_t)(c + 2) * ld + j];
-    s3 += (double)part[(size_t)(c + 3) * ld + j];
-  }
-  for (; c < grid; ++c) s0 += (double)part[(size_t)c * ld + j];
-  double s = (s0 + s1) + (s2 + s3);
-  if (colscale) s *= (double)colscale[j];
-  xtz[j] = s;
-}
-
-// ---- one-time Gram matrix G = X^T X in FP64 (Sect. 5, beta update, step i) --
-template <int XD>
-__device__ __forceinline__ double load_x(const void* X, size_t idx, const float* colscale, int j) {
-  if constexpr (XD == HS_X_F64) {
-    return static_cast<const double*>(X)[idx];
-  } else if constexpr (XD == HS_X_F32) {
-    return (double)static_cast<const float*>(X)[idx];
-  } else if constexpr (XD == HS_X_BF16) {
-    const uint16_t b = static_cast<const uint16_t*>(X)[idx];
-    return (double)__uint_as_float((uint32_t)b << 16);
-  } else {
-    const uint8_t q = static_cast<const uint8_t*>(X)[idx];
-    const __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3);
-    return (double)__half2float(*reinterpret_cast<const __half*>(&hr)) * (double)colscale[j];
-  }
-}
-
-constexpr int kGT = 32;  // Gram tile
-template <int XD>
-__global__ void __launch_bounds__(256) gram_kernel(const void* __restrict__ X, int64_t N, int ld, int p,
-                                                   const float* __restrict__ colscale, double* __restrict__ G) {
-  // lower-triangular tile index -> (bi, bj), bj <= bi
-  const int t = blockIdx.x;
-  int bi = (int)((sqrt(8.0 * t + 1.0) - 1.0) / 2.0);
-  while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
-  while (bi * (bi + 1) / 2 > t) --bi;
-  const int bj = t - bi * (bi + 1) / 2;
-  __shared__ double sa[kGT][kGT + 1];
-  __shared__ double sb[kGT][kGT + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double c00 = 0, c01 = 0, c10 = 0, c11 = 0;
-  for (int64_t r0 = 0; r0 < N; r0 += kGT) {
-    for (int e = threadIdx.x; e < kGT * kGT; e += 256) {
-      const int rr = e / kGT, cc = e % kGT;
-      const int64_t row = r0 + rr;
-      const int ja = bi * kGT + cc, jb = bj * kGT + cc;
-      sa[rr][cc] = (row < N && ja < p) ? load_x<XD>(X, (size_t)row * ld + ja, colscale, ja) : 0.0;
-      sb[rr][cc] = (row < N && jb < p) ? load_x<XD>(X, (size_t)row * ld + jb, colscale, jb) : 0.0;
+__global__ void __launch_bounds__(kRedCols * kRedGroups)
+    reduce_partials_kernel(const CT* __restrict__ part, int grid, int ld, int p, const float* __restrict__ colscale,
+                           double* __restrict__ xtz) {
+  __shared__ double s_grp[kRedGroups][kRedCols];
+  const int c = threadIdx.x % kRedCols, g = threadIdx.x / kRedCols;
+  const int j = blockIdx.x * kRedCols + c;
+  double s0 = 0.0, s1 = 0.0;
+  if (j < p) {
+    int b = g;
+    for (; b + kRedGroups < grid; b += 2 * kRedGroups) {
+      s0 += (double)part[(size_t)b * ld + j];
+      s1 += (double)part[(size_t)(b + kRedGroups) * ld + j];
     }
-    __syncthreads();
-#pragma unroll 8
-    for (int rr = 0; rr < kGT; ++rr) {
-      const double a0 = sa[rr][2 * ty], a1 = sa[rr][2 * ty + 1];
-      const double b0 = sb[rr][2 * tx], b1 = sb[rr][2 * tx + 1];
-      c00 = fma(a0, b0, c00);
-      c01 = fma(a0, b1, c01);
-      c10 = fma(a1, b0, c10);
-      c11 = fma(a1, b1, c11);
-    }
-    __syncthreads();
+    if (b < grid) s0 += (double)part[(size_t)b * ld + j];
   }
-  const double c[2][2] = {{c00, c01}, {c10, c11}};
+  s_grp[g][c] = s0 + s1;
+  __syncthreads();
+  if (g == 0 && j < p) {
+    double s = 0.0;
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const int i = bi * kGT + 2 * ty + a, j = bj * kGT + 2 * tx + b;
-      if (i < p && j < p) {
-        G[(size_t)i * p + j] = c[a][b];
-        G[(size_t)j * p + i] = c[a][b];
-      }
-    }
+    for (int q = 0; q < kRedGroups; ++q) s += s_grp[q][c];
+    if (colscale) s *= (double)colscale[j];
+    xtz[j] = s;
+  }
 }
 
 __global__ void check_y_kernel(const uint8_t* __restrict__ y, int64_t N, int* err) {
@@ -532,27 +484,13 @@ cudaError_t xstream_launch(int x_dtype, const XStreamArgs& a, int grid, cudaStre
 
 cudaError_t reduce_partials_launch(int x_dtype, const void* partials, int grid, int ld, int p,
                                    const float* colscale, double* xtz, cudaStream_t s) {
-  const int nb = (p + 255) / 256;
+  const int nb = (p + kRedCols - 1) / kRedCols;
   if (x_dtype == HS_X_F64)
-    reduce_partials_kernel<double><<<nb, 256, 0, s>>>(static_cast<const double*>(partials), grid, ld, p,
-                                                      colscale, xtz);
+    reduce_partials_kernel<double><<<nb, kRedCols * kRedGroups, 0, s>>>(static_cast<const double*>(partials), grid,
+                                                                         ld, p, colscale, xtz);
   else
-    reduce_partials_kernel<float><<<nb, 256, 0, s>>>(static_cast<const float*>(partials), grid, ld, p,
-                                                     colscale, xtz);
-  return cudaGetLastError();
-}
-
-cudaError_t gram_launch(int x_dtype, const void* X, int64_t N, int ld, int p, const float* colscale, double* G,
-                        cudaStream_t s) {
-  const int T = (p + kGT - 1) / kGT;
-  const int nt = T * (T + 1) / 2;
-  switch (x_dtype) {
-    case HS_X_F64: gram_kernel<HS_X_F64><<<nt, 256, 0, s>>>(X, N, ld, p, colscale, G); break;
-    case HS_X_F32: gram_kernel<HS_X_F32><<<nt, 256, 0, s>>>(X, N, ld, p, colscale, G); break;
-    case HS_X_BF16: gram_kernel<HS_X_BF16><<<nt, 256, 0, s>>>(X, N, ld, p, colscale, G); break;
-    case HS_X_FP8E4M3: gram_kernel<HS_X_FP8E4M3><<<nt, 256, 0, s>>>(X, N, ld, p, colscale, G); break;
-    default: return cudaErrorInvalidValue;
-  }
+    reduce_partials_kernel<float><<<nb, kRedCols * kRedGroups, 0, s>>>(static_cast<const float*>(partials), grid, ld,
+                                                                        p, colscale, xtz);
   return cudaGetLastError();
 }
 

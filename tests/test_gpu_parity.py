@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from tests.gpu_common import (assert_transition_close, gpu_transition, lib_pkg, oracle_transition, problem,
-                              random_state)
+                              random_state, x_f64)
 
 pytestmark = pytest.mark.gpu
 
@@ -94,6 +94,25 @@ def test_trajectory_fp64(pkg):
     np.testing.assert_allclose(got["lambda_inv2"], st.lam_inv2, rtol=1e-8)
     np.testing.assert_allclose(got["tau_inv2"], st.tau_inv2, rtol=1e-8)
     assert got["k"] == 30
+
+
+@pytest.mark.parametrize("dt,N,p", [("f32", 5003, 257), ("f32", 2, 1), ("f64", 3001, 100), ("bf16", 4099, 130),
+                                    ("fp8", 2999, 200), ("f32", 40000, 64), ("bf16", 300, 1100), ("f64", 37, 33)])
+def test_gram_on_tensor_cores_matches_definition(pkg, dt, N, p):
+    """X^T X of the stored X from exact BF16 digit products on the tensor
+    cores: every entry within 1e-12 of sum_r |x_ri x_rj| of the FP64
+    definition (ragged tiles: p not a multiple of 64 or 128, N not a multiple
+    of the 32-row stage or the 128-row window), and exactly symmetric."""
+    d = problem(N, p, min(3, p), dt, seed=p + N)
+    s = pkg.HSProbit(d["X"], d["y"], seed=1, scales=d["scales"])
+    G = s.gram()
+    s.close()
+    X = x_f64(d)
+    ref = X.T @ X
+    nrm = np.abs(X).T @ np.abs(X)
+    err = np.abs(G - ref) / np.maximum(nrm, 1e-300)
+    assert err.max() <= 1e-12, (err.max(), np.unravel_index(err.argmax(), err.shape))
+    assert np.array_equal(G, G.T)
 
 
 def test_gram_matches_definition(pkg):
