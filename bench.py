@@ -497,6 +497,7 @@ def main(argv=None):
         t0 = time.perf_counter()
         s2 = pkg.HSProbit(Xh, yh, seed=1, chain=rank, device=local, use_graph=bool(args.graph), chol_arith=chol,
                           scales=d["scales"])
+        t_init = time.perf_counter() - t0
         d2h = 0
         for _ in range(args.steps):
             s2.sweep(1)
@@ -506,8 +507,8 @@ def main(argv=None):
         t_e2e = max_over_ranks(dist, time.perf_counter() - t0)
         e2e = {"value": ws * args.steps / t_e2e, "unit": "sweeps/s",
                "h2d_bytes_per_step": int((d["X"].nbytes + d["y"].nbytes) / args.steps),
-               "d2h_bytes_per_step": int(d2h / args.steps),
-               "includes": "init from pinned host X and y (H2D copy + FP64 Gram) amortised over the steps, "
+               "d2h_bytes_per_step": int(d2h / args.steps), "init_s": t_init,
+               "includes": "init from pinned host X and y (H2D copy + Gram on the tensor cores) amortised over the steps, "
                            "then per step one sweep and the D2H of its draw (beta, lambda^-2, tau^-2)"}
 
     # ---- K chains on BF16 X (tensor-core X-stream), same N and p ----

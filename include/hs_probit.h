@@ -61,12 +61,19 @@ extern "C" {
 #define HS_CHOL_DF32  1  /* FP32 pairs (~48-bit significand) on the FP32 pipe; default */
 
 /* ---- launch schedule of the HS_CHOL_DF32 factorization -------------------
- * Both schedules compute the same tiles with the same operations in the same
- * order, so their results are bit-identical. */
-#define HS_SCHED_AUTO     0  /* single launch where the device has cooperative launch, else columns */
+ * COLUMNS and SINGLE compute the same tiles with the same operations in the
+ * same order, so their results are bit-identical. */
+#define HS_SCHED_AUTO     0  /* TENSOR for several chains or p > 2016, else the single launch
+                                where the device has cooperative launch, else columns */
 #define HS_SCHED_COLUMNS  1  /* one launch per 32-wide block column (P / 32 launches) */
 #define HS_SCHED_SINGLE   2  /* one cooperative launch, tiles scheduled by data readiness;
                                 init fails with HS_EUNSUPPORTED where the device lacks it */
+#define HS_SCHED_TENSOR   3  /* block columns of 128: each block column factored by the
+                                readiness-scheduled FP32-pair tile tasks (one launch), the
+                                rank-128 updates of the matrix to its right as exact
+                                products of BF16 digits on the tensor cores (one launch);
+                                factor only, so beta comes by substitution (HS_BETA_SUBST
+                                or AUTO); not bit-identical to the other two schedules */
 
 /* ---- how beta is drawn from the factor -----------------------------------
  * beta = S L~^{-T} (L~^{-1} S X^T z + s) either way (Sect. 5, beta update);
@@ -197,6 +204,22 @@ int64_t hs_probit_launches_per_sweep(const hs_probit* h);
  * and the kernel returned normally) or HS_ECUDA.  Does not touch the state. */
 int hs_probit_debug_wait_timeout(hs_probit* h, int64_t max_spins);
 
+/* The factorization's work matrix of one chain after the last sweep (FP32
+ * pairs as doubles, P x P row-major with P = 32 ceil(p / 32), host): the
+ * tiles on and below the diagonal hold the factor L~ of the equilibrated
+ * precision matrix (strictly lower tiles; a diagonal tile holds the updated
+ * block it was factored from).  HS_EUNSUPPORTED for HS_CHOL_F64.  For
+ * diagnosis. */
+int hs_probit_debug_factor(hs_probit* h, int chain, double* L_out);
+
+/* The device error word the last hs_probit_sweep (or init) read back: the
+ * status bits behind HS_ENOTPD, HS_ENONFINITE, HS_ETIMEOUT, and, for a bounded
+ * wait that ran out, one bit per place that gave up (bit 8 + site: 0 and 1
+ * the factorization's diagonal chain, 2 its tile tasks, 3 to 5 the loads, MMA
+ * issue and epilogue of the tensor-core trailing updates, 6 the chain's SM
+ * election).  For diagnosis; *word receives it. */
+int hs_probit_debug_error_word(const hs_probit* h, int* word);
+
 /* The X-stream of one sweep on caller-owned buffers, allocating nothing.
  * (The paper has no counterpart; this is a deployment entry point.)
  *
@@ -250,6 +273,14 @@ int hs_probit_xstream_noalloc(int x_dtype, const void* X, int64_t ld, const uint
  * count, or HS_EINVAL (T outside 1..256, workers < 1, inverse not 0 or 1,
  * max_codes < 0, codes NULL with max_codes > 0). */
 int64_t hs_chol_task_list(int32_t T, int32_t workers, int32_t inverse, int32_t* codes, int64_t max_codes);
+
+/* The worker task list of one block-column launch of the HS_SCHED_TENSOR
+ * factorization (host only; no CUDA call): tile columns [k0, k1) of T tiles,
+ * the tasks C(i, k) and UA(i, j, k) with j < k1 in the order the kernel hands
+ * them out, as codes of hs_chol_task_list.  Writes min(count, max_codes)
+ * codes and returns the count, or HS_EINVAL (T outside 1..256, not
+ * 0 <= k0 < k1 <= T, max_codes < 0, codes NULL with max_codes > 0). */
+int64_t hs_chol_block_task_list(int32_t T, int32_t k0, int32_t k1, int32_t* codes, int64_t max_codes);
 
 /* ---- K chains on one X (Sect. 5 sweep for each chain; batched form) --------
  * A handle made with cfg.num_chains = K > 1 runs K independent chains on the

@@ -23,12 +23,12 @@ import numpy as np
 
 __all__ = ["HSProbit", "HSProbitError", "load_library", "library_path", "STATUS",
            "X_F64", "X_F32", "X_BF16", "X_FP8E4M3", "CHOL_F64", "CHOL_DF32",
-           "SCHED_AUTO", "SCHED_COLUMNS", "SCHED_SINGLE", "BETA_AUTO", "BETA_INVERSE", "BETA_SUBST",
+           "SCHED_AUTO", "SCHED_COLUMNS", "SCHED_SINGLE", "SCHED_TENSOR", "BETA_AUTO", "BETA_INVERSE", "BETA_SUBST",
            "TN_INVCDF", "TN_REJECTION", "tn_sample"]
 
 X_F64, X_F32, X_BF16, X_FP8E4M3 = 0, 1, 2, 3
 CHOL_F64, CHOL_DF32 = 0, 1
-SCHED_AUTO, SCHED_COLUMNS, SCHED_SINGLE = 0, 1, 2
+SCHED_AUTO, SCHED_COLUMNS, SCHED_SINGLE, SCHED_TENSOR = 0, 1, 2, 3
 BETA_AUTO, BETA_INVERSE, BETA_SUBST = 0, 1, 2
 TN_INVCDF, TN_REJECTION = 0, 1
 STATUS = {0: "HS_OK", -1: "HS_EINVAL", -2: "HS_ENOMEM", -3: "HS_ECUDA", -4: "HS_ENOTPD",
@@ -100,6 +100,10 @@ _PROTOS = {
     "hs_probit_free": (None, [ctypes.c_void_p]),
     "hs_chol_task_list": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                            ctypes.c_int64]),
+    "hs_probit_debug_factor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "hs_probit_debug_error_word": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "hs_chol_block_task_list": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                                 ctypes.c_int64]),
     "hs_tn_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
                                     ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "hs_probit_xstream_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
@@ -292,6 +296,21 @@ class HSProbit:
 
     def launches_per_sweep(self) -> int:
         return int(self._lib.hs_probit_launches_per_sweep(self._h))
+
+    def debug_factor(self, chain: int = 0) -> np.ndarray:
+        """The factorization's P x P work matrix of one chain (lower tiles: the factor)."""
+        P = (self.p + 31) // 32 * 32
+        L = np.empty((P, P))
+        st = self._lib.hs_probit_debug_factor(self._h, int(chain), _ptr(L))
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_debug_factor")
+        return L
+
+    def debug_error_word(self) -> int:
+        """The raw device error word of the last sweep (status and wait-site bits)."""
+        w = ctypes.c_int()
+        self._lib.hs_probit_debug_error_word(self._h, ctypes.byref(w))
+        return int(w.value)
 
     def debug_wait_timeout(self, max_spins: int) -> int:
         return int(self._lib.hs_probit_debug_wait_timeout(self._h, int(max_spins)))

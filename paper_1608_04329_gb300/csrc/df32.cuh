@@ -14,6 +14,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
 
 namespace hs {
 
@@ -97,6 +99,28 @@ __host__ __device__ __forceinline__ void df_fma(float& sh, float& sl, df2 a, df2
   const float t = (sh - (s - bb)) + (p - bb);
   sh = s;
   sl += t + e;
+}
+
+// The six BF16 digits of a pair x with |x| <= 1 on the fixed grid 2^0:
+// x = sum_{t=1..6} d_t 2^{-8t} + rest, |rest| <= 2^{-49}, d_t = rint(256 r_{t-1})
+// with the remainder r kept as an exact pair (TwoSum after each step), so
+// |d_1| <= 256 and |d_t| <= 128 for t >= 2; each digit is an integer of at
+// most 8 significant bits, returned as its BF16 bit pattern (the low half of
+// its FP32 bits is zero).
+__host__ __device__ __forceinline__ void df_digits6(df2 x, uint16_t (&d)[6]) {
+  float rh = x.hi, rl = x.lo;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const float sh = rh * 256.0f, sl = rl * 256.0f;
+    const float dd = rintf(sh);
+    const float a = sh - dd;
+    const float s = a + sl, bb = s - a;
+    rl = (a - (s - bb)) + (sl - bb);
+    rh = s;
+    uint32_t bits;
+    memcpy(&bits, &dd, 4);
+    d[t] = (uint16_t)(bits >> 16);
+  }
 }
 
 __device__ __forceinline__ df2 df_shfl_xor(df2 v, int mask) {

@@ -16,6 +16,10 @@ enum : uint32_t { kPurZ = 1, kPurLambda = 2, kPurTau = 3, kPurBeta = 4, kPurNu =
 __device__ __forceinline__ void set_error(int* err, int bits) {
   if (err) atomicOr(err, bits);
 }
+// a bounded wait at `site` ran out
+__device__ __forceinline__ void set_timeout(int* err, int site) {
+  set_error(err, kErrTimeout | (1 << (kErrSiteShift + site)));
+}
 
 // ---- Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) --------------------
 // Ten rounds of (c0,c1,c2,c3) -> (hi(M1 c2)^c1^k0, lo(M1 c2), hi(M0 c0)^c3^k1,
@@ -169,6 +173,22 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+// The same with an L2 eviction-priority policy (createpolicy).
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+// Data read once: evicted from L2 first, so it does not push out the working
+// sets of kernels running beside it.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
 __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");

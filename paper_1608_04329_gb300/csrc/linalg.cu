@@ -792,7 +792,7 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 // timeout bit is set and the abort word raised) or another block gave up.
 template <int N>
 __device__ bool block_wait(const unsigned long long* const (&p)[N], const unsigned long long (&target)[N],
-                           const PSync& ps, unsigned long long e, int* err) {
+                           const PSync& ps, unsigned long long e, int* err, int site = kSiteChainStep) {
   int ok = 1;
   if (threadIdx.x == 0) {
     unsigned long long v[N];
@@ -808,7 +808,7 @@ __device__ bool block_wait(const unsigned long long* const (&p)[N], const unsign
             break;
           }
           if (global_ns() - t0 > 2000000000ull) {
-            set_error(err, kErrTimeout);
+            set_timeout(err, site);
             st_release_u64(ps.abort, e);
             ok = 0;
             break;
@@ -822,10 +822,10 @@ __device__ bool block_wait(const unsigned long long* const (&p)[N], const unsign
   return __syncthreads_and(ok) != 0;
 }
 __device__ __forceinline__ bool block_wait(const unsigned long long* p, unsigned long long target, const PSync& ps,
-                                           unsigned long long e, int* err) {
+                                           unsigned long long e, int* err, int site = kSiteChainStep) {
   const unsigned long long* const pp[1] = {p};
   const unsigned long long tt[1] = {target};
-  return block_wait<1>(pp, tt, ps, e, err);
+  return block_wait<1>(pp, tt, ps, e, err, site);
 }
 
 // All threads' global writes of the block become visible before *p = v.
@@ -1070,7 +1070,7 @@ __device__ bool gwait(const Grp& g, const unsigned long long* const (&p)[N], con
             break;
           }
           if (global_ns() - t0 > 2000000000ull) {
-            set_error(err, kErrTimeout);
+            set_timeout(err, kSiteTask);
             st_release_u64(ps.abort, e);
             ok = 0;
             break;
@@ -1094,15 +1094,32 @@ __device__ __forceinline__ void gpublish(const Grp& g, unsigned long long* p, un
 // The buffers of one chain of the launch.
 struct ChainView {
   df2 *A, *Linv, *LinvT;
+  uint16_t* dig;  // this chain's six digit planes, or nullptr
   DFCtx cx;
   PSync ps;
   __device__ ChainView(const CholArgs& a, int m, int T)
       : A(reinterpret_cast<df2*>(a.A) + (size_t)m * a.P * a.P),
         Linv(reinterpret_cast<df2*>(a.Linv) + (size_t)m * a.P * a.P),
         LinvT(reinterpret_cast<df2*>(a.LinvT) + (size_t)m * a.P * a.P),
+        dig(a.digits ? static_cast<uint16_t*>(a.digits) + (size_t)m * 6 * a.P * a.P : nullptr),
         cx{a.p, a.P, a.G, a.S + (size_t)m * a.P, a.lam_new + (size_t)m * a.p, a.tau_new[m]},
         ps(a.sync + (size_t)m * a.sync_words, T) {}
 };
+
+// The six BF16 digit planes of factor tile (ti, tk), from a tile in shared
+// memory; threads t0, t0 + nthr, ... of the caller (read by chol_trail_kernel).
+__device__ __forceinline__ void tile_digits_store(int t0, int nthr, const df2 (*Tl)[NB + 1], uint16_t* dig, int P,
+                                                  int ti, int tk) {
+  const size_t plane = (size_t)P * P;
+  for (int e = t0; e < NB * NB; e += nthr) {
+    const int r = e >> 5, c = e & 31;
+    uint16_t d[6];
+    df_digits6(Tl[r][c], d);
+    uint16_t* dst = dig + (size_t)(ti * NB + r) * P + tk * NB + c;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) dst[t * plane] = d[t];
+  }
+}
 
 constexpr int kPersistTiles = 6;  // chain: 5 tiles; workers: 3 per group
 constexpr size_t kPersistSmem = kPersistTiles * sizeof(DTile);
@@ -1125,14 +1142,19 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
   const int P = a.P;
   const int nch = a.nchains > 1 ? a.nchains : 1;
   const bool inv = a.inverse != 0;
+  // tile columns of this launch: all, or one block column whose trailing
+  // updates the tensor cores apply between launches
+  const int kb = a.k1 > 0 ? a.k0 : 0, ke = a.k1 > 0 ? a.k1 : T;
   const PSync ps0(a.sync, T);  // chain 0's words also hold the launch-wide header
   unsigned int smid;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
   if (threadIdx.x == 0) {
-    const unsigned long long e0 = *ps0.epoch + 1;  // (kernel-ordered after the previous launch's update)
+    // (kernel-ordered after the previous launch's update); the block-column
+    // launches of one factorization share the epoch of its first launch
+    const unsigned long long e0 = *ps0.epoch + (kb == 0 ? 1ull : 0ull);
     s_e = e0;
     int role = 0, chain = 0;
-    if (nch == 1) {
+    if (nch == 1 && a.k1 == 0) {
       // The chain goes to a block on an SM the X-stream left free (no mark
       // of this sweep), else to the last block to start.
       const unsigned int stamp = (unsigned int)(*a.k_dev + 1);
@@ -1145,7 +1167,8 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
       }
       if (role == 1) st_release_u64(ps0.chain_sm, (e0 << 16) | smid);
     } else {
-      // several chains: the first nch blocks to start walk the diagonal chains
+      // several chains, or block-column launches: the first nch blocks to
+      // start walk the diagonal chains
       const unsigned long long st = atomicAdd(ps0.start, 1ull);
       if (st == gridDim.x - 1) *ps0.start = 0;
       if (st < (unsigned long long)nch) {
@@ -1159,10 +1182,10 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
   __syncthreads();
   const unsigned long long e = s_e;
   const unsigned long long base = e * kEpochStride;
-  if (nch == 1 && s_role == 0 && gridDim.x >= 16) {
+  if (nch == 1 && a.k1 == 0 && s_role == 0 && gridDim.x >= 16) {
     // Blocks that share the chain's SM stay idle, leaving it the whole SM
     // (at most 3 of them: 4 blocks fit on an SM).
-    if (block_wait(ps0.chain_sm, e << 16, ps0, e, a.err)) {
+    if (block_wait(ps0.chain_sm, e << 16, ps0, e, a.err, kSiteStartRole)) {
       if (threadIdx.x == 0 && (unsigned)(ld_acquire_u64(ps0.chain_sm) & 0xFFFFu) == smid) s_role = 2;
     } else if (threadIdx.x == 0) {
       s_role = 2;
@@ -1179,30 +1202,50 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
     const DFCtx& cx = cv.cx;
     const PSync& ps = cv.ps;
     // Entering step k, sD holds D_k = A_kk after all k updates.
-    tile_load_gram(sD, cx, 0, 0);
+    bool go = true;
+    if (kb == 0) {
+      tile_load_gram(sD, cx, 0, 0);
+    } else {
+      // the first diagonal tile of a later block column, after the tensor-core updates
+      go = block_wait(&ps.cntA[kb * T + kb], base + (unsigned long long)kb, ps0, e, a.err, kSiteChainStart);
+      if (go) {
+        const TileRef t[1] = {{A, kb, kb, false, sD}};
+        tiles_load_cg<1>(t, P);
+      }
+    }
     __syncthreads();
-    for (int k = 0; k < T; ++k) {
+    for (int k = kb; k < ke && go; ++k) {
       potri_df(sD, sLi, sX1, s_piv, s_rs, a.err, true);  // sLi <- L_kk^{-1}, sX1 <- its transpose
       tile_store_cg(Linv, P, k, k, sLi, false);
       tile_store_cg(LinvT, P, k, k, sLi, true);
       block_publish(&ps.flagLi[k], e);
       if (k + 1 == T) break;
+      // the next tile row starts the next block column: its diagonal tile
+      // takes this block column's updates on the tensor cores
+      const bool last = (k + 1 == ke);
       // A_{k+1,k} and A_{k+1,k+1} after updates 0..k-1 (workers)
       if (k >= 1) {
         const unsigned long long* const wp2[2] = {&ps.cntA[(k + 1) * T + k], &ps.cntA[(k + 1) * T + k + 1]};
-        const unsigned long long wt2[2] = {base + (unsigned long long)k, base + (unsigned long long)k};
+        const unsigned long long wt2[2] = {base + (unsigned long long)k, last ? 0ull : base + (unsigned long long)k};
         if (!block_wait<2>(wp2, wt2, ps0, e, a.err)) break;
-        const TileRef t[2] = {{A, k + 1, k, false, sW}, {A, k + 1, k + 1, false, sD}};
-        tiles_load_cg<2>(t, P);
+        if (last) {
+          const TileRef t[1] = {{A, k + 1, k, false, sW}};
+          tiles_load_cg<1>(t, P);
+        } else {
+          const TileRef t[2] = {{A, k + 1, k, false, sW}, {A, k + 1, k + 1, false, sD}};
+          tiles_load_cg<2>(t, P);
+        }
       } else {
         tile_load_gram(sW, cx, 1, 0);
-        tile_load_gram(sD, cx, 1, 1);
+        if (!last) tile_load_gram(sD, cx, 1, 1);
       }
       __syncthreads();
       tile_mma<false>(sLi, sW, sX1);  // L_{k+1,k} = A_{k+1,k} L_kk^{-T}
       tile_store_cg(A, P, k + 1, k, sLi, false);
       if (!inv) tile_store_cg(LinvT, P, k, k + 1, sLi, true);
+      if (last && cv.dig) tile_digits_store(threadIdx.x, blockDim.x, sLi, cv.dig, P, k + 1, k);
       block_publish(&ps.flagL[(k + 1) * T + k], e);
+      if (last) break;
       for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) sX2[t & 31][t >> 5] = sLi[t >> 5][t & 31];
       __syncthreads();
       tile_mma<true>(sD, sLi, sX2);  // D_{k+1} = A_{k+1,k+1} - L_{k+1,k} L_{k+1,k}^T
@@ -1217,7 +1260,9 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
       }
     }
     __syncthreads();
-    const int total1 = s_step0[T];
+    // a block-column launch runs exactly its list (which may be empty: a
+    // last block column of one tile has no worker task)
+    const int total1 = a.k1 > 0 ? a.ntasks : s_step0[T];
     const long long total = (long long)total1 * nch;  // task t: chain t % nch, its list entry t / nch
     const int gi = threadIdx.x >> 7;                  // two groups of four warps, one task each
     const Grp g{(int)(threadIdx.x & 127), 1 + gi};
@@ -1305,6 +1350,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         gmma<false>(g, gX2, gW, gX1, tile_rows(cx.p, i));
         gstore_cg(g, A, P, i, k, gX2, false);
         if (!inv) gstore_cg(g, LinvT, P, k, i, gX2, true);
+        if (cv.dig && i >= ke) tile_digits_store(g.t, 128, gX2, cv.dig, P, i, k);
         gpublish(g, &ps.flagL[i * T + k], e);
         continue;
       }
@@ -1946,6 +1992,22 @@ std::vector<int> chol_task_codes(int T, int workers, bool inverse) {
     t = kind | (k << 2) | (i << 10) | (j << 18);
   }
   return order;
+}
+
+std::vector<int> chol_block_task_codes(int T, int k0, int k1) {
+  std::vector<int> out;
+  auto code = [](int kind, int i, int j, int k) { return kind | (k << 2) | (i << 10) | (j << 18); };
+  // step by step: the panel tiles C(i, k) below the chain's own L_{k+1,k}, then
+  // the updates of the block column's later tile columns (the chain applies the
+  // last update of the next diagonal tile itself).  Every task waits only on
+  // tasks before it in the list or on the diagonal chain.
+  for (int k = k0; k < k1; ++k) {
+    for (int i = k + 2; i < T; ++i) out.push_back(code(0, i, k, k));
+    for (int j = k + 1; j < k1; ++j)
+      for (int i = j; i < T; ++i)
+        if (!(i == k + 1 && j == k + 1)) out.push_back(code(2, i, j, k));
+  }
+  return out;
 }
 
 int chol_launch_count(int P, int arith, int persistent_grid) {

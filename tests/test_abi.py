@@ -131,7 +131,7 @@ def test_tn_sample_rejects_bad_arguments_on_host(lib):
     ("num_chains", 4, "f32", 64, -8),        # the batched form needs BF16 X
     ("num_chains", 4, "bf16", 1537, -8),     # and p <= 1536 (TMEM columns)
     ("beta_solve", 3, "f32", 64, -1),        # unknown beta form
-    ("chol_sched", 3, "f32", 64, -1),        # unknown schedule
+    ("chol_sched", 4, "f32", 64, -1),        # unknown schedule
 ])
 def test_init_rejects_bad_config_on_host(lib, field, value, dtype, p, status):
     import paper_1608_04329_gb300 as pkg

@@ -89,3 +89,40 @@ def test_task_list_rejects_bad_arguments(lib):
     assert lib.hs_chol_task_list(8, 0, 1, None, 0) == -1
     assert lib.hs_chol_task_list(8, 4, 2, None, 0) == -1
     assert lib.hs_chol_task_list(8, 4, 1, None, 5) == -1
+
+
+def _block_tasks(T, k0, k1):
+    out = set()
+    for k in range(k0, k1):
+        out |= {(0, i, k, k) for i in range(k + 2, T)}
+        out |= {(2, i, j, k) for j in range(k + 1, k1) for i in range(j, T) if not (i == j == k + 1)}
+    return out
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 5, 7, 8, 17, 32, 125])
+def test_block_column_task_lists(lib, T):
+    """The tensor-core schedule's block-column launches (tile columns
+    [4b, 4b + 4)): each list holds the panel tiles C(i, k) and the updates
+    UA(i, j, k) of the block column's later tile columns exactly once, every
+    task after the tasks of the same launch it reads (the updates of earlier
+    block columns come from the tensor-core launches between them)."""
+    for k0 in range(0, T, 4):
+        k1 = min(k0 + 4, T)
+        n = lib.hs_chol_block_task_list(T, k0, k1, None, 0)
+        want = _block_tasks(T, k0, k1)
+        assert n == len(want)
+        codes = np.zeros(max(n, 1), dtype=np.int32)
+        assert lib.hs_chol_block_task_list(T, k0, k1, codes.ctypes.data, n) == n
+        got = []
+        for c in codes[:n].tolist():
+            kind, k, i, j = c & 3, (c >> 2) & 0xFF, (c >> 10) & 0xFF, (c >> 18) & 0xFF
+            got.append((kind, i, j, k) if kind == 2 else (kind, i, k, k))
+        assert len(set(got)) == n and set(got) == want
+        pos = {t: p for p, t in enumerate(got)}
+        for t in got:
+            for d in _deps(t):
+                if d[3] >= k0:  # tasks of this launch
+                    assert d in pos, (t, d)
+                    assert pos[d] < pos[t], (t, d)
+    assert lib.hs_chol_block_task_list(8, 4, 4, None, 0) == -1
+    assert lib.hs_chol_block_task_list(8, 0, 9, None, 0) == -1

@@ -218,3 +218,35 @@ def test_batched_posterior_mean_error_vs_fp64_oracle():
           f"the unrounded X, of which BF16 storage of X alone accounts for {np.abs(m_ora4 - m_unr).max():.3e}; "
           f"Monte Carlo standard error of the 32-chain estimate {se:.3e}")
     assert err <= 1e-3, err
+
+
+@pytest.mark.parametrize("dt,N,p,K", [("bf16", 3001, 200, 4),    # 7 tiles: two block columns, the last ragged
+                                      ("bf16", 2000, 520, 2),    # 17 tiles: five block columns
+                                      ("bf16", 4099, 1000, 8),
+                                      ("f32", 3001, 300, 1)])    # one chain
+def test_tensor_core_trailing_updates_match_pair_arithmetic(pkg, dt, N, p, K):
+    """The block-column schedule (HS_SCHED_TENSOR: tile tasks in FP32-pair
+    arithmetic inside each 128-column block, the rank-128 updates to its right
+    as exact products of BF16 digits on the tensor cores) against the
+    single-launch schedule that applies every tile update in FP32-pair
+    arithmetic; both factor only, beta by substitution, from the same state
+    per chain.  The factor's updates carry about 48 bits either way, so beta
+    agrees to 1e-11 relative; lambda^{-2} and tau^{-2} (drawn before the
+    factorization) agree exactly."""
+    d = problem(N, p, 5, dt, seed=p)
+    states = [random_state(p, k=3, seed=40 + m) for m in range(K)]
+    out = {}
+    for sched in (pkg.SCHED_SINGLE, pkg.SCHED_TENSOR):
+        s = pkg.HSProbit(d["X"], d["y"], seed=7, num_chains=K, chol_sched=sched, beta_solve=pkg.BETA_SUBST)
+        try:
+            for m, st in enumerate(states):
+                s.set_state(st.beta, st.lam_inv2, st.nu_inv, st.tau_inv2, st.xi_inv, st.k, chain=m)
+            s.sweep(1)
+            out[sched] = [s.get_state(chain=m) for m in range(K)]
+        finally:
+            s.close()
+    for m in range(K):
+        a, b = out[pkg.SCHED_SINGLE][m], out[pkg.SCHED_TENSOR][m]
+        assert np.array_equal(a["lambda_inv2"], b["lambda_inv2"]) and a["tau_inv2"] == b["tau_inv2"]
+        db = np.linalg.norm(a["beta"] - b["beta"]) / np.linalg.norm(a["beta"])
+        assert db <= 1e-11, (m, db)
