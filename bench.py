@@ -83,8 +83,10 @@ def barrier(dist):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms; the samples
+    whose own timestamps fall in the timed region are kept (nvidia-smi's
+    output reaches the pipe in blocks, so arrival times say nothing)."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -92,7 +94,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []          # (arrival time, line)
-        self.window = None       # (t0, t1) of the timed region, host monotonic clock
+        self.window = None       # (t0, t1) of the timed region, host wall clock
 
     def __enter__(self):
         try:
@@ -114,9 +116,17 @@ class ClockSampler:
             self.lines.append((time.monotonic(), line.strip()))
 
     def mark(self, start: bool):
-        """Host time of the start (start=True) or end of the timed region."""
-        now = time.monotonic()
+        """Host wall-clock time of the start (start=True) or end of the timed region."""
+        now = time.time()
         self.window = (now, None) if start else (self.window[0] if self.window else now, now)
+
+    @staticmethod
+    def _stamp(field: str):
+        import datetime
+        try:
+            return datetime.datetime.strptime(field.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -129,20 +139,21 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        lines = self.lines
-        if self.window and self.window[1] is not None:
-            # samples that arrived during the timed region (plus one sampling period after it)
-            inside = [ln for t, ln in lines if self.window[0] <= t <= self.window[1] + 0.025]
-            if not inside:
-                after = [ln for t, ln in lines if t >= self.window[0]]
-                inside = after[:1]
-            lines = inside
-        else:
-            lines = [ln for _, ln in lines]
-        for ln in lines:
+        rows = []
+        for _, ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
+            if len(f) >= 10:
+                rows.append((self._stamp(f[0]), f[1:]))
+        if self.window and self.window[1] is not None:
+            # samples stamped inside the timed region (one sampling period of slack on each side)
+            t0, t1 = self.window
+            inside = [r for ts, r in rows if ts is not None and t0 - 0.02 <= ts <= t1 + 0.02]
+            if not inside:  # none in a region shorter than the period: the nearest after its start
+                later = sorted((ts, r) for ts, r in rows if ts is not None and ts >= t0)
+                inside = [later[0][1]] if later else []
+        else:
+            inside = [r for _, r in rows]
+        for f in inside:
             try:
                 sm.append(float(f[1]))
                 mx.append(float(f[2]))
