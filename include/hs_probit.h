@@ -277,10 +277,13 @@ int64_t hs_chol_task_list(int32_t T, int32_t workers, int32_t inverse, int32_t* 
 /* The worker task list of one block-column launch of the HS_SCHED_TENSOR
  * factorization (host only; no CUDA call): tile columns [k0, k1) of T tiles,
  * the tasks C(i, k) and UA(i, j, k) with j < k1 in the order the kernel hands
- * them out, as codes of hs_chol_task_list.  Writes min(count, max_codes)
- * codes and returns the count, or HS_EINVAL (T outside 1..256, not
- * 0 <= k0 < k1 <= T, max_codes < 0, codes NULL with max_codes > 0). */
-int64_t hs_chol_block_task_list(int32_t T, int32_t k0, int32_t k1, int32_t* codes, int64_t max_codes);
+ * them out (a list schedule for `workers` concurrent tasks, like
+ * hs_chol_task_list), as codes of hs_chol_task_list.  Writes
+ * min(count, max_codes) codes and returns the count, or HS_EINVAL (T outside
+ * 1..256, not 0 <= k0 < k1 <= T, workers < 1, max_codes < 0, codes NULL with
+ * max_codes > 0). */
+int64_t hs_chol_block_task_list(int32_t T, int32_t k0, int32_t k1, int32_t workers, int32_t* codes,
+                                int64_t max_codes);
 
 /* ---- K chains on one X (Sect. 5 sweep for each chain; batched form) --------
  * A handle made with cfg.num_chains = K > 1 runs K independent chains on the

@@ -25,11 +25,13 @@
 // subtracts it from the stored tile.
 //
 // One CTA per SM loops over work items (chain, 128-row strip, 64-column pair
-// of tiles): warp 0 lane 0 loads the digit tiles of two 32-column tiles of the
-// block per stage by TMA (128-byte swizzle, K-major), warp 1 lane 0 issues
+// of tiles): warp 0 lane 0 loads the digit tiles of one 32-column tile of the
+// block per stage by TMA into a ring of three stages (64-byte swizzle,
+// K-major), warp 1 lane 0 issues
 // tcgen05.mma (M 128, N 64, K 16), one TMEM accumulator of 64 columns per
-// class, warp 2 owns TMEM, warps 4-7 (one per 32-row tile of the strip) fold
-// the classes and write the tiles with their update counters.  Every wait is
+// class, warp 2 owns TMEM, warps 4-11 (one per 32 x 32 output tile, each
+// reading its tile's old values before the products finish) fold the classes
+// and write the tiles with their update counters.  Every wait is
 // bounded (2 s); a wait that runs out sets the timeout bit and the CTA winds down.
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -47,14 +49,15 @@ namespace {
 constexpr int NB = 32;                  // tile
 constexpr int kBlockTiles = 4;          // tiles per block column
 constexpr int kDigits = 6;
-constexpr int kStages = 1;
-constexpr int kKc = 64;                 // columns of the block per stage (two tiles; 128-byte rows)
-constexpr uint32_t kADigitBytes = 128 * kKc * 2;  // 128 rows x 64 columns of BF16: 16 KB
-constexpr uint32_t kBDigitBytes = 64 * kKc * 2;   // 64 rows: 8 KB
-constexpr uint32_t kStageBytes = kDigits * (kADigitBytes + kBDigitBytes);  // 144 KB
+constexpr int kStages = 3;
+constexpr int kKc = 32;                 // columns of the block per stage (one tile; 64-byte rows)
+constexpr uint32_t kADigitBytes = 128 * kKc * 2;  // 128 rows x 32 columns of BF16: 8 KB
+constexpr uint32_t kBDigitBytes = 64 * kKc * 2;   // 64 rows: 4 KB
+constexpr uint32_t kStageBytes = kDigits * (kADigitBytes + kBDigitBytes);  // 72 KB
 constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes;
 static_assert(kSmem <= 227 * 1024, "stages fit in shared memory");
-constexpr int kThreads = 256;
+constexpr int kEpiWarps = 8;            // warps 4..11: one 32 x 32 output tile each
+constexpr int kThreads = 128 + 32 * kEpiWarps;
 constexpr unsigned long long kEpochStride = 1024;  // as the readiness words of chol_persistent_kernel
 constexpr int kSyncHeader = 8;
 
@@ -87,9 +90,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// K-major operand in the 128-byte swizzled layout TMA writes (64 BF16 per
-// row, 8-row groups 1024 bytes apart); a K step of 16 moves the start by 32 bytes.
-__device__ __forceinline__ uint64_t kmaj_desc(uint32_t saddr) { return tc::sw128_desc(saddr, 16, 1024); }
+// K-major operand in the 64-byte swizzled layout TMA writes (32 BF16 per
+// row, 8-row groups 512 bytes apart; descriptor layout code 4); a K step of 16
+// moves the start by 32 bytes.
+__device__ __forceinline__ uint64_t kmaj_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) |
+         (4ull << 61);
+}
 
 // Work items of block column b: chain m, strip s >= b + 1 (tiles 4s..4s+3),
 // column pair jp (tiles 2jp, 2jp+1) with 2jp >= max(col_lo, 4(b + 1)),
@@ -135,14 +142,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int per_chain = is.per_chain();
   const int nitems = per_chain * a.nchains;
   const int k0 = kBlockTiles * a.b, k1 = min(k0 + kBlockTiles, T);
-  const int nk = (k1 - k0 + 1) / 2;  // stages per item (pairs of tile columns)
+  const int nk = k1 - k0;  // stages per item (tile columns of the block)
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&sh.full[s], 1);
       mbar_init(&sh.empty[s], 1);
     }
     mbar_init(&sh.acc_full, 1);
-    mbar_init(&sh.acc_empty, 128);
+    mbar_init(&sh.acc_empty, 32 * kEpiWarps);
     mbar_init(&sh.done, 1);
     sh.abort = 0;
     fence_mbar_init();
@@ -169,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (q >= kStages && !(ok = twait(&sh.empty[st], ((q / kStages) - 1) & 1, &sh, a.err, kSiteTrailLoad))) break;
         unsigned char* stg = base + (size_t)st * kStageBytes;
         mbar_arrive_expect_tx(&sh.full[st], kStageBytes);
-        const int x = NB * (k0 + 2 * kk);
+        const int x = NB * (k0 + kk);
 #pragma unroll
         for (int t = 0; t < kDigits; ++t) {
           const int plane = (m * kDigits + t) * a.P;
@@ -200,9 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::fence_after();
         const uint32_t sa = sbase + (uint32_t)st * kStageBytes;
         const uint32_t sb = sa + kDigits * kADigitBytes;
-        // K steps of 16 inside the block: the second tile column of the last
-        // stage may lie past the block (its loaded columns are not used)
-        const int nks = (k0 + 2 * kk + 1 < k1) ? kKc / 16 : NB / 16;
+        const int nks = kKc / 16;  // K steps of 16
 #pragma unroll
         for (int w = 2; w <= kDigits + 1; ++w) {
           int n = 0;
@@ -222,96 +227,98 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::mma_commit(&sh.done);
     mbar_wait(&sh.done, 0, 2000000000ull);  // nothing in flight when the CTA leaves
   } else if (warp >= 4) {
-    // ---------------- epilogue: one 32-row tile of the strip per warp ----------------
-    const int quad = warp & 3;
+    // ---------------- epilogue: one 32 x 32 output tile per warp ----------------
+    const int quad = warp & 3, jj = (warp - 4) >> 2;  // tile row 4s + quad, tile column 2jp + jj
     const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
     int n_item = 0;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++n_item) {
       const int m = it / per_chain;
       int s, jp;
       is.decode(it % per_chain, s, jp);
+      const int i = kBlockTiles * s + quad;  // tile row of this warp
+      const int j = 2 * jp + jj;             // tile column
+      const int r = NB * i + lane;           // matrix row of this thread
+      const bool live = i < T && j < T && j <= i;  // warp-uniform
+      df2* const A = static_cast<df2*>(a.A) + (size_t)m * a.P * a.P;
+      // the tile's current values (independent of the products: read before they finish)
+      df2 old[NB];
+      if (live) {
+        if (a.b == 0) {
+          // first touch: the equilibrated precision matrix, S (G + tau Lambda) S
+          const double* const S = a.S + (size_t)m * a.P;
+          const float sr = (float)S[r];
+#pragma unroll
+          for (int c = 0; c < NB; ++c) {
+            const int col = NB * j + c;
+            df2 v{0.0f, 0.0f};
+            if (r < a.p && col < a.p) {
+              const df2 g2 = static_cast<const df2*>(a.G2)[(size_t)r * a.P + col];
+              v = df_mul(df_mul(g2, df2{sr, 0.0f}), df2{(float)S[col], 0.0f});
+              if (r == col) v = df_add(v, df_split(S[r] * S[r] * a.tau_new[m] * a.lam_new[(size_t)m * a.p + r]));
+            } else if (r == col) {
+              v = df2{1.0f, 0.0f};
+            }
+            old[c] = v;
+          }
+        } else {
+          const float4* src = reinterpret_cast<const float4*>(A + (size_t)r * a.P + NB * j);
+#pragma unroll
+          for (int h = 0; h < NB / 2; ++h) {
+            const float4 v = __ldcg(src + h);
+            old[2 * h] = df2{v.x, v.y};
+            old[2 * h + 1] = df2{v.z, v.w};
+          }
+        }
+      }
       if (!twait(&sh.acc_full, n_item & 1, &sh, a.err, kSiteTrailEpi)) break;
       tc::fence_after();
-      const int i = kBlockTiles * s + quad;       // tile row of this warp
-      const int r = NB * i + lane;               // matrix row of this thread
-      df2* const A = static_cast<df2*>(a.A) + (size_t)m * a.P * a.P;
-      const double* const S = a.S + (size_t)m * a.P;
-      const double lam_r = (r < a.p) ? a.lam_new[(size_t)m * a.p + r] : 0.0;
-      const double tau = a.tau_new[m];
-      unsigned long long* const cntA = a.sync + (size_t)m * a.sync_words + kSyncHeader;
-#pragma unroll 1
-      for (int jj = 0; jj < 2; ++jj) {
-        const int j = 2 * jp + jj;
-        const bool live = i < T && j < T && j <= i;  // warp-uniform
-#pragma unroll 1
-        for (int g = 0; g < 4; ++g) {
-          uint32_t c[kDigits][8];
 #pragma unroll
-          for (int w = 0; w < kDigits; ++w) tc::tmem_ld8(tmem + lane_off + (uint32_t)w * 64 + 32 * jj + 8 * g, c[w]);
-          tc::tmem_ld_wait();
-          if (!live) continue;
-          const int c0 = NB * j + 8 * g;  // first matrix column of this group
-          df2 old[8];
-          if (a.b == 0) {
-            // first touch: the equilibrated precision matrix, S (G + tau Lambda) S
+      for (int g = 0; g < 4; ++g) {
+        uint32_t c[kDigits][8];
 #pragma unroll
-            for (int e2 = 0; e2 < 8; ++e2) {
-              const int col = c0 + e2;
-              df2 v{0.0f, 0.0f};
-              if (r < a.p && col < a.p) {
-                const df2 g2 = static_cast<const df2*>(a.G2)[(size_t)r * a.P + col];
-                v = df_mul(df_mul(g2, df2{(float)S[r], 0.0f}), df2{(float)S[col], 0.0f});
-                if (r == col) v = df_add(v, df_split(S[r] * S[r] * tau * lam_r));
-              } else if (r == col) {
-                v = df2{1.0f, 0.0f};
-              }
-              old[e2] = v;
-            }
-          } else {
-            const float4* src = reinterpret_cast<const float4*>(A + (size_t)r * a.P + c0);
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const float4 v = __ldcg(src + h);
-              old[2 * h] = df2{v.x, v.y};
-              old[2 * h + 1] = df2{v.z, v.w};
-            }
-          }
-          float4 outv[4];
-#pragma unroll
-          for (int e2 = 0; e2 < 8; ++e2) {
-            // sum_w C_w 2^{-8(w-2)} by Horner from the smallest class, in pairs; times 2^-16
-            float fh = __uint_as_float(c[kDigits - 1][e2]), fl = 0.0f;
-#pragma unroll
-            for (int w = kDigits - 2; w >= 0; --w) {
-              const float x = fh * 0x1p-8f, y = __uint_as_float(c[w][e2]);
-              const float sum = x + y, bb = sum - x;
-              const float er = (x - (sum - bb)) + (y - bb);
-              fh = sum;
-              fl = fmaf(fl, 0x1p-8f, er);
-            }
-            const df2 v = df_sub(old[e2], df2{fh * 0x1p-16f, fl * 0x1p-16f});
-            if (e2 & 1) {
-              outv[e2 >> 1].z = v.hi;
-              outv[e2 >> 1].w = v.lo;
-            } else {
-              outv[e2 >> 1].x = v.hi;
-              outv[e2 >> 1].y = v.lo;
-            }
-          }
-          float4* dst = reinterpret_cast<float4*>(A + (size_t)r * a.P + c0);
-#pragma unroll
-          for (int h = 0; h < 4; ++h) __stcg(dst + h, outv[h]);
+        for (int w = 0; w < kDigits; ++w) tc::tmem_ld8(tmem + lane_off + (uint32_t)w * 64 + 32 * jj + 8 * g, c[w]);
+        tc::tmem_ld_wait();
+        if (g == 3) {
+          tc::fence_before();
+          mbar_arrive(&sh.acc_empty);  // the MMA may overwrite the classes now
         }
-        // the tile has taken every update of this block column
+        if (!live) continue;
+        float4 outv[4];
+#pragma unroll
+        for (int e2 = 0; e2 < 8; ++e2) {
+          // sum_w C_w 2^{-8(w-2)} by Horner from the smallest class, in pairs; times 2^-16
+          float fh = __uint_as_float(c[kDigits - 1][e2]), fl = 0.0f;
+#pragma unroll
+          for (int w = kDigits - 2; w >= 0; --w) {
+            const float x = fh * 0x1p-8f, y = __uint_as_float(c[w][e2]);
+            const float sum = x + y, bb = sum - x;
+            const float er = (x - (sum - bb)) + (y - bb);
+            fh = sum;
+            fl = fmaf(fl, 0x1p-8f, er);
+          }
+          const df2 v = df_sub(old[8 * g + e2], df2{fh * 0x1p-16f, fl * 0x1p-16f});
+          if (e2 & 1) {
+            outv[e2 >> 1].z = v.hi;
+            outv[e2 >> 1].w = v.lo;
+          } else {
+            outv[e2 >> 1].x = v.hi;
+            outv[e2 >> 1].y = v.lo;
+          }
+        }
+        float4* dst = reinterpret_cast<float4*>(A + (size_t)r * a.P + NB * j + 8 * g);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) __stcg(dst + h, outv[h]);
+      }
+      // the tile has taken every update of this block column
+      if (live) {
+        __threadfence();
         __syncwarp();
-        if (live && lane == 0) {
-          __threadfence();
+        if (lane == 0) {
+          unsigned long long* const cntA = a.sync + (size_t)m * a.sync_words + kSyncHeader;
           asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(cntA + (size_t)i * T + j), "l"(done_count)
                        : "memory");
         }
       }
-      tc::fence_before();
-      mbar_arrive(&sh.acc_empty);
     }
   }
   tc::fence_before();
@@ -356,7 +363,7 @@ cudaError_t chol_trail_prepare() {
 }
 
 // Tensor maps of the digit planes (nchains x 6 planes of P x P BF16, row-major,
-// one after another): 64-column boxes of 128 rows (A) and 64 rows (B), 128-byte
+// one after another): 32-column boxes of 128 rows (A) and 64 rows (B), 64-byte
 // swizzle.  0 on success.
 int chol_trail_make_maps(const void* digits, int P, int nchains, void* mapA, void* mapB) {
   EncodeFn enc = encode_fn();
@@ -366,11 +373,11 @@ int chol_trail_make_maps(const void* digits, int P, int nchains, void* mapA, voi
   const cuuint32_t estr[2] = {1, 1};
   const cuuint32_t boxA[2] = {kKc, 128}, boxB[2] = {kKc, 64};
   CUresult r = enc(reinterpret_cast<CUtensorMap*>(mapA), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(digits),
-                   dims, strides, boxA, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   dims, strides, boxA, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return -1;
   r = enc(reinterpret_cast<CUtensorMap*>(mapB), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(digits), dims,
-          strides, boxB, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+          strides, boxB, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -1;
 }

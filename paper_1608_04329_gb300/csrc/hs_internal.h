@@ -158,6 +158,9 @@ struct CholArgs {
   int k0, k1;                   // 0, 0: the whole matrix in one launch
   int ntasks;                   // > 0: entries of order (block-column launches)
   void* digits;                 // or nullptr
+  // block-column launches: per-SM claim and role words (2 x kSmMarks, zeroed
+  // once) for placing the chains on SMs of their own; or nullptr
+  unsigned long long* sm_role;
 };
 // Enqueues the whole factorization; *launches receives the kernel count.
 cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches);
@@ -176,8 +179,9 @@ std::vector<int> chol_task_order(int T, int workers, bool inverse);
 std::vector<int> chol_task_codes(int T, int workers, bool inverse);
 
 // Task list of one block-column launch (tile columns [k0, k1) of T): C(i, k) and
-// the updates UA(i, j, k) with j < k1, as codes kind | k << 2 | i << 10 | j << 18.
-std::vector<int> chol_block_task_codes(int T, int k0, int k1);
+// the updates UA(i, j, k) with j < k1, as codes kind | k << 2 | i << 10 | j << 18,
+// in the start order of a list schedule for about `workers` concurrent task slots.
+std::vector<int> chol_block_task_codes(int T, int k0, int k1, int workers);
 
 // ---- trailing updates on the tensor cores (chol_trail.cu) -------------------
 struct TrailArgs {

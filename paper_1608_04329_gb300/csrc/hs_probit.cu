@@ -84,6 +84,7 @@ struct hs_probit {
   // HS_SCHED_TENSOR: block-column launches and tensor-core trailing updates
   bool tensor_sched = false;
   void* digits = nullptr;                   // K x 6 digit planes of P x P BF16
+  unsigned long long* sm_role = nullptr;    // per-SM claim and role words of the block-column launches
   void* G2 = nullptr;                       // P x P FP32 pairs of the Gram matrix
   int* blk_order = nullptr;                 // the block columns' task lists, one after another
   std::vector<int> blk_off, blk_len;
@@ -354,6 +355,7 @@ cudaError_t enqueue_sweep(hs_probit* h) {
         hs::CholArgs ca = chol_args(h, 0);
         ca.nchains = h->K;
         ca.digits = h->digits;
+        ca.sm_role = h->sm_role;
         hs::TrailArgs ta{};
         ta.p = h->p;
         ta.P = h->P;
@@ -753,10 +755,14 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   if (h->tensor_sched) {
     check(hs::chol_trail_prepare());
     check(h->alloc(&h->digits, K * 6 * P2 * sizeof(uint16_t)));
+    check(h->alloc(&h->sm_role, 2 * hs::kSmMarks * sizeof(unsigned long long)));
+    if (e == cudaSuccess) check(cudaMemset(h->sm_role, 0, 2 * hs::kSmMarks * sizeof(unsigned long long)));
     check(h->alloc(&h->G2, P2 * 2 * sizeof(float)));
     std::vector<int> all;
     for (int b = 0; 4 * b < h->T; ++b) {
-      const std::vector<int> c = hs::chol_block_task_codes(h->T, 4 * b, std::min(4 * b + 4, h->T));
+      // task slots per chain: two per worker block, shared by the chains
+      const int slots = std::max(1, 2 * (h->chol_grid - h->K) / h->K);
+      const std::vector<int> c = hs::chol_block_task_codes(h->T, 4 * b, std::min(4 * b + 4, h->T), slots);
       h->blk_off.push_back((int)all.size());
       h->blk_len.push_back((int)c.size());
       all.insert(all.end(), c.begin(), c.end());
@@ -1121,11 +1127,12 @@ int hs_probit_debug_error_word(const hs_probit* h, int* word) {
   return HS_OK;
 }
 
-int64_t hs_chol_block_task_list(int32_t T, int32_t k0, int32_t k1, int32_t* codes, int64_t max_codes) {
-  if (T < 1 || T > 256 || k0 < 0 || k1 <= k0 || k1 > T || max_codes < 0 || (max_codes > 0 && !codes))
+int64_t hs_chol_block_task_list(int32_t T, int32_t k0, int32_t k1, int32_t workers, int32_t* codes,
+                                int64_t max_codes) {
+  if (T < 1 || T > 256 || k0 < 0 || k1 <= k0 || k1 > T || workers < 1 || max_codes < 0 || (max_codes > 0 && !codes))
     return HS_EINVAL;
   try {
-    const std::vector<int> list = hs::chol_block_task_codes(T, k0, k1);
+    const std::vector<int> list = hs::chol_block_task_codes(T, k0, k1, workers);
     const int64_t n = (int64_t)list.size();
     for (int64_t t = 0; t < n && t < max_codes; ++t) codes[t] = list[(size_t)t];
     return n;

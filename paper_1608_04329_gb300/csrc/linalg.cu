@@ -731,7 +731,8 @@ __global__ void __launch_bounds__(256) step_df_kernel(CholArgs a, int k) {
 // Word layout of the scheduling buffer (u64, zeroed once when the handle is
 // made): header [0] epoch of the last finished launch, [1] exit ticket,
 // [2] abort, [3] chain claim (epoch), [4] start ticket, [5] chain SM
-// (epoch << 16 | SM id), [6] next worker task; then cntA and cntB (T*T
+// (epoch << 16 | SM id), [6] next worker task, [7] chain ticket of the
+// block-column launches; then cntA and cntB (T*T
 // each: updates applied to tile (i, j) of A or B, at i*T + j), flagL and
 // flagX (T*T: L_ik, X_kj published), flagLi (T: L_kk^{-1} published).
 // Flags hold the epoch of the launch that published them; counters hold
@@ -752,7 +753,7 @@ __host__ __device__ __forceinline__ int nTasks(int T, int k, bool inv) {
   return nC(T, k) + nUA(T, k) + (inv ? k + nUB(T, k) : 0);
 }
 struct PSync {
-  unsigned long long *epoch, *ticket, *abort, *claim, *start, *chain_sm, *next;
+  unsigned long long *epoch, *ticket, *abort, *claim, *start, *chain_sm, *next, *chain_ticket;
   unsigned long long *cntA, *cntB, *flagL, *flagX, *flagLi;
   __device__ PSync(unsigned long long* w, int T) {
     epoch = w;
@@ -762,6 +763,7 @@ struct PSync {
     start = w + 4;
     chain_sm = w + 5;
     next = w + 6;
+    chain_ticket = w + 7;
     cntA = w + kSyncHeader;
     cntB = cntA + T * T;
     flagL = cntB + T * T;
@@ -1166,9 +1168,37 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         if (role == 0 && atomicCAS(ps0.claim, e0 - 1, e0) == e0 - 1) role = 1;
       }
       if (role == 1) st_release_u64(ps0.chain_sm, (e0 << 16) | smid);
+    } else if (a.k1 > 0 && a.sm_role && smid < (unsigned)kSmMarks) {
+      // Block-column launches: the first block to start on each SM may walk a
+      // chain (the first nch of them do), and the other blocks on a chain's SM
+      // stay idle, leaving the latency-bound chain the whole SM.  The tag is
+      // unique and increasing per launch, so the per-SM words need no reset.
+      const unsigned long long tag = (e0 << 8) | (unsigned long long)(kb / 4 + 1);
+      unsigned long long* const claim = a.sm_role + smid;
+      unsigned long long* const rword = a.sm_role + kSmMarks + smid;
+      if (atomicMax(claim, tag) < tag) {
+        const unsigned long long t = atomicAdd(ps0.chain_ticket, 1ull);
+        if (t < (unsigned long long)nch) {
+          role = 1;
+          chain = (int)t;
+        }
+        st_release_u64(rword, 2 * tag + (role == 1 ? 1ull : 0ull));
+      } else {
+        unsigned long long v = ld_acquire_u64(rword);
+        const uint64_t t0 = global_ns();
+        while (v < 2 * tag) {
+          if (global_ns() - t0 > 2000000000ull) {
+            set_timeout(a.err, kSiteStartRole);
+            st_release_u64(ps0.abort, e0);
+            break;
+          }
+          __nanosleep(32);
+          v = ld_acquire_u64(rword);
+        }
+        role = (v < 2 * tag || (v & 1ull)) ? 2 : 0;
+      }
     } else {
-      // several chains, or block-column launches: the first nch blocks to
-      // start walk the diagonal chains
+      // several chains: the first nch blocks to start walk the diagonal chains
       const unsigned long long st = atomicAdd(ps0.start, 1ull);
       if (st == gridDim.x - 1) *ps0.start = 0;
       if (st < (unsigned long long)nch) {
@@ -1414,6 +1444,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
     if (atomicAdd(ps0.ticket, 1ull) == (unsigned long long)(gridDim.x - 1)) {
       *ps0.ticket = 0;
       *ps0.next = 0;
+      *ps0.chain_ticket = 0;
       *ps0.epoch = e;
     }
   }
@@ -1994,20 +2025,149 @@ std::vector<int> chol_task_codes(int T, int workers, bool inverse) {
   return order;
 }
 
-std::vector<int> chol_block_task_codes(int T, int k0, int k1) {
-  std::vector<int> out;
+// The task list of one block-column launch: the panel tiles C(i, k) below the
+// chain's own L_{k+1,k} and the updates UA(i, j, k) of the block column's
+// later tile columns (the chain applies the last update of the next diagonal
+// tile itself), for k in [k0, k1).  As for the single launch, the list is the
+// start order of a simulated list schedule (ready task with the longest
+// remaining path first, beside the diagonal chain), so the few tasks the chain
+// waits on next are taken before the bulk; the order is checked to be
+// topological (every task after the tasks of this launch it reads) and the
+// canonical order (step by step) is used if the check fails.
+std::vector<int> chol_block_task_codes(int T, int k0, int k1, int workers) {
   auto code = [](int kind, int i, int j, int k) { return kind | (k << 2) | (i << 10) | (j << 18); };
-  // step by step: the panel tiles C(i, k) below the chain's own L_{k+1,k}, then
-  // the updates of the block column's later tile columns (the chain applies the
-  // last update of the next diagonal tile itself).  Every task waits only on
-  // tasks before it in the list or on the diagonal chain.
+  struct Task {
+    int kind, i, j, k;
+  };
+  std::vector<Task> tasks;
   for (int k = k0; k < k1; ++k) {
-    for (int i = k + 2; i < T; ++i) out.push_back(code(0, i, k, k));
+    for (int i = k + 2; i < T; ++i) tasks.push_back({0, i, k, k});
     for (int j = k + 1; j < k1; ++j)
       for (int i = j; i < T; ++i)
-        if (!(i == k + 1 && j == k + 1)) out.push_back(code(2, i, j, k));
+        if (!(i == k + 1 && j == k + 1)) tasks.push_back({2, i, j, k});
   }
-  return out;
+  const int n = (int)tasks.size();
+  std::vector<int> canonical(n);
+  for (int t = 0; t < n; ++t) canonical[t] = code(tasks[t].kind, tasks[t].i, tasks[t].j, tasks[t].k);
+  if (n == 0 || workers < 1) return canonical;
+  // ids: tasks 0..n-1; chain nodes n + 2 (k - k0) (L_kk^{-1}), + 1 (L_{k+1,k} and the next diagonal)
+  const int nk = k1 - k0, N = n + 2 * nk;
+  auto Li = [&](int k) { return n + 2 * (k - k0); };
+  auto Ln = [&](int k) { return n + 2 * (k - k0) + 1; };
+  std::vector<int> idC((size_t)T * T, -1), idUA((size_t)T * T * (nk > 0 ? nk : 1), -1);
+  auto ua_at = [&](int i, int j, int k) -> int& { return idUA[((size_t)(k - k0) * T + i) * T + j]; };
+  for (int t = 0; t < n; ++t) {
+    const Task& x = tasks[t];
+    if (x.kind == 0) idC[(size_t)x.i * T + x.k] = t; else ua_at(x.i, x.j, x.k) = t;
+  }
+  auto UA = [&](int i, int j, int k) { return (k >= k0 && k < k1) ? ua_at(i, j, k) : -1; };
+  std::vector<std::vector<int>> deps(N);
+  auto add = [&](int v, int d) {
+    if (d >= 0) deps[v].push_back(d);
+  };
+  for (int t = 0; t < n; ++t) {
+    const Task& x = tasks[t];
+    if (x.kind == 0) {
+      add(t, Li(x.k));
+      add(t, UA(x.i, x.k, x.k - 1));
+    } else {
+      add(t, x.i == x.k + 1 ? Ln(x.k) : idC[(size_t)x.i * T + x.k]);
+      if (x.j != x.i) add(t, x.j == x.k + 1 ? Ln(x.k) : idC[(size_t)x.j * T + x.k]);
+      add(t, UA(x.i, x.j, x.k - 1));
+    }
+  }
+  for (int k = k0; k < k1; ++k) {
+    if (k > k0) add(Li(k), Ln(k - 1));
+    add(Li(k), UA(k, k, k - 2));
+    if (k + 1 < T) {
+      add(Ln(k), Li(k));
+      add(Ln(k), UA(k + 1, k, k - 1));
+      if (k + 1 < k1) add(Ln(k), UA(k + 1, k + 1, k - 1));
+    }
+  }
+  // durations (us, as the single launch): diagonal tile 10, panel tile and next diagonal 6, tile task 6
+  std::vector<double> dur(N, 6.0);
+  for (int k = k0; k < k1; ++k) dur[Li(k)] = 10.0;
+  std::vector<std::vector<int>> succ(N);
+  for (int v = 0; v < N; ++v)
+    for (int d : deps[v]) succ[d].push_back(v);
+  std::vector<int> cnt(N), topo, stack;
+  topo.reserve(N);
+  for (int v = 0; v < N; ++v)
+    if ((cnt[v] = (int)deps[v].size()) == 0) stack.push_back(v);
+  while (!stack.empty()) {
+    const int v = stack.back();
+    stack.pop_back();
+    topo.push_back(v);
+    for (int w : succ[v])
+      if (--cnt[w] == 0) stack.push_back(w);
+  }
+  if ((int)topo.size() != N) return canonical;
+  std::vector<double> bl(N, 0.0);
+  for (int x = N - 1; x >= 0; --x) {
+    const int v = topo[x];
+    double m = 0.0;
+    for (int w : succ[v]) m = std::max(m, bl[w]);
+    bl[v] = dur[v] + m;
+  }
+  std::vector<int> rem(N);
+  for (int v = 0; v < N; ++v) rem[v] = (int)deps[v].size();
+  using RQ = std::pair<double, int>;
+  std::priority_queue<RQ, std::vector<RQ>, std::greater<RQ>> ready;
+  std::priority_queue<int, std::vector<int>, std::greater<int>> chain_ready;
+  using EV = std::pair<double, int>;
+  std::priority_queue<EV, std::vector<EV>, std::greater<EV>> ev;
+  for (int v = 0; v < N; ++v)
+    if (rem[v] == 0) {
+      if (v >= n) chain_ready.push(v); else ready.push({-bl[v], v});
+    }
+  std::vector<int> out;
+  out.reserve(n);
+  std::vector<double> start(N, -1.0);
+  double now = 0.0;
+  int free_w = workers;
+  bool chain_busy = false;
+  for (;;) {
+    while (free_w > 0 && !ready.empty()) {
+      const int v = ready.top().second;
+      ready.pop();
+      start[v] = now;
+      out.push_back(v);
+      --free_w;
+      ev.push({now + dur[v], v});
+    }
+    if (!chain_busy && !chain_ready.empty()) {
+      const int v = chain_ready.top();
+      chain_ready.pop();
+      start[v] = now;
+      chain_busy = true;
+      ev.push({now + dur[v], v});
+    }
+    if (ev.empty()) break;
+    now = ev.top().first;
+    const int v = ev.top().second;
+    ev.pop();
+    if (v >= n) chain_busy = false; else ++free_w;
+    for (int w : succ[v])
+      if (--rem[w] == 0) {
+        if (w >= n) chain_ready.push(w); else ready.push({-bl[w], w});
+      }
+  }
+  if ((int)out.size() != n) return canonical;
+  std::vector<char> seen(n, 0);
+  for (int v : out) {
+    if (v < 0 || v >= n || seen[v]) return canonical;
+    seen[v] = 1;
+  }
+  for (int v = 0; v < N; ++v)
+    for (int d : deps[v])
+      if (!(start[d] >= 0.0 && start[v] >= start[d] + dur[d] - 1e-9)) return canonical;
+  std::vector<int> codes(n);
+  for (int q = 0; q < n; ++q) {
+    const Task& x = tasks[out[q]];
+    codes[q] = code(x.kind, x.i, x.j, x.k);
+  }
+  return codes;
 }
 
 int chol_launch_count(int P, int arith, int persistent_grid) {

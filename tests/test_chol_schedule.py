@@ -99,20 +99,22 @@ def _block_tasks(T, k0, k1):
     return out
 
 
+@pytest.mark.parametrize("workers", [1, 17, 500])
 @pytest.mark.parametrize("T", [1, 2, 3, 5, 7, 8, 17, 32, 125])
-def test_block_column_task_lists(lib, T):
+def test_block_column_task_lists(lib, T, workers):
     """The tensor-core schedule's block-column launches (tile columns
-    [4b, 4b + 4)): each list holds the panel tiles C(i, k) and the updates
+    [4b, 4b + 4), list-scheduled for a number of task slots): each list holds
+    the panel tiles C(i, k) and the updates
     UA(i, j, k) of the block column's later tile columns exactly once, every
     task after the tasks of the same launch it reads (the updates of earlier
     block columns come from the tensor-core launches between them)."""
     for k0 in range(0, T, 4):
         k1 = min(k0 + 4, T)
-        n = lib.hs_chol_block_task_list(T, k0, k1, None, 0)
+        n = lib.hs_chol_block_task_list(T, k0, k1, workers, None, 0)
         want = _block_tasks(T, k0, k1)
         assert n == len(want)
         codes = np.zeros(max(n, 1), dtype=np.int32)
-        assert lib.hs_chol_block_task_list(T, k0, k1, codes.ctypes.data, n) == n
+        assert lib.hs_chol_block_task_list(T, k0, k1, workers, codes.ctypes.data, n) == n
         got = []
         for c in codes[:n].tolist():
             kind, k, i, j = c & 3, (c >> 2) & 0xFF, (c >> 10) & 0xFF, (c >> 18) & 0xFF
@@ -124,5 +126,6 @@ def test_block_column_task_lists(lib, T):
                 if d[3] >= k0:  # tasks of this launch
                     assert d in pos, (t, d)
                     assert pos[d] < pos[t], (t, d)
-    assert lib.hs_chol_block_task_list(8, 4, 4, None, 0) == -1
-    assert lib.hs_chol_block_task_list(8, 0, 9, None, 0) == -1
+    assert lib.hs_chol_block_task_list(8, 4, 4, 4, None, 0) == -1
+    assert lib.hs_chol_block_task_list(8, 0, 9, 4, None, 0) == -1
+    assert lib.hs_chol_block_task_list(8, 0, 4, 0, None, 0) == -1
