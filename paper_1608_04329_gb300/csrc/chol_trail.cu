@@ -2,8 +2,8 @@
 // (Sect. 5, beta update, step iii: the factor of X^T X + tau^{-2} Lambda^{-2},
 // equilibrated to unit diagonal).
 //
-// The factorization runs over block columns of four 32-wide tiles (128
-// columns).  Inside a block column the FP32-pair tile tasks of
+// The factorization runs over block columns of kTrailBlockTiles 32-wide tiles
+// (four: 128 columns).  Inside a block column the FP32-pair tile tasks of
 // chol_persistent_kernel factor the diagonal block and form the panel L_ib;
 // everything to the right of the block column then takes the rank-128 update
 //     A_ij -= sum_{k in block b} L_ik L_jk^T
@@ -16,8 +16,8 @@
 // when they store L.  With classes C_w = sum_{t+u=w} sum_k d_t(i,k) d_u(j,k),
 // w = 2..7 (pairs with t + u > 7 weigh below 2^{-56}),
 //     sum_k L_ik L_jk = sum_w 2^{-8w} C_w.
-// Each C_w over the 128 columns of a block is an integer below 2^24: the pairs
-// with a first digit are bounded through the unit row norm
+// Each C_w over the (at most 128) columns of a block is an integer below 2^24:
+// the pairs with a first digit are bounded through the unit row norm
 // (sum_k |d_1(i,k)| <= sqrt(128) 262), the others by 128^3 each, so the FP32
 // accumulators of the tensor cores hold the classes exactly.  The epilogue
 // combines them into an FP32 pair (about 48 bits, absolute error near 2^{-48}
@@ -47,7 +47,7 @@ namespace hs {
 namespace {
 
 constexpr int NB = 32;                  // tile
-constexpr int kBlockTiles = 4;          // tiles per block column
+constexpr int kBlockTiles = kTrailBlockTiles;  // tiles per block column
 constexpr int kDigits = 6;
 constexpr int kStages = 3;
 constexpr int kKc = 32;                 // columns of the block per stage (one tile; 64-byte rows)
@@ -56,6 +56,7 @@ constexpr uint32_t kBDigitBytes = 64 * kKc * 2;   // 64 rows: 4 KB
 constexpr uint32_t kStageBytes = kDigits * (kADigitBytes + kBDigitBytes);  // 72 KB
 constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes;
 static_assert(kSmem <= 227 * 1024, "stages fit in shared memory");
+static_assert(kBlockTiles * 32 <= 128, "class sums stay exact over a block column of at most 128 columns");
 constexpr int kEpiWarps = 8;            // warps 4..11: one 32 x 32 output tile each
 constexpr int kThreads = 128 + 32 * kEpiWarps;
 constexpr unsigned long long kEpochStride = 1024;  // as the readiness words of chol_persistent_kernel
@@ -98,15 +99,17 @@ __device__ __forceinline__ uint64_t kmaj_desc(uint32_t saddr) {
          (4ull << 61);
 }
 
-// Work items of block column b: chain m, strip s >= b + 1 (tiles 4s..4s+3),
-// column pair jp (tiles 2jp, 2jp+1) with 2jp >= max(col_lo, 4(b + 1)),
-// 2jp < col_hi and 2jp <= 4s + 3.
+// Work items of block column b (tiles from c1 = kBlockTiles (b + 1) on are
+// updated): chain m, strip s of 128 rows (tiles 4s..4s+3) reaching row tile c1,
+// column pair jp (tiles 2jp, 2jp+1) with 2jp >= max(col_lo, c1), 2jp < col_hi
+// and 2jp <= 4s + 3; tiles above the diagonal are not stored.
 struct ItemSpace {
   int T, nstrip, s0, jp0, jp1;  // strips s0..nstrip-1, column pairs jp0..jp1-1
   __host__ __device__ ItemSpace(int T_, int b, int col_lo, int col_hi) : T(T_) {
-    nstrip = (T + kBlockTiles - 1) / kBlockTiles;
-    s0 = b + 1;
-    jp0 = max(col_lo, kBlockTiles * (b + 1)) / 2;  // only columns right of the block column
+    const int c1 = kBlockTiles * (b + 1);
+    nstrip = (T + 3) / 4;
+    s0 = c1 / 4;
+    jp0 = max(col_lo, c1) / 2;  // only columns right of the block column
     jp1 = (min(col_hi, T) + 1) / 2;
   }
   __host__ __device__ int pairs_in_strip(int s) const {
@@ -235,39 +238,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int m = it / per_chain;
       int s, jp;
       is.decode(it % per_chain, s, jp);
-      const int i = kBlockTiles * s + quad;  // tile row of this warp
+      const int i = 4 * s + quad;            // tile row of this warp
       const int j = 2 * jp + jj;             // tile column
       const int r = NB * i + lane;           // matrix row of this thread
       const bool live = i < T && j < T && j <= i;  // warp-uniform
       df2* const A = static_cast<df2*>(a.A) + (size_t)m * a.P * a.P;
-      // the tile's current values (independent of the products: read before they finish)
+      // the tile's current values (independent of the products: read before they
+      // finish); before the first block column they are the equilibrated
+      // precision matrix that precision_pairs_kernel wrote
       df2 old[NB];
       if (live) {
-        if (a.b == 0) {
-          // first touch: the equilibrated precision matrix, S (G + tau Lambda) S
-          const double* const S = a.S + (size_t)m * a.P;
-          const float sr = (float)S[r];
+        const float4* src = reinterpret_cast<const float4*>(A + (size_t)r * a.P + NB * j);
 #pragma unroll
-          for (int c = 0; c < NB; ++c) {
-            const int col = NB * j + c;
-            df2 v{0.0f, 0.0f};
-            if (r < a.p && col < a.p) {
-              const df2 g2 = static_cast<const df2*>(a.G2)[(size_t)r * a.P + col];
-              v = df_mul(df_mul(g2, df2{sr, 0.0f}), df2{(float)S[col], 0.0f});
-              if (r == col) v = df_add(v, df_split(S[r] * S[r] * a.tau_new[m] * a.lam_new[(size_t)m * a.p + r]));
-            } else if (r == col) {
-              v = df2{1.0f, 0.0f};
-            }
-            old[c] = v;
-          }
-        } else {
-          const float4* src = reinterpret_cast<const float4*>(A + (size_t)r * a.P + NB * j);
-#pragma unroll
-          for (int h = 0; h < NB / 2; ++h) {
-            const float4 v = __ldcg(src + h);
-            old[2 * h] = df2{v.x, v.y};
-            old[2 * h + 1] = df2{v.z, v.w};
-          }
+        for (int h = 0; h < NB / 2; ++h) {
+          const float4 v = __ldcg(src + h);
+          old[2 * h] = df2{v.x, v.y};
+          old[2 * h + 1] = df2{v.z, v.w};
         }
       }
       if (!twait(&sh.acc_full, n_item & 1, &sh, a.err, kSiteTrailEpi)) break;
@@ -326,6 +312,31 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 2) {
     tc::fence_after();
     tc::tmem_free(tmem, 512);
+  }
+}
+
+// The lower tiles of the equilibrated precision matrix of every chain,
+// A~ = S (G + tau^{-2} Lambda^{-2}) S as FP32 pairs (identity past p), from the
+// Gram matrix in pairs: the work matrix the block-column factorization starts
+// from.  blockIdx.y is the chain.
+__global__ void precision_pairs_kernel(TrailArgs a) {
+  const int m = blockIdx.y;
+  const int64_t n = (int64_t)a.P * a.P;
+  df2* const A = static_cast<df2*>(a.A) + (size_t)m * n;
+  const df2* const G2 = static_cast<const df2*>(a.G2);
+  const double* const S = a.S + (size_t)m * a.P;
+  const double tau = a.tau_new[m];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / a.P), c = (int)(e % a.P);
+    if ((c >> 5) > (r >> 5)) continue;  // tiles right of the diagonal tile are never read
+    df2 v{0.0f, 0.0f};
+    if (r < a.p && c < a.p) {
+      v = df_mul(df_mul(G2[e], df2{(float)S[r], 0.0f}), df2{(float)S[c], 0.0f});
+      if (r == c) v = df_add(v, df_split(S[r] * S[r] * tau * a.lam_new[(size_t)m * a.p + r]));
+    } else if (r == c) {
+      v = df2{1.0f, 0.0f};
+    }
+    A[e] = v;
   }
 }
 
@@ -393,6 +404,11 @@ cudaError_t chol_trail_launch(const void* mapA, const void* mapB, const TrailArg
   memcpy(&ma, mapA, sizeof(ma));
   memcpy(&mb, mapB, sizeof(mb));
   chol_trail_kernel<<<grid, kThreads, kSmem, s>>>(ma, mb, a);
+  return cudaGetLastError();
+}
+
+cudaError_t precision_pairs_launch(const TrailArgs& a, cudaStream_t s) {
+  precision_pairs_kernel<<<dim3(256, a.nchains), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -161,6 +161,8 @@ struct CholArgs {
   // block-column launches: per-SM claim and role words (2 x kSmMarks, zeroed
   // once) for placing the chains on SMs of their own; or nullptr
   unsigned long long* sm_role;
+  int prebuilt;                 // 1: A already holds the equilibrated precision matrix
+                                // (lower tiles), so no tile is formed from the Gram matrix
 };
 // Enqueues the whole factorization; *launches receives the kernel count.
 cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches);
@@ -184,9 +186,11 @@ std::vector<int> chol_task_codes(int T, int workers, bool inverse);
 std::vector<int> chol_block_task_codes(int T, int k0, int k1, int workers);
 
 // ---- trailing updates on the tensor cores (chol_trail.cu) -------------------
+// Tile columns per block column of the HS_SCHED_TENSOR factorization.
+constexpr int kTrailBlockTiles = 4;
 struct TrailArgs {
   int p, P, nchains;
-  int b;                        // block column (tiles 4b .. 4b+3)
+  int b;                        // block column (tiles kTrailBlockTiles b ..)
   int col_lo, col_hi;           // output tile columns [col_lo, col_hi) of this launch
   void* A;                      // nchains x P x P FP32 pairs (tiles of A~ and of L~)
   const void* G2;               // P x P FP32 pairs of the Gram matrix (first block column only)
@@ -203,6 +207,8 @@ int chol_trail_make_maps(const void* digits, int P, int nchains, void* mapA, voi
 int chol_trail_items(int P, int b, int col_lo, int col_hi, int nchains);
 cudaError_t chol_trail_launch(const void* mapA, const void* mapB, const TrailArgs& a, int grid, cudaStream_t s);
 cudaError_t gram_pairs_launch(const double* G, int p, int P, void* G2, cudaStream_t s);
+// A~ = S (G + tau Lambda) S into the work matrix of every chain (lower tiles, FP32 pairs)
+cudaError_t precision_pairs_launch(const TrailArgs& a, cudaStream_t s);
 
 // ---- beta tail, nu/xi, commit ----------------------------------------------
 struct TailArgs {

@@ -302,6 +302,24 @@ hs::TailArgs tail_args(hs_probit* h, int m) {
   return a;
 }
 
+hs::TrailArgs trail_args(hs_probit* h) {
+  hs::TrailArgs ta{};
+  ta.p = h->p;
+  ta.P = h->P;
+  ta.nchains = h->K;
+  ta.col_lo = 0;
+  ta.col_hi = h->T;
+  ta.A = h->A;
+  ta.G2 = h->G2;
+  ta.S = h->S;
+  ta.lam_new = h->lam_new;
+  ta.tau_new = h->tau_new;
+  ta.sync = h->chol_sync;
+  ta.sync_words = h->chol_words;
+  ta.err = h->err;
+  return ta;
+}
+
 // Record a profiling event pair around a group on a stream.  While a graph is
 // being captured the group's placeholder events are recorded instead, which
 // become event-record nodes of the graph.
@@ -340,6 +358,9 @@ cudaError_t enqueue_sweep(hs_probit* h) {
     if ((e = hs::shrink_launch(shrink_args(h, 0), h->s1, h->K)) != cudaSuccess) return e;
   }
   if (!h->chol_inverse && (e = cudaEventRecord(h->ev_shrink, h->s1)) != cudaSuccess) return e;
+  // the work matrix of the factorization, beside the X-stream (outside the
+  // timed spans: one span per kernel group and sweep)
+  if (h->tensor_sched && (e = hs::precision_pairs_launch(trail_args(h), h->s1)) != cudaSuccess) return e;
   // One chain: the factorization runs beside the X-stream (its blocks are
   // small enough to share the SMs).  Several chains on the single-launch
   // schedule: both fill the GPU, so the factorization follows the X-stream
@@ -355,29 +376,22 @@ cudaError_t enqueue_sweep(hs_probit* h) {
         hs::CholArgs ca = chol_args(h, 0);
         ca.nchains = h->K;
         ca.digits = h->digits;
-        ca.sm_role = h->sm_role;
-        hs::TrailArgs ta{};
-        ta.p = h->p;
-        ta.P = h->P;
-        ta.nchains = h->K;
-        ta.col_lo = 0;
-        ta.col_hi = h->T;
-        ta.A = h->A;
-        ta.G2 = h->G2;
-        ta.S = h->S;
-        ta.lam_new = h->lam_new;
-        ta.tau_new = h->tau_new;
-        ta.sync = h->chol_sync;
-        ta.sync_words = h->chol_words;
-        ta.err = h->err;
+        ca.prebuilt = 1;  // precision_pairs_kernel wrote A~ beside the X-stream
+        const hs::TrailArgs ta = trail_args(h);
+        const int slots = 2 * (h->chol_grid - h->K);
         for (int b = 0; b < (int)h->blk_off.size(); ++b) {
-          ca.k0 = 4 * b;
-          ca.k1 = std::min(4 * b + 4, h->T);
+          ca.k0 = hs::kTrailBlockTiles * b;
+          ca.k1 = std::min(hs::kTrailBlockTiles * (b + 1), h->T);
           ca.order = h->blk_order + h->blk_off[b];
           ca.ntasks = h->blk_len[b];
+          // chains on SMs of their own where the block column's chain, not its
+          // task list, bounds the launch (measured: fewer than about five tasks
+          // per worker slot)
+          ca.sm_role = (h->K == 1 || (double)h->blk_len[b] * h->K < 5.0 * slots) ? h->sm_role : nullptr;
           if ((ee = hs::chol_enqueue(ca, h->s1, nullptr)) != cudaSuccess) return ee;
-          ta.b = b;
-          if ((ee = hs::chol_trail_launch(h->tmapA, h->tmapB, ta, h->trail_grid, h->s1)) != cudaSuccess) return ee;
+          hs::TrailArgs tb = ta;
+          tb.b = b;
+          if ((ee = hs::chol_trail_launch(h->tmapA, h->tmapB, tb, h->trail_grid, h->s1)) != cudaSuccess) return ee;
         }
       } else if (after_xstream) {
         // every chain's factorization in one launch
@@ -759,10 +773,11 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
     if (e == cudaSuccess) check(cudaMemset(h->sm_role, 0, 2 * hs::kSmMarks * sizeof(unsigned long long)));
     check(h->alloc(&h->G2, P2 * 2 * sizeof(float)));
     std::vector<int> all;
-    for (int b = 0; 4 * b < h->T; ++b) {
+    for (int b = 0; hs::kTrailBlockTiles * b < h->T; ++b) {
       // task slots per chain: two per worker block, shared by the chains
       const int slots = std::max(1, 2 * (h->chol_grid - h->K) / h->K);
-      const std::vector<int> c = hs::chol_block_task_codes(h->T, 4 * b, std::min(4 * b + 4, h->T), slots);
+      const std::vector<int> c = hs::chol_block_task_codes(
+          h->T, hs::kTrailBlockTiles * b, std::min(hs::kTrailBlockTiles * (b + 1), h->T), slots);
       h->blk_off.push_back((int)all.size());
       h->blk_len.push_back((int)c.size());
       all.insert(all.end(), c.begin(), c.end());
@@ -857,7 +872,8 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   // per chain: shrink, the factorization, two draws, commit; then the X-stream and its reduce
   int64_t chol_l = hs::chol_launch_count(h->P, h->cfg.chol_arith, h->chol_grid);
   if (h->tensor_sched) {
-    chol_l = 0;
+    chol_l = 1;  // the precision matrix in pairs
+
     for (int b = 0; b < (int)h->blk_off.size(); ++b)
       chol_l += 1 + (hs::chol_trail_items(h->P, b, 0, h->T, h->K) > 0 ? 1 : 0);
   }

@@ -1173,7 +1173,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
       // chain (the first nch of them do), and the other blocks on a chain's SM
       // stay idle, leaving the latency-bound chain the whole SM.  The tag is
       // unique and increasing per launch, so the per-SM words need no reset.
-      const unsigned long long tag = (e0 << 8) | (unsigned long long)(kb / 4 + 1);
+      const unsigned long long tag = (e0 << 8) | (unsigned long long)(kb + 1);  // kb < 256
       unsigned long long* const claim = a.sm_role + smid;
       unsigned long long* const rword = a.sm_role + kSmMarks + smid;
       if (atomicMax(claim, tag) < tag) {
@@ -1233,8 +1233,11 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
     const PSync& ps = cv.ps;
     // Entering step k, sD holds D_k = A_kk after all k updates.
     bool go = true;
-    if (kb == 0) {
+    if (kb == 0 && !a.prebuilt) {
       tile_load_gram(sD, cx, 0, 0);
+    } else if (kb == 0) {
+      const TileRef t[1] = {{A, 0, 0, false, sD}};
+      tiles_load_cg<1>(t, P);
     } else {
       // the first diagonal tile of a later block column, after the tensor-core updates
       go = block_wait(&ps.cntA[kb * T + kb], base + (unsigned long long)kb, ps0, e, a.err, kSiteChainStart);
@@ -1265,9 +1268,15 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
           const TileRef t[2] = {{A, k + 1, k, false, sW}, {A, k + 1, k + 1, false, sD}};
           tiles_load_cg<2>(t, P);
         }
-      } else {
+      } else if (!a.prebuilt) {
         tile_load_gram(sW, cx, 1, 0);
         if (!last) tile_load_gram(sD, cx, 1, 1);
+      } else if (last) {
+        const TileRef t[1] = {{A, 1, 0, false, sW}};
+        tiles_load_cg<1>(t, P);
+      } else {
+        const TileRef t[2] = {{A, 1, 0, false, sW}, {A, 1, 1, false, sD}};
+        tiles_load_cg<2>(t, P);
       }
       __syncthreads();
       tile_mma<false>(sLi, sW, sX1);  // L_{k+1,k} = A_{k+1,k} L_kk^{-T}
@@ -1368,7 +1377,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         const unsigned long long* const wp2[2] = {&ps.flagLi[k], &ps.cntA[i * T + k]};
         const unsigned long long wt2[2] = {e, k >= 1 ? done_k : 0ull};
         if (!gwait<2>(g, wp2, wt2, ps0, e, a.err)) break;
-        if (k == 0) {
+        if (k == 0 && !a.prebuilt) {
           gload_gram(g, gW, cx, i, 0);
           const TileRef t1[1] = {{LinvT, k, k, false, gX1}};
           gload_cg<1>(g, t1, P);
@@ -1403,7 +1412,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         const unsigned long long* const wp3[3] = {&ps.flagL[i * T + k], &ps.flagL[j * T + k], &ps.cntA[i * T + j]};
         const unsigned long long wt3[3] = {e, e, k >= 1 ? done_k : 0ull};
         if (!gwait<3>(g, wp3, wt3, ps0, e, a.err)) break;
-        if (k == 0) {
+        if (k == 0 && !a.prebuilt) {
           gload_gram(g, gW, cx, i, j);
           const TileRef t2[2] = {{A, i, k, false, gX1}, {A, j, k, false, gX2}};
           gload_cg<2>(g, t2, P);
