@@ -47,6 +47,9 @@ WORKLOADS = {
                name="horseshoe-probit sweep, N=4e6, p=4000, X rows N(0, Toeplitz 0.5^|i-j|) fp8 e4m3 with column "
                     "scales (16 GB), 20 nonzeros U[0.5,2], 1 chain"),
 }
+UNEVEN = dict(n=64, N=(10_000, 200_000), p=(50, 2000), K=4, dt="bf16", nz_frac=0.01,
+              name="uneven multi-problem batch: 64 probit problems, N log-uniform [1e4, 2e5], p log-uniform "
+                   "[50, 2000], X iid N(0,1) bf16, 1% nonzeros U[1,3], 4 chains each, one graph launch per sweep")
 XSTREAM_SOURCES = ["paper_1608_04329_gb300/csrc/xstream.cu", "paper_1608_04329_gb300/csrc/hs_common.cuh"]
 XSTREAM_K_SOURCES = ["paper_1608_04329_gb300/csrc/xstream_k.cu", "paper_1608_04329_gb300/csrc/hs_common.cuh"]
 
@@ -372,6 +375,98 @@ def run_k_chains(args, wk, pkg, torch, dist, ws, rank, local, chol, one_chain_va
             "workload": wk["name"]}
 
 
+def run_uneven_batch(args, pkg, torch, dist, ws, rank, local, chol):
+    """Many problems of uneven N and p, K chains each, swept by one graph per
+    sweep after the batch tuner has picked the launch shapes."""
+    import hs_synth
+    u = UNEVEN
+    peak, peak_kind = _peaks()
+    t_gen = time.perf_counter()
+    sizes = hs_synth.uneven_sizes(u["n"], u["N"], u["p"], seed=0)
+    ds = [hs_synth.make_problem(N, p, max(1, round(u["nz_frac"] * p)), u["dt"], seed=1000 + m)
+          for m, (N, p) in enumerate(sizes)]
+    t_gen = time.perf_counter() - t_gen
+    x_bytes = sum(d["X"].nbytes for d in ds)
+    y_bytes = sum(d["y"].nbytes for d in ds)
+    root = torch.cuda.Stream(device=local)
+    t0 = time.perf_counter()
+    b = pkg.HSProbitBatch([(d["X"], d["y"]) for d in ds], seed=0, num_chains=u["K"], chol_arith=chol,
+                          problem=u["n"] * rank, device=local, stream=root.cuda_stream,
+                          ring_size=max(args.c3_steps + 8, 16))
+    t_init = time.perf_counter() - t0
+    b.sweep(3)  # warm-up
+    t0 = time.perf_counter()
+    best = b.tune(3)
+    t_tune = time.perf_counter() - t0
+    trials = b.tune_trials()
+    shapes = [b.problem(m).launch_shape() for m in range(len(ds))]
+    b.sweep(3)  # warm-up of the tuned graph
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        clk.mark(True)
+        e0.record(root)
+        b.sweep(args.c3_steps)
+        e1.record(root)
+        torch.cuda.synchronize()
+        clk.mark(False)
+    barrier(dist)
+    ms = max_over_ranks(dist, e0.elapsed_time(e1))
+    ms_sweep = ms / args.c3_steps
+    # e2e through the public API: per step one batch sweep and every chain's newest draw read back
+    for m in range(len(ds)):
+        for c in range(u["K"]):
+            b.problem(m).draws(chain=c)  # read what the timed sweeps left, before the clock starts
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.c3_steps // 5)):
+        b.sweep(1)
+        for m in range(len(ds)):
+            for c in range(u["K"]):
+                dr = b.problem(m).draws(chain=c)
+                d2h += sum(v.nbytes for v in dr.values())
+    n_e2e = max(1, args.c3_steps // 5)
+    t_e2e = max_over_ranks(dist, time.perf_counter() - t0)
+    launches = sum(b.problem(m).launches_per_sweep() for m in range(len(ds)))
+    b.close()
+    sweeps_s = ws * args.c3_steps / (ms / 1e3)
+    # lower bounds of a sweep: X read once (HBM), and the K factorizations as
+    # FP32-pair FMAs on the CUDA cores (K p^3 / 6 each) at the ALU issue bound
+    t_hbm = (x_bytes + y_bytes) / (peak * 1e9) * 1e3
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz, mhz_src = float(json.load(f)["sm_max_mhz"]), "measured"
+    except (OSError, KeyError, ValueError):
+        mhz, mhz_src = 2070.0, "nominal"
+    alu_peak = sms * 128 * mhz * 1e6 / 12.0  # pair-FMAs/s
+    pair_fmas = sum(u["K"] * float(p) ** 3 / 6.0 for _, p in sizes)
+    t_alu = pair_fmas / alu_peak * 1e3
+    bound = max(t_hbm, t_alu)
+    return {"value": sweeps_s * u["n"] * u["K"], "unit": "chain-sweeps/s", "batch_sweeps_per_s": sweeps_s,
+            "problems": u["n"], "K": u["K"], "steps": args.c3_steps, "warmup": 6, "ms_per_sweep": ms_sweep,
+            "workload": u["name"],
+            "realised": {"sum_x_bytes": x_bytes, "sum_4p3_over_3_flop": sum(4.0 * p ** 3 / 3.0 for _, p in sizes),
+                         "sum_K_p3_over_6_pair_fma": pair_fmas, "N_min_max": [min(n for n, _ in sizes),
+                                                                                max(n for n, _ in sizes)],
+                         "p_min_max": [min(p for _, p in sizes), max(p for _, p in sizes)]},
+            "roofline": {"bound": "hbm" if t_hbm >= t_alu else "alu", "achieved_ms": ms_sweep,
+                         "bound_ms": bound, "frac": bound / ms_sweep, "hbm_ms": t_hbm, "alu_ms": t_alu,
+                         "hbm_peak_gbs": peak, "peak_source": peak_kind,
+                         "alu_peak": f"SMs x 128 FP32 lanes x {mhz_src} max SM clock / 12 FP32 instructions "
+                                     "per pair-FMA"},
+            "tuner": {"best_ms_per_sweep": best, "trials": trials, "tune_s": t_tune,
+                      "xk_chains": sorted({sh["xk_chains"] for sh in shapes}),
+                      "xk_stages": sorted({sh["xk_stages"] for sh in shapes})},
+            "e2e": {"value": ws * n_e2e * u["n"] * u["K"] / t_e2e, "unit": "chain-sweeps/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h / n_e2e),
+                    "includes": "per step one batch sweep and the D2H of every chain's newest draw; inputs were "
+                                f"copied from host once at init ({t_init:.1f} s, {(x_bytes + y_bytes) / 1e9:.2f} GB)"},
+            "gpu_launches_per_sweep": launches, "init_s": t_init, "gen_s": t_gen, "clocks": clk.summary()}
+
+
 def run_tn_compare(d, pkg, torch, local, reps=20):
     """The latent draw alone, both samplers, on this workload's mu* = y* x_i beta_true
     (N draws): time per launch (CUDA events), proposals per draw, and how long a
@@ -422,6 +517,8 @@ def main(argv=None):
                     help="also time the batched form: K chains on BF16 X (0: skip)")
     ap.add_argument("--k-steps", type=int, default=20)
     ap.add_argument("--no-tn", action="store_true", help="skip the standalone sampler comparison")
+    ap.add_argument("--no-c3", action="store_true", help="skip the uneven multi-problem batch")
+    ap.add_argument("--c3-steps", type=int, default=50, help="timed sweeps of the uneven batch")
     ap.add_argument("--traffic-from", default=None, metavar="CSV",
                     help="write profiles/<kernel>_traffic.json from an ncu CSV of --workload c1s or c2s and exit")
     ap.add_argument("--traffic-command", default="", help="the ncu command that made the CSV (recorded)")
@@ -527,6 +624,10 @@ def main(argv=None):
     if args.k_chains > 1:
         kch = run_k_chains(args, WORKLOADS["c2"], pkg, torch, dist, ws, rank, local, chol, value)
 
+    c3 = None
+    if not args.no_c3 and wl is WORKLOADS["c1"]:
+        c3 = run_uneven_batch(args, pkg, torch, dist, ws, rank, local, chol)
+
     tnc = None
     if rank == 0 and not args.no_tn and wl["dt"] in ("f32", "f64"):
         tnc = run_tn_compare(d, pkg, torch, local)
@@ -549,7 +650,7 @@ def main(argv=None):
                 "clocks": clk.summary(),
                 "kernel_ms_per_sweep": {g: (v[0] / max(v[1], 1)) for g, v in groups.items()},
                 "hbm_roofline_frac_whole_sweep": (bytes_per_launch / (ms / args.steps / 1e3) / 1e9) / 8000.0,
-                "k_chains": kch, "tn_samplers": tnc}
+                "k_chains": kch, "uneven_batch": c3, "tn_samplers": tnc}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -25,7 +25,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["make_problem", "paper_beta", "fp8_e4m3_values", "stored_to_float64",
-           "counter_uniform_bits"]
+           "counter_uniform_bits", "uneven_sizes"]
 
 
 def paper_beta(p: int) -> np.ndarray:
@@ -162,6 +162,17 @@ def make_problem(N: int, p: int, n_nonzero: int, x_dtype: str = "f64", seed: int
         list(ex.map(fill, range(len(starts))))
     return {"X": X, "scales": scales, "y": y, "beta_true": beta_true,
             "x_dtype": x_dtype, "N": N, "p": p}
+
+
+def uneven_sizes(n: int, N_range=(10_000, 200_000), p_range=(50, 2000), seed: int = 0) -> list:
+    """Sizes (N_m, p_m) of n independent problems, each log-uniform on its
+    range (rounded to integers), from a Philox stream of its own keyed by seed."""
+    rng = _chunk_rng(seed, 1 << 40)
+    lo_n, hi_n = np.log(N_range[0]), np.log(N_range[1])
+    lo_p, hi_p = np.log(p_range[0]), np.log(p_range[1])
+    Ns = np.rint(np.exp(rng.uniform(lo_n, hi_n, size=n))).astype(np.int64)
+    ps = np.rint(np.exp(rng.uniform(lo_p, hi_p, size=n))).astype(np.int64)
+    return [(int(a), int(b)) for a, b in zip(Ns, ps)]
 
 
 def counter_uniform_bits(n: int, seed: int) -> np.ndarray:

@@ -91,7 +91,8 @@ typedef struct hs_probit hs_probit;  /* opaque handle */
 
 typedef struct hs_probit_config {
   int32_t x_dtype;     /* HS_X_*; hs_probit_init uses HS_X_F32 */
-  int32_t x_is_device; /* 1: X, y and x_scales are device pointers (copied) */
+  int32_t x_is_device; /* 1: X, y and x_scales are device pointers (copied);
+                          HS_X_ADOPT: as 1, but X is used in place (see hs_probit_init_ex) */
   int32_t thin;        /* keep every thin-th sweep in the draw ring (>= 1) */
   int32_t ring_size;   /* number of draws the device ring holds (>= 1) */
   int32_t debug;       /* 1: keep z and X^T z of the last sweep for debug_* */
@@ -103,10 +104,22 @@ typedef struct hs_probit_config {
   void* stream;        /* cudaStream_t for the sweep; NULL: library-owned stream */
   const float* x_scales; /* HS_X_FP8E4M3 only: p column scales (host or device) */
   int32_t chol_sched;  /* HS_SCHED_*; ignored for HS_CHOL_F64 */
-  int32_t num_chains;  /* K independent chains sharing X (1..32; > 1 needs HS_X_BF16 and p <= 1536) */
+  int32_t num_chains;  /* K independent chains sharing X (1..32) */
   int32_t beta_solve;  /* HS_BETA_* */
-  int32_t reserved[5];
+  int32_t update_mask; /* test hook: 0 = every variable is drawn (the sampler); otherwise
+                          only the HS_UPD_* variables set here are drawn each sweep, the
+                          others keep their values (z and beta are always drawn) */
+  int32_t reserved[4];
 } hs_probit_config;
+
+/* cfg.x_is_device value: adopt the caller's device X without a copy. */
+#define HS_X_ADOPT 2
+
+/* Bits of cfg.update_mask (Eq. 12: the shrinkage variables). */
+#define HS_UPD_LAMBDA 1  /* lambda_j^{-2} */
+#define HS_UPD_TAU    2  /* tau^{-2} */
+#define HS_UPD_NU     4  /* nu_j^{-1} */
+#define HS_UPD_XI     8  /* xi^{-1} */
 
 /* Values of one sampler state (Eq. 12 variables).  Arrays are host memory of
  * length p owned by the caller. */
@@ -134,8 +147,12 @@ hs_probit* hs_probit_init(const float* X, const uint8_t* y, int64_t N, int64_t p
 
 /* As hs_probit_init with a configuration.  X is of type cfg->x_dtype (double,
  * float, uint16 bf16 bits or uint8 e4m3 codes), host or device per
- * cfg->x_is_device; X is copied, never adopted.  For HS_X_FP8E4M3 the value of
- * X[i][j] is x_scales[j] * e4m3(X[i][j]).  cfg may be NULL (defaults). */
+ * cfg->x_is_device, and copied; with cfg->x_is_device = HS_X_ADOPT the
+ * device X is used in place instead (zero copy, e.g. a torch CUDA tensor):
+ * its rows must be 16-byte multiples (p * element size) and X 16-byte
+ * aligned, else HS_EINVAL; the caller keeps X alive and unchanged until
+ * hs_probit_free.  For HS_X_FP8E4M3 the value of X[i][j] is
+ * x_scales[j] * e4m3(X[i][j]).  cfg may be NULL (defaults). */
 hs_probit* hs_probit_init_ex(const hs_probit_config* cfg, const void* X, const uint8_t* y,
                              int64_t N, int64_t p, uint64_t seed);
 
@@ -287,16 +304,31 @@ int64_t hs_chol_block_task_list(int32_t T, int32_t k0, int32_t k1, int32_t worke
 
 /* ---- K chains on one X (Sect. 5 sweep for each chain; batched form) --------
  * A handle made with cfg.num_chains = K > 1 runs K independent chains on the
- * same BF16 X.  Chain m uses chain id cfg.chain + m in its Philox counters, so
- * it is the same transition as a one-chain handle with that chain id.  The
- * X-stream of all K chains is one pass over X on the tensor cores (eta = X B
- * and X^T Z as BF16 products, beta and z each split into two BF16 parts,
- * FP32 accumulation); the factorizations of all chains are one launch (on the
- * single-launch schedule, by default without the inverse factor, beta then
- * coming from block substitution: see beta_solve), and the other steps run per
- * chain.  The sweep count k is shared: hs_probit_sweep advances every chain,
- * and the last set_state call sets k for all of them.  The functions without a
- * chain argument act on chain 0. */
+ * same X.  Chain m uses chain id cfg.chain + m in its Philox counters, so
+ * it is the same transition as a one-chain handle with that chain id.  For
+ * BF16 X the X-stream of all K chains is one pass over X on the tensor cores
+ * (eta = X B and X^T Z as BF16 products, beta and z each split into two BF16
+ * parts, FP32 accumulation), for p <= 1536 (K > 16) or p <= 3584 (K <= 16);
+ * otherwise it is one pass of the one-chain X-stream per chain.  The
+ * factorizations of all chains are one launch (on the single-launch
+ * schedule, by default without the inverse factor, beta then coming from
+ * block substitution: see beta_solve), and the other steps run per chain.
+ * The sweep count k is shared: hs_probit_sweep advances every chain, and the
+ * last set_state call sets k for all of them.  The functions without a chain
+ * argument act on chain 0. */
+
+/* Asynchronous form of hs_probit_draws_chain: starts copying up to
+ * max_draws of the chain's unread draws into the caller's host buffers on a
+ * side stream and returns the count at once, so the copy runs while later
+ * sweeps compute (Sect. 5: Monte Carlo output downloaded through CUDA
+ * streams while the sampler runs).  Page-locked buffers make the copy truly
+ * asynchronous; the buffers must stay valid, and are not to be read, until
+ * hs_probit_draws_wait returns.  A later sweep that would overwrite a ring
+ * slot still being copied waits for the copy first. */
+int64_t hs_probit_draws_async(hs_probit* h, int chain, double* beta, double* lambda_inv2, double* tau_inv2,
+                              int64_t max_draws);
+/* Wait for every copy started by hs_probit_draws_async on the handle. */
+int hs_probit_draws_wait(hs_probit* h);
 
 /* Number of chains of the handle (>= 1), or HS_EINVAL. */
 int hs_probit_num_chains(const hs_probit* h);
@@ -316,6 +348,85 @@ int64_t hs_probit_draws_chain(hs_probit* h, int chain, double* beta, double* lam
  * values) of one chain; host buffers owned by the caller. */
 int hs_probit_debug_z_chain(hs_probit* h, int chain, double* z_out);
 int hs_probit_debug_xtz_chain(hs_probit* h, int chain, double* xtz_out);
+
+/* ---- launch shapes ---------------------------------------------------------
+ * Grid and tile sizes of a handle's kernels.  They change how the work of a
+ * sweep is spread over the GPU, never what a sweep computes: every shape
+ * gives the same transition (bit for bit for everything but the order of
+ * the X^T z partial sums, which depends on the X-stream's CTA count).  The
+ * batch tuner (below) sets them; hs_probit_set_launch_shape lets a caller do
+ * the same.  A field of 0 leaves that size as it is. */
+typedef struct hs_launch_shape {
+  int32_t xk_chains;    /* chain columns of a tensor-core X-stream tile: 16 (K <= 16) or 32 */
+  int32_t xk_stages;    /* shared-memory ring stages of that X-stream: 4, 6 or 8 */
+  int32_t xstream_ctas; /* CTAs of the X-stream: 1 .. the value the handle started with */
+  int32_t chol_ctas;    /* blocks of each factorization launch: K + 1 .. the starting value */
+  int32_t trail_ctas;   /* CTAs of the tensor-core trailing updates: 1 .. the starting value */
+  int32_t reserved[3];  /* must be 0 */
+} hs_launch_shape;
+
+/* Current shapes (fields that do not apply to the handle read 0). */
+int hs_probit_get_launch_shape(const hs_probit* h, hs_launch_shape* out);
+/* Set shapes; waits for the handle's work in flight and drops its captured
+ * graph.  HS_EINVAL for a size out of range (nothing is changed),
+ * HS_EUNSUPPORTED for X-stream tile fields on a handle without the
+ * tensor-core X-stream. */
+int hs_probit_set_launch_shape(hs_probit* h, const hs_launch_shape* in);
+
+/* ---- many problems in one launch (Sect. 4: exchangeable models) ------------
+ * The sweep applies to any data-augmented model with an exchangeable
+ * likelihood (Sect. 4, Eqs. 1-3); a batch runs n independent Horseshoe probit
+ * problems of uneven N and p side by side, each with K = cfg->num_chains
+ * chains.  Problem m is an ordinary handle made by hs_probit_init_ex(cfg', X_m,
+ * y_m, N_m, p_m, seed) with cfg'.problem = cfg->problem + m (its own Philox
+ * counter field, so its transition is exactly that handle's) and
+ * cfg'.x_scales = problems[m].x_scales.  One call of hs_probit_batch_sweep
+ * replays, per sweep, a single CUDA graph holding every problem's sweep on
+ * branches of its own, so the problems' kernels share the GPU. */
+typedef struct hs_problem {
+  const void* X;          /* N x p of cfg->x_dtype; host, or device if cfg->x_is_device (copied) */
+  const uint8_t* y;       /* N values in {0, 1}; same memory kind as X (copied) */
+  int64_t N;              /* >= 2 */
+  int64_t p;              /* >= 1 */
+  const float* x_scales;  /* p column scales for HS_X_FP8E4M3, else NULL */
+} hs_problem;
+
+typedef struct hs_probit_batch hs_probit_batch;  /* opaque */
+
+/* Make n >= 1 problems (problems: host array of n).  cfg->stream, if set, is
+ * the stream the batch's graph is launched on; cfg->use_graph is ignored.
+ * NULL on error; hs_probit_last_error() gives the status. */
+hs_probit_batch* hs_probit_batch_init(const hs_probit_config* cfg, int32_t n, const hs_problem* problems,
+                                      uint64_t seed);
+/* Number of problems, or HS_EINVAL. */
+int32_t hs_probit_batch_size(const hs_probit_batch* b);
+/* Problem m's handle (owned by the batch): draws, get/set_state and the
+ * debug copies work on it as on any handle.  NULL if m is out of range. */
+hs_probit* hs_probit_batch_problem(hs_probit_batch* b, int32_t m);
+/* n_iter sweeps of every problem.  HS_ESTATE if a problem is in an error
+ * state; otherwise the first failing problem's status (the others' states
+ * are valid). */
+int hs_probit_batch_sweep(hs_probit_batch* b, int64_t n_iter);
+/* The autotuner: times trial launch shapes over `sweeps` sweeps each and
+ * keeps the fastest.  Candidates: for each problem, X-stream CTAs and
+ * factorization blocks in proportion to its share of the batch's X bytes and
+ * factorization flops, at several oversubscription factors, and the
+ * tensor-core X-stream's chain columns and ring stages.  Every problem's
+ * state is saved first and restored after, so tuning leaves the chains where
+ * they were.  *best_ms receives the best time per sweep (may be NULL). */
+int hs_probit_batch_tune(hs_probit_batch* b, int32_t sweeps, double* best_ms);
+/* One trial of the last hs_probit_batch_tune call. */
+typedef struct hs_tune_trial {
+  double ms_per_sweep;  /* measured time per batch sweep */
+  int32_t oversub_x4;   /* 4 x the oversubscription factor of the proportional shares */
+  int32_t xk_chains;    /* tensor-core X-stream chain columns tried (0: unchanged) */
+  int32_t xk_stages;    /* its ring stages tried (0: unchanged) */
+  int32_t reserved;
+} hs_tune_trial;
+/* Copies up to max trials into out (host); returns the number of trials. */
+int32_t hs_probit_batch_tune_trials(const hs_probit_batch* b, hs_tune_trial* out, int32_t max);
+/* Release the batch and its problems.  NULL is allowed. */
+void hs_probit_batch_free(hs_probit_batch* b);
 
 /* Release the handle and everything it owns.  NULL is allowed. */
 void hs_probit_free(hs_probit* h);

@@ -24,13 +24,16 @@ import numpy as np
 __all__ = ["HSProbit", "HSProbitError", "load_library", "library_path", "STATUS",
            "X_F64", "X_F32", "X_BF16", "X_FP8E4M3", "CHOL_F64", "CHOL_DF32",
            "SCHED_AUTO", "SCHED_COLUMNS", "SCHED_SINGLE", "SCHED_TENSOR", "BETA_AUTO", "BETA_INVERSE", "BETA_SUBST",
-           "TN_INVCDF", "TN_REJECTION", "tn_sample"]
+           "TN_INVCDF", "TN_REJECTION", "tn_sample", "HSProbitBatch", "X_ADOPT", "UPD_LAMBDA", "UPD_TAU",
+           "UPD_NU", "UPD_XI"]
 
 X_F64, X_F32, X_BF16, X_FP8E4M3 = 0, 1, 2, 3
 CHOL_F64, CHOL_DF32 = 0, 1
 SCHED_AUTO, SCHED_COLUMNS, SCHED_SINGLE, SCHED_TENSOR = 0, 1, 2, 3
 BETA_AUTO, BETA_INVERSE, BETA_SUBST = 0, 1, 2
 TN_INVCDF, TN_REJECTION = 0, 1
+X_ADOPT = 2
+UPD_LAMBDA, UPD_TAU, UPD_NU, UPD_XI = 1, 2, 4, 8
 STATUS = {0: "HS_OK", -1: "HS_EINVAL", -2: "HS_ENOMEM", -3: "HS_ECUDA", -4: "HS_ENOTPD",
           -5: "HS_ENONFINITE", -6: "HS_ETIMEOUT", -7: "HS_ESTATE", -8: "HS_EUNSUPPORTED"}
 KERNEL_GROUPS = {"xstream": 0, "reduce": 1, "shrink": 2, "cholesky": 3, "tail": 4, "gram": 5}
@@ -54,12 +57,27 @@ class _Config(ctypes.Structure):
                 ("chol_arith", ctypes.c_int32), ("device", ctypes.c_int32), ("chain", ctypes.c_uint32),
                 ("problem", ctypes.c_uint32), ("stream", ctypes.c_void_p), ("x_scales", ctypes.c_void_p),
                 ("chol_sched", ctypes.c_int32), ("num_chains", ctypes.c_int32), ("beta_solve", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("update_mask", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class _StateView(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_void_p), ("lambda_inv2", ctypes.c_void_p), ("nu_inv", ctypes.c_void_p),
                 ("tau_inv2", ctypes.c_double), ("xi_inv", ctypes.c_double), ("k", ctypes.c_int64)]
+
+
+class _LaunchShape(ctypes.Structure):
+    _fields_ = [("xk_chains", ctypes.c_int32), ("xk_stages", ctypes.c_int32), ("xstream_ctas", ctypes.c_int32),
+                ("chol_ctas", ctypes.c_int32), ("trail_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("y", ctypes.c_void_p), ("N", ctypes.c_int64), ("p", ctypes.c_int64),
+                ("x_scales", ctypes.c_void_p)]
+
+
+class _TuneTrial(ctypes.Structure):
+    _fields_ = [("ms_per_sweep", ctypes.c_double), ("oversub_x4", ctypes.c_int32), ("xk_chains", ctypes.c_int32),
+                ("xk_stages", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _LIB = None
@@ -106,6 +124,19 @@ _PROTOS = {
                                                  ctypes.c_void_p, ctypes.c_int64]),
     "hs_tn_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
                                     ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "hs_probit_draws_async": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_int64]),
+    "hs_probit_draws_wait": (ctypes.c_int, [ctypes.c_void_p]),
+    "hs_probit_get_launch_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_LaunchShape)]),
+    "hs_probit_set_launch_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_LaunchShape)]),
+    "hs_probit_batch_init": (ctypes.c_void_p, [ctypes.POINTER(_Config), ctypes.c_int32, ctypes.POINTER(_Problem),
+                                               ctypes.c_uint64]),
+    "hs_probit_batch_size": (ctypes.c_int32, [ctypes.c_void_p]),
+    "hs_probit_batch_problem": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int32]),
+    "hs_probit_batch_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "hs_probit_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "hs_probit_batch_tune_trials": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(_TuneTrial), ctypes.c_int32]),
+    "hs_probit_batch_free": (None, [ctypes.c_void_p]),
     "hs_probit_xstream_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
@@ -162,9 +193,11 @@ class HSProbit:
     def __init__(self, X, y, seed: int = 0, *, scales=None, thin: int = 1, ring_size: int = 1024,
                  debug: bool = False, use_graph: bool = False, chol_arith: int = CHOL_DF32, chain: int = 0,
                  problem: int = 0, stream=None, device: int = 0, x_dtype: int | None = None,
-                 chol_sched: int = SCHED_AUTO, num_chains: int = 1, beta_solve: int = BETA_AUTO):
+                 chol_sched: int = SCHED_AUTO, num_chains: int = 1, beta_solve: int = BETA_AUTO,
+                 adopt: bool = False, update_mask: int = 0):
         self._lib = load_library()
         self._h = None
+        self._adopted = None
         is_dev = hasattr(X, "is_cuda") and bool(X.is_cuda)
         dt = _infer_dtype(X) if x_dtype is None else int(x_dtype)
         self._keep = []
@@ -183,7 +216,10 @@ class HSProbit:
         cfg = _Config()
         self._lib.hs_probit_config_default(ctypes.byref(cfg))
         cfg.x_dtype = dt
-        cfg.x_is_device = 1 if is_dev else 0
+        cfg.x_is_device = (X_ADOPT if adopt else 1) if is_dev else 0
+        if adopt and not is_dev:
+            raise ValueError("adopt needs X in CUDA device memory")
+        cfg.update_mask = update_mask
         cfg.thin = thin
         cfg.ring_size = ring_size
         cfg.debug = 1 if debug else 0
@@ -208,6 +244,8 @@ class HSProbit:
         if not h:
             raise HSProbitError(self._lib.hs_probit_last_error(), "hs_probit_init_ex")
         self._h = ctypes.c_void_p(h)
+        if adopt:
+            self._adopted = Xc  # the library reads this tensor in place: keep it alive
         self._keep = []
         self.N, self.p, self.seed, self.x_dtype = int(N), int(p), int(seed), dt
 
@@ -235,6 +273,27 @@ class HSProbit:
         if got < 0:
             raise HSProbitError(got, "hs_probit_draws_chain")
         return {"beta": beta[:got], "lambda_inv2": lam[:got], "tau_inv2": tau[:got]}
+
+    def draws_async(self, out: dict, chain: int = 0) -> int:
+        """Start copying the chain's unread draws into ``out`` (arrays
+        "beta" (n, p), "lambda_inv2" (n, p), "tau_inv2" (n,), float64, ideally
+        page-locked) on a side stream; returns how many are being copied.
+        Read ``out`` only after ``draws_wait()``."""
+        n = min(len(out["beta"]), len(out["lambda_inv2"]), len(out["tau_inv2"]))
+        for k in ("beta", "lambda_inv2", "tau_inv2"):
+            a = out[k]
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or (k != "tau_inv2" and a.shape[1:] != (self.p,)):
+                raise ValueError(f"{k}: C-contiguous float64 with rows of p values expected")
+        got = self._lib.hs_probit_draws_async(self._h, int(chain), _ptr(out["beta"]), _ptr(out["lambda_inv2"]),
+                                              _ptr(out["tau_inv2"]), n)
+        if got < 0:
+            raise HSProbitError(got, "hs_probit_draws_async")
+        return int(got)
+
+    def draws_wait(self) -> None:
+        st = self._lib.hs_probit_draws_wait(self._h)
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_draws_wait")
 
     def get_state(self, chain: int = 0) -> dict:
         beta, lam, nu = np.empty(self.p), np.empty(self.p), np.empty(self.p)
@@ -297,6 +356,23 @@ class HSProbit:
     def launches_per_sweep(self) -> int:
         return int(self._lib.hs_probit_launches_per_sweep(self._h))
 
+    def launch_shape(self) -> dict:
+        """Grid and tile sizes of the handle's kernels (``hs_probit_get_launch_shape``)."""
+        ls = _LaunchShape()
+        st = self._lib.hs_probit_get_launch_shape(self._h, ctypes.byref(ls))
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_get_launch_shape")
+        return {f: int(getattr(ls, f)) for f in ("xk_chains", "xk_stages", "xstream_ctas", "chol_ctas", "trail_ctas")}
+
+    def set_launch_shape(self, **sizes) -> None:
+        """Change launch sizes (keyword per field; omitted fields stay)."""
+        ls = _LaunchShape()
+        for k, v in sizes.items():
+            setattr(ls, k, int(v))
+        st = self._lib.hs_probit_set_launch_shape(self._h, ctypes.byref(ls))
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_set_launch_shape")
+
     def debug_factor(self, chain: int = 0) -> np.ndarray:
         """The factorization's P x P work matrix of one chain (lower tiles: the factor)."""
         P = (self.p + 31) // 32 * 32
@@ -315,10 +391,125 @@ class HSProbit:
     def debug_wait_timeout(self, max_spins: int) -> int:
         return int(self._lib.hs_probit_debug_wait_timeout(self._h, int(max_spins)))
 
+    @classmethod
+    def _member(cls, lib, handle, N: int, p: int, seed: int, x_dtype: int, owner) -> "HSProbit":
+        """A view of a handle another object owns (a batch's problem)."""
+        self = cls.__new__(cls)
+        self._lib, self._h, self._keep, self._owner = lib, ctypes.c_void_p(handle), [], owner
+        self.N, self.p, self.seed, self.x_dtype = int(N), int(p), int(seed), int(x_dtype)
+        return self
+
     def close(self) -> None:
+        if getattr(self, "_owner", None) is not None:
+            self._h = None  # the owner frees the handle
+            return
         if self._h is not None and self._lib is not None:
             self._lib.hs_probit_free(self._h)
         self._h = None
+        self._adopted = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class HSProbitBatch:
+    """Independent problems of uneven N and p swept together (``hs_probit_batch_*``).
+
+    problems: list of (X, y) or (X, y, scales), host numpy arrays or torch
+    tensors (all host or all CUDA), X of one element type.  Problem m uses
+    Philox problem id ``problem + m``; each has ``num_chains`` chains.  One
+    ``sweep(n)`` replays, n times, one CUDA graph that holds a sweep of every
+    problem.  ``problem(m)`` gives problem m's handle as an ``HSProbit``.
+    """
+
+    def __init__(self, problems, seed: int = 0, *, num_chains: int = 1, thin: int = 1, ring_size: int = 1024,
+                 debug: bool = False, chol_arith: int = CHOL_DF32, chain: int = 0, problem: int = 0, stream=None,
+                 device: int = 0, x_dtype: int | None = None, chol_sched: int = SCHED_AUTO,
+                 beta_solve: int = BETA_AUTO):
+        self._lib = load_library()
+        self._b = None
+        if not problems:
+            raise ValueError("no problems")
+        keep, arr = [], (_Problem * len(problems))()
+        dts, dev = set(), set()
+        for m, pr in enumerate(problems):
+            X, y = pr[0], pr[1]
+            sc = pr[2] if len(pr) > 2 else None
+            dts.add(_infer_dtype(X) if x_dtype is None else int(x_dtype))
+            dev.add(bool(getattr(X, "is_cuda", False)))
+            if hasattr(X, "data_ptr"):
+                Xc, yc = X.contiguous(), y.contiguous()
+                xp, yp = Xc.data_ptr(), yc.data_ptr()
+            else:
+                Xc, yc = np.ascontiguousarray(X), np.ascontiguousarray(y, dtype=np.uint8)
+                xp, yp = Xc.ctypes.data, yc.ctypes.data
+            keep += [Xc, yc]
+            sp = None
+            if sc is not None:
+                scc = sc.contiguous() if hasattr(sc, "data_ptr") else np.ascontiguousarray(sc, dtype=np.float32)
+                keep.append(scc)
+                sp = scc.data_ptr() if hasattr(scc, "data_ptr") else scc.ctypes.data
+            arr[m] = _Problem(xp, yp, int(Xc.shape[0]), int(Xc.shape[1]), sp)
+        if len(dts) != 1 or len(dev) != 1:
+            raise ValueError("every problem's X must have one element type and sit on one side (host or device)")
+        cfg = _Config()
+        self._lib.hs_probit_config_default(ctypes.byref(cfg))
+        cfg.x_dtype = dts.pop()
+        cfg.x_is_device = 1 if dev.pop() else 0
+        cfg.thin, cfg.ring_size, cfg.debug = thin, ring_size, 1 if debug else 0
+        cfg.chol_arith, cfg.chol_sched, cfg.num_chains, cfg.beta_solve = chol_arith, chol_sched, num_chains, beta_solve
+        cfg.device, cfg.chain, cfg.problem = device, chain, problem
+        cfg.stream = ctypes.c_void_p(int(stream)) if stream is not None else None
+        b = self._lib.hs_probit_batch_init(ctypes.byref(cfg), len(problems), arr, ctypes.c_uint64(seed & (2**64 - 1)))
+        if not b:
+            raise HSProbitError(self._lib.hs_probit_last_error(), "hs_probit_batch_init")
+        self._b = ctypes.c_void_p(b)
+        self._members = [HSProbit._member(self._lib, self._lib.hs_probit_batch_problem(self._b, m),
+                                          arr[m].N, arr[m].p, seed, cfg.x_dtype, self)
+                         for m in range(len(problems))]
+        self.seed = int(seed)
+
+    def __len__(self) -> int:
+        return len(self._members)
+
+    def problem(self, m: int) -> HSProbit:
+        return self._members[m]
+
+    def sweep(self, n: int = 1) -> None:
+        st = self._lib.hs_probit_batch_sweep(self._b, int(n))
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_batch_sweep")
+
+    def tune(self, sweeps: int = 3) -> float:
+        """Run the autotuner; returns the best ms per batch sweep."""
+        ms = ctypes.c_double()
+        st = self._lib.hs_probit_batch_tune(self._b, int(sweeps), ctypes.byref(ms))
+        if st != 0:
+            raise HSProbitError(st, "hs_probit_batch_tune")
+        return float(ms.value)
+
+    def tune_trials(self) -> list:
+        n = int(self._lib.hs_probit_batch_tune_trials(self._b, None, 0))
+        arr = (_TuneTrial * max(n, 1))()
+        self._lib.hs_probit_batch_tune_trials(self._b, arr, n)
+        return [{"ms_per_sweep": t.ms_per_sweep, "oversub": t.oversub_x4 / 4.0, "xk_chains": t.xk_chains,
+                 "xk_stages": t.xk_stages} for t in arr[:n]]
+
+    def close(self) -> None:
+        for h in getattr(self, "_members", []):
+            h._h = None
+        if self._b is not None and self._lib is not None:
+            self._lib.hs_probit_batch_free(self._b)
+        self._b = None
 
     def __del__(self):
         try:

@@ -59,9 +59,11 @@ struct XKArgs {
   int p;
   int nch;                // 64-feature chunks (even)
   int fpad;               // nch * 64
-  int K;                  // chains (<= 32)
-  const void* bsw;        // nch x 8 KB: B^T (BF16 high and low parts), swizzled for the MMA
-  float* partials;        // grid x fpad x 32 FP32 (written)
+  int K;                  // chains (<= kc)
+  int kc;                 // chain columns of the launch shape (16 or 32)
+  int stages;             // ring stages of the launch shape (4, 6 or 8)
+  const void* bsw;        // nch x (kc x 256 B): B^T (BF16 high and low parts), swizzled for the MMA
+  float* partials;        // grid x fpad x kc FP32 (written)
   double* z_out;          // K x N (chain-major), or nullptr
   const int64_t* k_dev;   // sweeps done; this sweep is *k_dev + 1
   RngKey rng;             // rng.chain is chain 0's id; chain m uses rng.chain + m
@@ -69,11 +71,16 @@ struct XKArgs {
   unsigned int* sm_mark;  // or nullptr, as XStreamArgs::sm_mark
 };
 int xstream_k_chunks(int p);
-bool xstream_k_supported(int p);
-size_t xstream_k_smem_bytes(int p);
-cudaError_t xstream_k_prepare(int p);
+// Launch shapes: kc chain columns (16 or 32), stages ring stages (4, 6 or 8).
+bool xstream_k_supported(int p, int kc, int stages);
+int xstream_k_default_kc(int K);
+constexpr int kXkDefaultStages = 8;
+size_t xstream_k_smem_bytes(int kc, int stages);
+cudaError_t xstream_k_prepare(int kc, int stages);
 int xstream_k_grid(int64_t N, int num_sms);
-size_t xstream_k_partial_floats(int p, int grid);
+int64_t xstream_k_tiles(int64_t N);
+size_t xstream_k_partial_floats(int p, int grid, int kc);
+size_t xstream_k_bsw_bytes(int p, int kc);
 // Tensor map of BF16 X (N rows, ld columns) into map_out (128 bytes, 64-byte aligned); 0 on success.
 int xstream_k_make_map(const void* X, int64_t N, int ld, void* map_out);
 // B^T preparation and the X-stream kernel; then the fixed-order reduce of the partials.
@@ -123,6 +130,7 @@ struct ShrinkArgs {
   double* part;           // ceil(p / 128) block partial sums (scratch)
   unsigned int* ticket;   // zero between sweeps (scratch)
   int* err;
+  int update_mask;        // HS_UPD_* bits of the variables drawn (the others keep their values)
 };
 // nchains > 1: chains 0..nchains-1 at fixed strides past a's buffers (blockIdx.y = chain)
 cudaError_t shrink_launch(const ShrinkArgs& a, cudaStream_t s, int nchains = 1);
@@ -163,6 +171,11 @@ struct CholArgs {
   unsigned long long* sm_role;
   int prebuilt;                 // 1: A already holds the equilibrated precision matrix
                                 // (lower tiles), so no tile is formed from the Gram matrix
+  // 1: the single-launch schedule launches cooperatively (all blocks resident);
+  // 0: an ordinary launch, for grids that share the GPU with other work (the
+  // tasks are taken in list order and wait only on earlier ones or on the
+  // chains, which the first blocks to start walk, so residency is not needed)
+  int cooperative;
 };
 // Enqueues the whole factorization; *launches receives the kernel count.
 cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches);
@@ -244,6 +257,7 @@ struct TailArgs {
   double* ring_tau;        // ring
   int ring_size, thin;
   int* err;
+  int update_mask;         // HS_UPD_* bits of the variables drawn (the others keep their values)
 };
 // The beta tail in two parts: the beta and nu draws, then the commit (every
 // chain's commit must follow every chain's draws).

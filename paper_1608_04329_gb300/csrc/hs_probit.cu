@@ -95,6 +95,16 @@ struct hs_probit {
   int K = 1;
   int64_t* k_scratch = nullptr;             // K: commits of chains 0..K-2 record the sweep here
   int kgrid = 0;                            // batched X-stream CTAs
+  bool xk = false;                          // K chains on the tensor-core X-stream (else one pass per chain)
+  int xk_kc = 32, xk_stages = 8;            // its launch shape (chain columns, ring stages)
+  int grid_max = 0, kgrid_max = 0, trail_max = 0, chol_max = 0;  // launch sizes the buffers were made for
+  // draws copied on a side stream while later sweeps compute
+  cudaStream_t s_dl = nullptr;
+  cudaEvent_t ev_mark = nullptr, ev_dl = nullptr;
+  int64_t dl_oldest = -1;                   // oldest draw index a copy may still read, or -1
+  // launch shapes set by a batch (hs_probit_batch_*): no cooperative launch, no
+  // chain SM isolation, and the factorization's grid chosen by the batch's tuner
+  bool batch_member = false;
   unsigned char* bsw = nullptr;             // B^T of the batched X-stream
   float* kpartials = nullptr;
   alignas(64) unsigned char xmap[128];      // tensor map of X (batched X-stream)
@@ -175,6 +185,29 @@ int status_from_err_bits(int bits) {
   return HS_ECUDA;
 }
 
+// Worker task list of the single-launch factorization: two task slots per
+// worker block, shared by the chains.
+std::vector<int> single_task_list(const hs_probit* h) {
+  const int slots = 2 * (h->chol_grid - h->K) / h->K;
+  return hs::chol_task_codes(h->T, slots > 1 ? slots : 1, h->chol_inverse);
+}
+
+// The block columns' task lists, one after another (fills blk_off, blk_len).
+std::vector<int> block_task_lists(hs_probit* h) {
+  std::vector<int> all;
+  h->blk_off.clear();
+  h->blk_len.clear();
+  for (int b = 0; hs::kTrailBlockTiles * b < h->T; ++b) {
+    const int slots = std::max(1, 2 * (h->chol_grid - h->K) / h->K);
+    const std::vector<int> c = hs::chol_block_task_codes(
+        h->T, hs::kTrailBlockTiles * b, std::min(hs::kTrailBlockTiles * (b + 1), h->T), slots);
+    h->blk_off.push_back((int)all.size());
+    h->blk_len.push_back((int)c.size());
+    all.insert(all.end(), c.begin(), c.end());
+  }
+  return all;
+}
+
 hs::XStreamArgs xstream_args(hs_probit* h) {
   hs::XStreamArgs a{};
   a.X = h->X;
@@ -200,6 +233,8 @@ hs::XKArgs xk_args(hs_probit* h) {
   a.nch = hs::xstream_k_chunks(h->p);
   a.fpad = a.nch * 64;
   a.K = h->K;
+  a.kc = h->xk_kc;
+  a.stages = h->xk_stages;
   a.bsw = h->bsw;
   a.partials = h->kpartials;
   a.z_out = h->cfg.debug ? h->z : nullptr;
@@ -218,9 +253,14 @@ hs::RngKey chain_rng(const hs_probit* h, int m) {
 
 size_t shrink_blocks(const hs_probit* h) { return (size_t)((h->p + 127) / 128); }
 
+int update_mask(const hs_probit* h) {
+  return h->cfg.update_mask ? h->cfg.update_mask : (HS_UPD_LAMBDA | HS_UPD_TAU | HS_UPD_NU | HS_UPD_XI);
+}
+
 hs::ShrinkArgs shrink_args(hs_probit* h, int m) {
   const size_t p = (size_t)h->p;
   hs::ShrinkArgs a{};
+  a.update_mask = update_mask(h);
   a.p = h->p;
   a.P = h->P;
   a.rng = chain_rng(h, m);
@@ -261,12 +301,14 @@ hs::CholArgs chol_args(hs_probit* h, int m) {
   a.sync_words = h->chol_words;
   a.order = h->chol_order;
   a.inverse = h->chol_inverse ? 1 : 0;
+  a.cooperative = h->batch_member ? 0 : 1;
   return a;
 }
 
 hs::TailArgs tail_args(hs_probit* h, int m) {
   const size_t p = (size_t)h->p, P2 = (size_t)h->P * h->P, rp = (size_t)h->ring_size * p;
   hs::TailArgs a{};
+  a.update_mask = update_mask(h);
   a.p = h->p;
   a.P = h->P;
   a.ld = h->ld;
@@ -388,6 +430,7 @@ cudaError_t enqueue_sweep(hs_probit* h) {
           // task list, bounds the launch (measured: fewer than about five tasks
           // per worker slot)
           ca.sm_role = (h->K == 1 || (double)h->blk_len[b] * h->K < 5.0 * slots) ? h->sm_role : nullptr;
+          if (h->batch_member) ca.sm_role = nullptr;  // the batch's tuner sizes the grid instead
           if ((ee = hs::chol_enqueue(ca, h->s1, nullptr)) != cudaSuccess) return ee;
           hs::TrailArgs tb = ta;
           tb.b = b;
@@ -417,7 +460,7 @@ cudaError_t enqueue_sweep(hs_probit* h) {
                                           h->s0)) != cudaSuccess)
         return e;
     }
-  } else {
+  } else if (h->xk) {
     const hs::XKArgs xa = xk_args(h);
     {
       ProfSpan sp(h, 0, h->s0);
@@ -427,6 +470,31 @@ cudaError_t enqueue_sweep(hs_probit* h) {
     {
       ProfSpan sp(h, 1, h->s0);
       if ((e = hs::xstream_k_reduce(xa, h->kgrid, h->xtz, h->p, h->s0)) != cudaSuccess) return e;
+    }
+  } else {
+    // K chains beyond the tensor-core X-stream (not BF16, or p past its TMEM
+    // budget): one pass of the one-chain X-stream per chain
+    const size_t part = (size_t)h->grid * h->ld * hs::partial_elem_bytes(h->x_dtype);
+    const size_t bc = (size_t)h->ld * (h->x_dtype == HS_X_F64 ? 8 : 4);
+    {
+      ProfSpan sp(h, 0, h->s0);
+      for (int m = 0; m < h->K && e == cudaSuccess; ++m) {
+        hs::XStreamArgs a = xstream_args(h);
+        a.beta_c = static_cast<const unsigned char*>(h->beta_c) + m * bc;
+        a.partials = static_cast<unsigned char*>(h->partials) + m * part;
+        a.z_out = h->cfg.debug ? h->z + (size_t)m * h->N : nullptr;
+        a.rng.chain += (uint32_t)m;
+        a.sm_mark = nullptr;
+        e = hs::xstream_launch(h->x_dtype, a, h->grid, h->s0);
+      }
+      if (e != cudaSuccess) return e;
+    }
+    {
+      ProfSpan sp(h, 1, h->s0);
+      for (int m = 0; m < h->K && e == cudaSuccess; ++m)
+        e = hs::reduce_partials_launch(h->x_dtype, static_cast<unsigned char*>(h->partials) + m * part, h->grid,
+                                       h->ld, h->p, h->colscale, h->xtz + (size_t)m * h->p, h->s0);
+      if (e != cudaSuccess) return e;
     }
   }
   if (!h->chol_inverse) {
@@ -523,6 +591,7 @@ void destroy(hs_probit* h) {
   if (!h) return;
   if (h->s0) cudaStreamSynchronize(h->s0);
   if (h->s1) cudaStreamSynchronize(h->s1);
+  if (h->s_dl) cudaStreamSynchronize(h->s_dl);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
   for (int i = 0; i < kProfGroups; ++i)
@@ -537,6 +606,9 @@ void destroy(hs_probit* h) {
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_shrink) cudaEventDestroy(h->ev_shrink);
   if (h->ev_xs) cudaEventDestroy(h->ev_xs);
+  if (h->ev_mark) cudaEventDestroy(h->ev_mark);
+  if (h->ev_dl) cudaEventDestroy(h->ev_dl);
+  if (h->s_dl) cudaStreamDestroy(h->s_dl);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->h_k) cudaFreeHost(h->h_k);
@@ -544,6 +616,21 @@ void destroy(hs_probit* h) {
   if (h->own_s0 && h->s0) cudaStreamDestroy(h->s0);
   (void)cudaGetLastError();
   delete h;
+}
+
+// Before n_iter more sweeps are enqueued on stream s: if they would write a
+// ring slot that a side-stream copy may still be reading, s waits for the
+// copies first.
+cudaError_t guard_ring(hs_probit* h, int64_t n_iter, cudaStream_t s) {
+  if (h->dl_oldest < 0) return cudaSuccess;
+  if (cudaEventQuery(h->ev_dl) == cudaSuccess) {
+    h->dl_oldest = -1;
+    return cudaSuccess;
+  }
+  (void)cudaGetLastError();  // cudaErrorNotReady
+  const int64_t newest_after = (h->k_host + n_iter) / h->thin;
+  if (newest_after - h->dl_oldest + 1 <= h->ring_size) return cudaSuccess;
+  return cudaStreamWaitEvent(s, h->ev_dl, 0);
 }
 
 int sync_and_check(hs_probit* h) {
@@ -620,15 +707,20 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
     fail(HS_EINVAL);
     return nullptr;
   }
-  if (Kc > 1 && (cfg.x_dtype != HS_X_BF16 || !hs::xstream_k_supported((int)p))) {
-    fail(HS_EUNSUPPORTED);
-    return nullptr;
-  }
+
   {
     // The X-stream takes at most 2048 16-byte slices per row (p <= 4096 for FP64 X).
     const int64_t eb = cfg.x_dtype == HS_X_F64 ? 8 : cfg.x_dtype == HS_X_F32 ? 4 : cfg.x_dtype == HS_X_BF16 ? 2 : 1;
     const int64_t ve = 16 / eb;
     if ((p + ve - 1) / ve > 2048) {
+      fail(HS_EINVAL);
+      return nullptr;
+    }
+    // an adopted X is the library's row layout as it stands: rows of whole
+    // 16-byte slices (no pad columns) from a 16-byte aligned base
+    if (cfg.x_is_device < 0 || cfg.x_is_device > HS_X_ADOPT ||
+        (cfg.x_is_device == HS_X_ADOPT && ((p * eb) % 16 != 0 || (reinterpret_cast<uintptr_t>(X) & 15u) != 0)) ||
+        (cfg.update_mask & ~(HS_UPD_LAMBDA | HS_UPD_TAU | HS_UPD_NU | HS_UPD_XI)) != 0) {
       fail(HS_EINVAL);
       return nullptr;
     }
@@ -658,6 +750,9 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   }
   h->cfg = cfg;
   h->K = Kc;
+  h->xk_kc = hs::xstream_k_default_kc(Kc);
+  h->xk_stages = hs::kXkDefaultStages;
+  h->xk = Kc > 1 && cfg.x_dtype == HS_X_BF16 && hs::xstream_k_supported((int)p, h->xk_kc, h->xk_stages);
   h->drained.assign((size_t)Kc, 0);
   h->device = cfg.device;
   h->x_dtype = cfg.x_dtype;
@@ -729,12 +824,15 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   const size_t K = (size_t)h->K;
   const size_t bc_bytes = (size_t)h->ld * (h->x_dtype == HS_X_F64 ? 8 : 4);
   h->grid = hs::xstream_grid(h->x_dtype, h->p, h->ld, N, num_sms > 0 ? num_sms : 1);
-  if (h->K > 1) {
-    check(hs::xstream_k_prepare(h->p));
+  if (h->xk) {
+    check(hs::xstream_k_prepare(h->xk_kc, h->xk_stages));
     h->kgrid = hs::xstream_k_grid(N, num_sms > 0 ? num_sms : 1);
   }
   h->chol_words = hs::chol_sync_words(h->P);
-  check(h->alloc(&h->X, (size_t)N * h->ld * h->elem));
+  if (cfg.x_is_device == HS_X_ADOPT)
+    h->X = const_cast<void*>(X);  // the caller's buffer, never freed here
+  else
+    check(h->alloc(&h->X, (size_t)N * h->ld * h->elem));
   check(h->alloc(&h->y, (size_t)N));
   if (cfg.x_dtype == HS_X_FP8E4M3) check(h->alloc(&h->colscale, (size_t)p * sizeof(float)));
   check(h->alloc(&h->beta, K * pd));
@@ -761,9 +859,7 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   if (h->chol_grid > 0) {
     check(h->alloc(&h->chol_sync, K * h->chol_words * sizeof(unsigned long long)));
     check(h->alloc(&h->sm_mark, hs::kSmMarks * sizeof(unsigned int)));
-    // two task slots per worker block, shared by the chains
-    const int slots = 2 * (h->chol_grid - h->K) / h->K;
-    order = hs::chol_task_codes(h->T, slots > 1 ? slots : 1, h->chol_inverse);
+    order = single_task_list(h);
     if (!order.empty()) check(h->alloc(&h->chol_order, order.size() * sizeof(int)));
   }
   if (h->tensor_sched) {
@@ -772,16 +868,7 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
     check(h->alloc(&h->sm_role, 2 * hs::kSmMarks * sizeof(unsigned long long)));
     if (e == cudaSuccess) check(cudaMemset(h->sm_role, 0, 2 * hs::kSmMarks * sizeof(unsigned long long)));
     check(h->alloc(&h->G2, P2 * 2 * sizeof(float)));
-    std::vector<int> all;
-    for (int b = 0; hs::kTrailBlockTiles * b < h->T; ++b) {
-      // task slots per chain: two per worker block, shared by the chains
-      const int slots = std::max(1, 2 * (h->chol_grid - h->K) / h->K);
-      const std::vector<int> c = hs::chol_block_task_codes(
-          h->T, hs::kTrailBlockTiles * b, std::min(hs::kTrailBlockTiles * (b + 1), h->T), slots);
-      h->blk_off.push_back((int)all.size());
-      h->blk_len.push_back((int)c.size());
-      all.insert(all.end(), c.begin(), c.end());
-    }
+    const std::vector<int> all = block_task_lists(h);
     check(h->alloc(&h->blk_order, std::max<size_t>(all.size(), 1) * sizeof(int)));
     if (e == cudaSuccess && !all.empty())
       check(cudaMemcpy(h->blk_order, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -789,11 +876,12 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
       e = cudaErrorInvalidValue;
     h->trail_grid = num_sms > 0 ? num_sms : 1;
   }
-  if (h->K == 1) {
-    check(h->alloc(&h->partials, (size_t)h->grid * h->ld * hs::partial_elem_bytes(h->x_dtype)));
+  if (!h->xk) {
+    check(h->alloc(&h->partials, K * h->grid * h->ld * hs::partial_elem_bytes(h->x_dtype)));
   } else {
-    check(h->alloc(&h->bsw, (size_t)hs::xstream_k_chunks(h->p) * 8192));
-    check(h->alloc(&h->kpartials, hs::xstream_k_partial_floats(h->p, h->kgrid) * sizeof(float)));
+    // sized for the widest launch shape (32 chain columns), so a tuner may switch
+    check(h->alloc(&h->bsw, hs::xstream_k_bsw_bytes(h->p, 32)));
+    check(h->alloc(&h->kpartials, hs::xstream_k_partial_floats(h->p, h->kgrid, 32) * sizeof(float)));
   }
   if (cfg.debug) check(h->alloc(&h->z, K * (size_t)N * sizeof(double)));
   check(h->alloc(&h->ring_beta, K * (size_t)h->ring_size * pd));
@@ -812,9 +900,11 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   }
   // ---- data ----
   const cudaMemcpyKind kind = cfg.x_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  check(cudaMemsetAsync(h->X, 0, (size_t)N * h->ld * h->elem, h->s0));
-  check(cudaMemcpy2DAsync(h->X, (size_t)h->ld * h->elem, X, (size_t)p * h->elem, (size_t)p * h->elem, (size_t)N,
-                          kind, h->s0));
+  if (cfg.x_is_device != HS_X_ADOPT) {
+    check(cudaMemsetAsync(h->X, 0, (size_t)N * h->ld * h->elem, h->s0));
+    check(cudaMemcpy2DAsync(h->X, (size_t)h->ld * h->elem, X, (size_t)p * h->elem, (size_t)p * h->elem, (size_t)N,
+                            kind, h->s0));
+  }
   check(cudaMemcpyAsync(h->y, y, (size_t)N, kind, h->s0));
   if (h->colscale) check(cudaMemcpyAsync(h->colscale, cfg.x_scales, (size_t)p * sizeof(float), kind, h->s0));
   check(cudaMemsetAsync(h->err, 0, sizeof(int), h->s0));
@@ -826,7 +916,7 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
     check(cudaMemsetAsync(h->chol_sync, 0, K * h->chol_words * sizeof(unsigned long long), h->s0));
     check(cudaMemsetAsync(h->sm_mark, 0, hs::kSmMarks * sizeof(unsigned int), h->s0));
   }
-  if (h->K > 1 && e == cudaSuccess && hs::xstream_k_make_map(h->X, N, h->ld, h->xmap) != 0) e = cudaErrorInvalidValue;
+  if (h->xk && e == cudaSuccess && hs::xstream_k_make_map(h->X, N, h->ld, h->xmap) != 0) e = cudaErrorInvalidValue;
   if (cfg.x_is_device) check(hs::check_y_launch(h->y, N, h->err, h->s0));
   // ---- cold start (Sect. 6.1): beta = 0, lambda = nu = tau = xi = 1, k = 0, every chain ----
   {
@@ -880,7 +970,11 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   // shrink, factorization (one launch for every chain when single-launch), two draws, commits
   h->launches = 1 + ((h->K > 1 && h->chol_grid > 0) ? chol_l : h->K * chol_l) + 2 +
                 (h->K > 1 ? 2 : 1) +
-                (h->K == 1 ? 2 : 3);
+                (h->K == 1 ? 2 : h->xk ? 3 : 2 * h->K);
+  h->grid_max = h->grid;
+  h->kgrid_max = h->kgrid;
+  h->trail_max = h->trail_grid;
+  h->chol_max = h->chol_grid;
   return h;
 }
 
@@ -914,6 +1008,7 @@ static int sweep_impl(hs_probit* h, int64_t n_iter) {
     e = build_graph(h);
     if (e != cudaSuccess) return cuda_status(e);
   }
+  e = guard_ring(h, n_iter, h->s0);
   for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) {
     if (graph) {
       if (h->profiling) e = arm_graph_events(h);
@@ -975,6 +1070,61 @@ int64_t hs_probit_draws_chain(hs_probit* h, int chain, double* beta, double* lam
   }
   h->drained[chain] = first + count - 1;
   return count;
+}
+
+int64_t hs_probit_draws_async(hs_probit* h, int chain, double* beta, double* lambda_inv2, double* tau_inv2,
+                              int64_t max_draws) {
+  if (!h || max_draws < 0 || chain < 0 || chain >= h->K) return HS_EINVAL;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return HS_ECUDA;
+  cudaError_t e = cudaSuccess;
+  if (!h->s_dl) {
+    e = cudaStreamCreateWithFlags(&h->s_dl, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_mark, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_dl, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  // the copies follow everything enqueued on the sweep stream so far
+  e = cudaEventRecord(h->ev_mark, h->s0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_dl, h->ev_mark, 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int64_t newest = h->k_host / h->thin;
+  int64_t first = h->drained[chain] + 1;
+  if (newest - first + 1 > h->ring_size) first = newest - h->ring_size + 1;
+  int64_t count = newest >= first ? newest - first + 1 : 0;
+  if (count > max_draws) count = max_draws;
+  const size_t p = (size_t)h->p;
+  const double* rb = h->ring_beta + (size_t)chain * h->ring_size * p;
+  const double* rl = h->ring_lam + (size_t)chain * h->ring_size * p;
+  const double* rt = h->ring_tau + (size_t)chain * h->ring_size;
+  for (int64_t d = 0; d < count && e == cudaSuccess;) {
+    const int64_t slot = (first + d - 1) % h->ring_size;
+    int64_t run = h->ring_size - slot;
+    if (run > count - d) run = count - d;
+    if (beta)
+      e = cudaMemcpyAsync(beta + d * p, rb + slot * p, run * p * sizeof(double), cudaMemcpyDeviceToHost, h->s_dl);
+    if (e == cudaSuccess && lambda_inv2)
+      e = cudaMemcpyAsync(lambda_inv2 + d * p, rl + slot * p, run * p * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->s_dl);
+    if (e == cudaSuccess && tau_inv2)
+      e = cudaMemcpyAsync(tau_inv2 + d, rt + slot, run * sizeof(double), cudaMemcpyDeviceToHost, h->s_dl);
+    d += run;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_dl, h->s_dl);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (count > 0) h->dl_oldest = h->dl_oldest < 0 ? first : std::min(h->dl_oldest, first);
+  h->drained[chain] = first + count - 1;
+  return count;
+}
+
+int hs_probit_draws_wait(hs_probit* h) {
+  if (!h) return HS_EINVAL;
+  if (!h->ev_dl) return HS_OK;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return HS_ECUDA;
+  if (cudaEventSynchronize(h->ev_dl) != cudaSuccess) return HS_ECUDA;
+  h->dl_oldest = -1;
+  return HS_OK;
 }
 
 int64_t hs_probit_draws(hs_probit* h, double* beta, double* lambda_inv2, double* tau_inv2, int64_t max_draws) {
@@ -1137,6 +1287,66 @@ int hs_probit_debug_factor(hs_probit* h, int chain, double* L_out) {
   return HS_OK;
 }
 
+int hs_probit_get_launch_shape(const hs_probit* h, hs_launch_shape* out) {
+  if (!h || !out) return HS_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->xk_chains = h->xk ? h->xk_kc : 0;
+  out->xk_stages = h->xk ? h->xk_stages : 0;
+  out->xstream_ctas = h->xk ? h->kgrid : h->grid;
+  out->chol_ctas = h->chol_grid;
+  out->trail_ctas = h->tensor_sched ? h->trail_grid : 0;
+  return HS_OK;
+}
+
+int hs_probit_set_launch_shape(hs_probit* h, const hs_launch_shape* in) {
+  if (!h || !in) return HS_EINVAL;
+  for (int r : in->reserved)
+    if (r != 0) return HS_EINVAL;
+  const int kc = in->xk_chains ? in->xk_chains : h->xk_kc;
+  const int st = in->xk_stages ? in->xk_stages : h->xk_stages;
+  const int xs = in->xstream_ctas ? in->xstream_ctas : (h->xk ? h->kgrid : h->grid);
+  const int cg = in->chol_ctas ? in->chol_ctas : h->chol_grid;
+  const int tg = in->trail_ctas ? in->trail_ctas : h->trail_grid;
+  if (in->xk_chains < 0 || in->xk_stages < 0 || in->xstream_ctas < 0 || in->chol_ctas < 0 || in->trail_ctas < 0)
+    return HS_EINVAL;
+  if ((in->xk_chains || in->xk_stages) && !h->xk) return HS_EUNSUPPORTED;
+  if (h->xk && (kc < h->K || !hs::xstream_k_supported(h->p, kc, st))) return HS_EINVAL;
+  if (xs < 1 || xs > (h->xk ? h->kgrid_max : h->grid_max)) return HS_EINVAL;
+  if (in->chol_ctas && (h->chol_grid == 0 || cg < h->K + 1 || cg > h->chol_max)) return HS_EINVAL;
+  if (in->trail_ctas && (!h->tensor_sched || tg < 1 || tg > h->trail_max)) return HS_EINVAL;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return HS_ECUDA;
+  if (cudaStreamSynchronize(h->s0) != cudaSuccess || cudaStreamSynchronize(h->s1) != cudaSuccess) return HS_ECUDA;
+  if (h->xk && hs::xstream_k_prepare(kc, st) != cudaSuccess) return HS_ECUDA;
+  h->xk_kc = kc;
+  h->xk_stages = st;
+  if (h->xk) h->kgrid = xs;
+  else h->grid = xs;
+  h->trail_grid = tg;
+  if (cg != h->chol_grid) {
+    // the task lists are ordered for the worker count; their lengths do not change
+    h->chol_grid = cg;
+    if (h->chol_order) {
+      const std::vector<int> order = single_task_list(h);
+      if (cudaMemcpy(h->chol_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return HS_ECUDA;
+    }
+    if (h->blk_order) {
+      const std::vector<int> all = block_task_lists(h);
+      if (!all.empty() &&
+          cudaMemcpy(h->blk_order, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return HS_ECUDA;
+    }
+  }
+  // a captured sweep holds the old shapes
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+  h->graph_ready = false;
+  return HS_OK;
+}
+
 int hs_probit_debug_error_word(const hs_probit* h, int* word) {
   if (!h || !word) return HS_EINVAL;
   *word = h->last_err_word;
@@ -1176,6 +1386,353 @@ void hs_probit_free(hs_probit* h) {
   if (!h) return;
   DeviceGuard dg(h->device);
   destroy(h);
+}
+
+}  // extern "C"
+
+// ---- many problems in one launch (Sect. 4) ------------------------------------
+struct hs_probit_batch {
+  std::vector<hs_probit*> probs;
+  int device = 0;
+  int num_sms = 1;
+  cudaStream_t root = nullptr;
+  bool own_root = false;
+  cudaEvent_t ev_start = nullptr;
+  std::vector<cudaEvent_t> ev_done;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<double> wx, wc;  // each problem's X bytes and factorization work (K P^3)
+  double wx_sum = 0, wc_sum = 0;
+  std::vector<hs_tune_trial> trials;
+};
+
+namespace {
+
+void batch_drop_graph(hs_probit_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+}
+
+// One graph for a sweep of every problem: the root stream forks to each
+// problem's streams and joins them again, so the problems are independent
+// branches.
+cudaError_t batch_build_graph(hs_probit_batch* b) {
+  batch_drop_graph(b);
+  cudaError_t e = cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t e2 = cudaEventRecord(b->ev_start, b->root);
+  for (size_t m = 0; m < b->probs.size() && e2 == cudaSuccess; ++m) {
+    hs_probit* h = b->probs[m];
+    e2 = cudaStreamWaitEvent(h->s0, b->ev_start, 0);
+    if (e2 == cudaSuccess) e2 = enqueue_sweep(h);
+    if (e2 == cudaSuccess) e2 = cudaEventRecord(b->ev_done[m], h->s0);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(b->root, b->ev_done[m], 0);
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->root, &g);
+  if (e2 != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return e2 != cudaSuccess ? e2 : e;
+  }
+  e = cudaGraphInstantiate(&b->gexec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return e;
+  }
+  b->graph = g;
+  return cudaSuccess;
+}
+
+// After the root stream is idle: each problem's error word and sweep count.
+int batch_check(hs_probit_batch* b) {
+  if (cudaStreamSynchronize(b->root) != cudaSuccess) return HS_ECUDA;
+  int first = HS_OK;
+  for (hs_probit* h : b->probs) {
+    const int st = sync_and_check(h);
+    if (st != HS_OK) {
+      h->sticky = st;
+      if (first == HS_OK) first = st;
+    }
+  }
+  return first;
+}
+
+// Launch shapes of every problem for oversubscription factor f: X-stream CTAs
+// in proportion to the problem's share of the X bytes, factorization blocks
+// and trailing-update CTAs to its share of the factorization work; kc, stages
+// for the tensor-core X-streams (0: leave as is).
+int batch_apply_shapes(hs_probit_batch* b, double f, int kc, int stages) {
+  for (size_t m = 0; m < b->probs.size(); ++m) {
+    hs_probit* h = b->probs[m];
+    const double sx = b->wx[m] / b->wx_sum, sc = b->wc[m] / b->wc_sum;
+    auto share = [](double v, int lo, int hi) {
+      const long r = std::lround(v);
+      return (int)std::max<long>(lo, std::min<long>(hi, r));
+    };
+    hs_launch_shape ls{};
+    ls.xstream_ctas = share(f * b->num_sms * sx, 1, h->xk ? h->kgrid_max : h->grid_max);
+    if (h->chol_grid > 0) ls.chol_ctas = share(f * h->chol_max * sc, h->K + 1, h->chol_max);
+    if (h->tensor_sched) ls.trail_ctas = share(f * b->num_sms * sc, 1, h->trail_max);
+    if (h->xk && kc > 0) {
+      const int c = kc >= h->K ? kc : 32;
+      if (hs::xstream_k_supported(h->p, c, stages)) {
+        ls.xk_chains = c;
+        ls.xk_stages = stages;
+      }
+    }
+    const int st = hs_probit_set_launch_shape(h, &ls);
+    if (st != HS_OK) return st;
+  }
+  return HS_OK;
+}
+
+// Time `sweeps` graph launches (after one untimed launch); ms per sweep.
+int batch_time(hs_probit_batch* b, int sweeps, double* ms) {
+  cudaError_t e = batch_build_graph(b);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->gexec, b->root);
+  if (e == cudaSuccess) e = cudaEventRecord(t0, b->root);
+  for (int i = 0; i < sweeps && e == cudaSuccess; ++i) e = cudaGraphLaunch(b->gexec, b->root);
+  if (e == cudaSuccess) e = cudaEventRecord(t1, b->root);
+  int st = e == cudaSuccess ? batch_check(b) : cuda_status(e);
+  float t = 0.f;
+  if (st == HS_OK && cudaEventElapsedTime(&t, t0, t1) != cudaSuccess) st = HS_ECUDA;
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  *ms = (double)t / sweeps;
+  return st;
+}
+
+void batch_destroy(hs_probit_batch* b) {
+  if (b->root) cudaStreamSynchronize(b->root);
+  batch_drop_graph(b);
+  for (hs_probit* h : b->probs) hs_probit_free(h);
+  for (cudaEvent_t ev : b->ev_done)
+    if (ev) cudaEventDestroy(ev);
+  if (b->ev_start) cudaEventDestroy(b->ev_start);
+  if (b->own_root && b->root) cudaStreamDestroy(b->root);
+  delete b;
+}
+
+hs_probit_batch* batch_init_impl(const hs_probit_config* cfg, int32_t n, const hs_problem* problems, uint64_t seed) {
+  if (!cfg || n < 1 || !problems) {
+    fail(HS_EINVAL);
+    return nullptr;
+  }
+  for (int32_t m = 0; m < n; ++m)
+    if (!problems[m].X || !problems[m].y || problems[m].N < 2 || problems[m].p < 1) {
+      fail(HS_EINVAL);
+      return nullptr;
+    }
+  DeviceGuard dg(cfg->device);
+  if (!dg.ok) {
+    fail(HS_ECUDA);
+    return nullptr;
+  }
+  hs_probit_batch* b = new hs_probit_batch();
+  b->device = cfg->device;
+  auto bail = [&](int st) -> hs_probit_batch* {
+    batch_destroy(b);
+    fail(st);
+    return nullptr;
+  };
+  if (cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess)
+    return bail(HS_ECUDA);
+  cudaError_t e = cudaSuccess;
+  if (cfg->stream) {
+    b->root = static_cast<cudaStream_t>(cfg->stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking);
+    b->own_root = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming);
+  b->ev_done.assign((size_t)n, nullptr);
+  for (int32_t m = 0; m < n && e == cudaSuccess; ++m) e = cudaEventCreateWithFlags(&b->ev_done[m], cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(cuda_status(e));
+  const int64_t eb = cfg->x_dtype == HS_X_F64 ? 8 : cfg->x_dtype == HS_X_F32 ? 4 : cfg->x_dtype == HS_X_BF16 ? 2 : 1;
+  for (int32_t m = 0; m < n; ++m) {
+    hs_probit_config c = *cfg;
+    c.problem = cfg->problem + (uint32_t)m;
+    c.x_scales = problems[m].x_scales;
+    c.stream = nullptr;
+    c.use_graph = 0;
+    hs_probit* h = init_ex_impl(&c, problems[m].X, problems[m].y, problems[m].N, problems[m].p, seed);
+    if (!h) return bail(g_last_error != HS_OK ? g_last_error : HS_ECUDA);
+    h->batch_member = true;
+    b->probs.push_back(h);
+    b->wx.push_back((double)problems[m].N * (double)problems[m].p * (double)eb);
+    b->wc.push_back((double)h->K * (double)h->P * (double)h->P * (double)h->P);
+    b->wx_sum += b->wx.back();
+    b->wc_sum += b->wc.back();
+  }
+  // the starting shapes: every problem's kernels sized to its share of the GPU
+  const int st = batch_apply_shapes(b, 1.0, 0, 0);
+  if (st != HS_OK) return bail(st);
+  g_last_error = HS_OK;
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+hs_probit_batch* hs_probit_batch_init(const hs_probit_config* cfg, int32_t n, const hs_problem* problems,
+                                      uint64_t seed) {
+  try {
+    return batch_init_impl(cfg, n, problems, seed);
+  } catch (...) {
+    fail(HS_ENOMEM);
+    return nullptr;
+  }
+}
+
+int32_t hs_probit_batch_size(const hs_probit_batch* b) { return b ? (int32_t)b->probs.size() : HS_EINVAL; }
+
+hs_probit* hs_probit_batch_problem(hs_probit_batch* b, int32_t m) {
+  if (!b || m < 0 || m >= (int32_t)b->probs.size()) return nullptr;
+  return b->probs[(size_t)m];
+}
+
+int hs_probit_batch_sweep(hs_probit_batch* b, int64_t n_iter) {
+  if (!b || n_iter < 0) return HS_EINVAL;
+  for (hs_probit* h : b->probs)
+    if (h->sticky != HS_OK) return HS_ESTATE;
+  if (n_iter == 0) return HS_OK;
+  DeviceGuard dg(b->device);
+  if (!dg.ok) return HS_ECUDA;
+  try {
+    // a problem's own work (a sweep, a state change) is ordered before the batch's
+    for (hs_probit* h : b->probs) {
+      if (cudaStreamSynchronize(h->s0) != cudaSuccess || cudaStreamSynchronize(h->s1) != cudaSuccess)
+        return HS_ECUDA;
+    }
+    if (!b->gexec) {
+      const cudaError_t e = batch_build_graph(b);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    cudaError_t e = cudaSuccess;
+    for (hs_probit* h : b->probs)
+      if (e == cudaSuccess) e = guard_ring(h, n_iter, b->root);
+    for (int64_t i = 0; i < n_iter && e == cudaSuccess; ++i) e = cudaGraphLaunch(b->gexec, b->root);
+    if (e != cudaSuccess) {
+      cudaStreamSynchronize(b->root);
+      return cuda_status(e);
+    }
+    return batch_check(b);
+  } catch (...) {
+    return HS_ENOMEM;
+  }
+}
+
+int hs_probit_batch_tune(hs_probit_batch* b, int32_t sweeps, double* best_ms) {
+  if (!b || sweeps < 1) return HS_EINVAL;
+  for (hs_probit* h : b->probs)
+    if (h->sticky != HS_OK) return HS_ESTATE;
+  DeviceGuard dg(b->device);
+  if (!dg.ok) return HS_ECUDA;
+  try {
+    // save every chain's state
+    struct Saved {
+      std::vector<double> beta, lam, nu;
+      double tau, xi;
+      int64_t k;
+    };
+    std::vector<std::vector<Saved>> saved(b->probs.size());
+    for (size_t m = 0; m < b->probs.size(); ++m) {
+      hs_probit* h = b->probs[m];
+      saved[m].resize((size_t)h->K);
+      for (int c = 0; c < h->K; ++c) {
+        Saved& sv = saved[m][(size_t)c];
+        sv.beta.resize((size_t)h->p);
+        sv.lam.resize((size_t)h->p);
+        sv.nu.resize((size_t)h->p);
+        hs_probit_state_view v{sv.beta.data(), sv.lam.data(), sv.nu.data(), 0.0, 0.0, 0};
+        const int st = hs_probit_get_state_chain(h, c, &v);
+        if (st != HS_OK) return st;
+        sv.tau = v.tau_inv2;
+        sv.xi = v.xi_inv;
+        sv.k = v.k;
+      }
+    }
+    b->trials.clear();
+    int status = HS_OK;
+    auto trial = [&](double f, int kc, int stages) -> double {
+      double ms = -1.0;
+      if (status != HS_OK) return ms;
+      status = batch_apply_shapes(b, f, kc, stages);
+      if (status == HS_OK) status = batch_time(b, sweeps, &ms);
+      if (status != HS_OK) return -1.0;
+      hs_tune_trial t{};
+      t.ms_per_sweep = ms;
+      t.oversub_x4 = (int32_t)std::lround(4.0 * f);
+      t.xk_chains = kc;
+      t.xk_stages = stages;
+      b->trials.push_back(t);
+      return ms;
+    };
+    // oversubscription of the proportional shares, then the X-stream tiles at the best one
+    const double fs[] = {0.5, 1.0, 2.0, 4.0};
+    double best = -1.0, best_f = 1.0;
+    for (double f : fs) {
+      const double ms = trial(f, 0, 0);
+      if (ms >= 0 && (best < 0 || ms < best)) {
+        best = ms;
+        best_f = f;
+      }
+    }
+    int best_kc = 0, best_st = 0;
+    bool any_xk = false;
+    for (hs_probit* h : b->probs) any_xk = any_xk || h->xk;
+    if (any_xk) {
+      const int shapes[][2] = {{16, 4}, {16, 6}, {16, 8}, {32, 8}};
+      for (const auto& sh : shapes) {
+        const double ms = trial(best_f, sh[0], sh[1]);
+        if (ms >= 0 && (best < 0 || ms < best)) {
+          best = ms;
+          best_kc = sh[0];
+          best_st = sh[1];
+        }
+      }
+    }
+    if (status == HS_OK) status = batch_apply_shapes(b, best_f, best_kc, best_st);
+    if (status == HS_OK) {
+      const cudaError_t e = batch_build_graph(b);
+      if (e != cudaSuccess) status = cuda_status(e);
+    }
+    // put every chain back where it was
+    for (size_t m = 0; m < b->probs.size(); ++m) {
+      hs_probit* h = b->probs[m];
+      if (h->sticky != HS_OK) continue;
+      for (int c = 0; c < h->K; ++c) {
+        Saved& sv = saved[m][(size_t)c];
+        hs_probit_state_view v{sv.beta.data(), sv.lam.data(), sv.nu.data(), sv.tau, sv.xi, sv.k};
+        const int st = hs_probit_set_state_chain(h, c, &v);
+        if (st != HS_OK && status == HS_OK) status = st;
+      }
+    }
+    if (best_ms) *best_ms = best;
+    return status;
+  } catch (...) {
+    return HS_ENOMEM;
+  }
+}
+
+int32_t hs_probit_batch_tune_trials(const hs_probit_batch* b, hs_tune_trial* out, int32_t max) {
+  if (!b || max < 0 || (max > 0 && !out)) return HS_EINVAL;
+  const int32_t n = (int32_t)b->trials.size();
+  for (int32_t i = 0; i < n && i < max; ++i) out[i] = b->trials[(size_t)i];
+  return n;
+}
+
+void hs_probit_batch_free(hs_probit_batch* b) {
+  if (!b) return;
+  DeviceGuard dg(b->device);
+  batch_destroy(b);
 }
 
 }  // extern "C"

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
     double u, uc;
     unit_pair(w.x, w.y, u, uc);
     const double bj = a.beta[j];
-    const double l = -log(u) / (a.nu[j] + tau * bj * bj * 0.5);
+    const double l = (a.update_mask & HS_UPD_LAMBDA) ? -log(u) / (a.nu[j] + tau * bj * bj * 0.5) : a.lam[j];
     a.lam_new[j] = l;
     part = l * bj * bj;
   }
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
     }
     if (lane == 0) {
       if (!found) set_error(a.err, kErrGamma);
-      const double t = g / (a.scal[1] + 0.5 * tot);
+      const double t = (a.update_mask & HS_UPD_TAU) ? g / (a.scal[1] + 0.5 * tot) : a.scal[0];
       *a.tau_new = t;
       s_tau = t;
       *a.ticket = 0u;  // ready for the next sweep
@@ -726,8 +726,13 @@ __global__ void __launch_bounds__(256) step_df_kernel(CholArgs a, int k) {
 // holds e once its tile is published; an update counter holds e*64 + n after
 // n updates (values of earlier sweeps are smaller, so nothing is reset).
 // Every wait is bounded (2 s) and a global abort word stops all blocks after
-// a timeout.  Blocks must all be resident: the kernel is launched
-// cooperatively.
+// a timeout.  The single-launch schedule is launched cooperatively, and
+// one chain's launch then gives the chain to a block on an SM the X-stream
+// left free.  An ordinary launch (a grid sharing the GPU with other
+// problems' work) needs no residency: the chains go to the first blocks to
+// start, and workers take tasks in list order, which respects every
+// dependency through the chains, so the earliest unfinished task is always
+// held by a running block or not yet taken.
 // Word layout of the scheduling buffer (u64, zeroed once when the handle is
 // made): header [0] epoch of the last finished launch, [1] exit ticket,
 // [2] abort, [3] chain claim (epoch), [4] start ticket, [5] chain SM
@@ -1156,9 +1161,10 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
     const unsigned long long e0 = *ps0.epoch + (kb == 0 ? 1ull : 0ull);
     s_e = e0;
     int role = 0, chain = 0;
-    if (nch == 1 && a.k1 == 0) {
+    if (nch == 1 && a.k1 == 0 && a.cooperative) {
       // The chain goes to a block on an SM the X-stream left free (no mark
-      // of this sweep), else to the last block to start.
+      // of this sweep), else to the last block to start (every block starts:
+      // the launch is cooperative).
       const unsigned int stamp = (unsigned int)(*a.k_dev + 1);
       const bool free_sm = a.sm_mark && smid < (unsigned)kSmMarks && __ldcg(a.sm_mark + smid) != stamp;
       if (free_sm && atomicCAS(ps0.claim, e0 - 1, e0) == e0 - 1) role = 1;
@@ -1198,7 +1204,9 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         role = (v < 2 * tag || (v & 1ull)) ? 2 : 0;
       }
     } else {
-      // several chains: the first nch blocks to start walk the diagonal chains
+      // several chains, or an ordinary launch: the first nch blocks to start
+      // walk the diagonal chains (a block that has started holds its role, so
+      // the chains run whether or not the rest of the grid is resident)
       const unsigned long long st = atomicAdd(ps0.start, 1ull);
       if (st == gridDim.x - 1) *ps0.start = 0;
       if (st < (unsigned long long)nch) {
@@ -1212,7 +1220,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
   __syncthreads();
   const unsigned long long e = s_e;
   const unsigned long long base = e * kEpochStride;
-  if (nch == 1 && a.k1 == 0 && s_role == 0 && gridDim.x >= 16) {
+  if (nch == 1 && a.k1 == 0 && a.cooperative && s_role == 0 && gridDim.x >= 16) {
     // Blocks that share the chain's SM stay idle, leaving it the whole SM
     // (at most 3 of them: 4 blocks fit on an SM).
     if (block_wait(ps0.chain_sm, e << 16, ps0, e, a.err, kSiteStartRole)) {
@@ -1720,7 +1728,7 @@ __global__ void __launch_bounds__(1024) commit_kernel(TailArgs a0) {
       bj = a.beta_new[j];
       a.beta[j] = bj;
       a.lam[j] = a.lam_new[j];
-      a.nu[j] = a.nu_new[j];
+      if (a.update_mask & HS_UPD_NU) a.nu[j] = a.nu_new[j];
       if (rec) {
         a.ring_beta[slot * a.p + j] = bj;
         a.ring_lam[slot * a.p + j] = a.lam_new[j];
@@ -1739,7 +1747,7 @@ __global__ void __launch_bounds__(1024) commit_kernel(TailArgs a0) {
     double u, uc;
     unit_pair(w.x, w.y, u, uc);
     a.scal[0] = tn;
-    a.scal[1] = -log(u) / (1.0 + tn);
+    if (a.update_mask & HS_UPD_XI) a.scal[1] = -log(u) / (1.0 + tn);
     if (rec) a.ring_tau[slot] = tn;
   }
   __syncthreads();
@@ -2198,7 +2206,7 @@ cudaError_t chol_enqueue(const CholArgs& a, cudaStream_t s, int* launches) {
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = a.cooperative ? 1 : 0;
     if (launches) *launches = 1;
     return cudaLaunchKernelEx(&cfg, chol_persistent_kernel, a);
   }

@@ -16,19 +16,24 @@
 // is exact in BF16 and the tensor cores accumulate in FP32.
 //
 // Data movement: X tiles arrive by TMA (box 64 features x 128 rows, 128-byte
-// swizzle) in a ring of 8 stages of 24 KB; in pass 1 each stage also receives
-// the matching 8 KB chunk of B^T (both parts, pre-swizzled in global memory,
-// L2-resident) by a bulk copy.  Pass 2 reads the same tile again, which the
+// swizzle) in a ring of S stages of 16 KB + the matching B^T chunk: in pass 1
+// each stage also receives the 64-feature chunk of B^T (both parts,
+// pre-swizzled in global memory, L2-resident) by a bulk copy.  Pass 2 reads the same tile again, which the
 // 129 MB L2 still holds, so HBM sees X once per sweep.  Each CTA owns a
 // contiguous range of row tiles and keeps its X^T Z partial in TMEM; at the
-// end it writes the partial (p x 32, FP32) and a second kernel sums the
+// end it writes the partial (p x KC, FP32) and a second kernel sums the
 // partials in a fixed order in FP64.
 //
-// Warp roles (640 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues
-// tcgen05.mma, warp 2 owns the TMEM allocation, warps 4..19 read eta, draw z
-// and write Z^T: warp w serves TMEM lane quadrant w % 4 (thread = tile row)
-// and chains 8 (w - 4) / 4 .. +7 (four warps per SM sub-partition hide the
-// latency of the draw's dependent arithmetic).  Every wait is
+// Launch shape: KC chain columns per tile (32, or 16 for K <= 16: the narrow
+// form, half the B^T and Z^T traffic through shared memory and half the TMEM
+// columns per feature group, so p up to 3584 fits), and S ring stages (4, 6
+// or 8); a tuner picks them (and the grid) per workload.
+//
+// Warp roles (128 + 32 KC / 2 threads): warp 0 lane 0 issues TMA, warp 1
+// lane 0 issues tcgen05.mma, warp 2 owns the TMEM allocation, warps 4.. read
+// eta, draw z and write Z^T: warp w serves TMEM lane quadrant w % 4 (thread =
+// tile row) and chains 8 (w - 4) / 4 .. +7 (several warps per SM
+// sub-partition hide the latency of the draw's dependent arithmetic).  Every wait is
 // bounded (2 s); a wait that runs out sets the timeout bit and all roles wind
 // down through a shared abort flag.
 #include <cuda.h>
@@ -36,6 +41,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "hs_common.cuh"
 #include "hs_internal.h"
@@ -43,19 +49,28 @@
 namespace hs {
 namespace {
 
-constexpr int kKc = 32;          // chains per launch (padded)
 constexpr int kTR = 128;         // rows per tile (MMA M of pass 1; K of pass 2)
 constexpr int kCF = 64;          // features per chunk (one 128-byte swizzle row)
-constexpr int kXStages = 8;      // ring stages (even: pass 2 takes them in pairs)
 constexpr uint32_t kXChunkBytes = kTR * kCF * 2;      // 16 KB: 128 rows x 64 features of X
-constexpr uint32_t kBChunkBytes = 2 * kKc * kCF * 2;  // 8 KB: 64 rows (hi chains, lo chains) x 128 B of B^T
-constexpr uint32_t kStageBytes = kXChunkBytes + kBChunkBytes;  // 24 KB: X chunk, then (pass 1) its B^T chunk
-constexpr uint32_t kZBlock = kKc * 128;               // 4 KB: 32 chains x 64 rows x 2 B
-constexpr int kEpiWarps = 16;
-constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kEpiChains = kKc / (kEpiWarps / 4);  // chains per epilogue warp
-constexpr int kThreads = 128 + kEpiThreads;     // 4 role warps + the epilogue warps
-static_assert(kEpiChains == 8, "the epilogue reads eta with 8-column TMEM loads");
+constexpr int kEpiChains = 8;                         // chains per epilogue warp (8-column TMEM loads)
+
+// The launch shape: KC chain columns (padded; K <= KC), S ring stages (even:
+// pass 2 takes them in pairs).
+template <int KC, int S>
+struct XKShape {
+  static_assert(KC == 16 || KC == 32, "chain columns");
+  static_assert(S >= 4 && S % 2 == 0, "ring stages");
+  static constexpr int kKc = KC;
+  static constexpr int kStages = S;
+  static constexpr uint32_t kBChunkBytes = 2 * KC * kCF * 2;      // 2 KC rows (hi chains, lo chains) x 128 B of B^T
+  static constexpr uint32_t kStageBytes = kXChunkBytes + kBChunkBytes;  // X chunk, then (pass 1) its B^T chunk
+  static constexpr uint32_t kZBlock = KC * 128;                  // KC chains x 64 rows x 2 B
+  static constexpr int kEpiWarps = 4 * (KC / kEpiChains);
+  static constexpr int kEpiThreads = 32 * kEpiWarps;
+  static constexpr int kThreads = 128 + kEpiThreads;  // 4 role warps + the epilogue warps
+  static constexpr size_t kSmem = 1024 + (size_t)S * kStageBytes + 4 * (size_t)kZBlock;
+};
+__host__ __device__ constexpr uint32_t bchunk_bytes(int kc) { return 2u * kc * kCF * 2; }
 
 // ---- tcgen05 helpers (shared-memory descriptors, 128-byte swizzle) ---------
 // Descriptor: start address >> 4 in bits 0-13, leading byte offset >> 4 in
@@ -98,6 +113,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+// 32 lanes x 16 consecutive columns of TMEM into 16 registers per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
 // 32 lanes x 8 consecutive columns of TMEM into 8 registers per thread.
@@ -183,36 +206,55 @@ __device__ __forceinline__ float tn_main_k(float ms, float u, float uc) {
   return ms - (lower ? w0 : -w0);
 }
 
+template <int S>
 struct XKShared {
-  uint64_t full[kXStages], empty[kXStages];
+  uint64_t full[S], empty[S];
   uint64_t eta_full[2], eta_empty[2], z_ready, zt_empty, acc_done;
   uint32_t tmem;
   int abort;
 };
 
 // Bounded wait; on timeout records the error and raises the CTA's abort flag.
-__device__ __forceinline__ bool xk_wait(uint64_t* bar, uint32_t parity, XKShared* sh, int* err) {
+__device__ __forceinline__ bool xk_wait(uint64_t* bar, uint32_t parity, int* abort, int* err) {
   if (mbar_test(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_test(bar, parity)) {
-    if (*(volatile int*)&sh->abort) return false;
+    if (*(volatile int*)abort) return false;
     if (global_ns() - t0 > 2000000000ull) {
       set_error(err, kErrTimeout);
-      *(volatile int*)&sh->abort = 1;
+      *(volatile int*)abort = 1;
       return false;
     }
   }
   return true;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// TMEM columns of a CTA: two eta' buffers of 2 KC columns, then KC per
+// 128-feature group, rounded up to a power of two (at least 32).
+__host__ __device__ constexpr uint32_t xk_tmem_cols(int kc, int nch) {
+  const uint32_t need = (uint32_t)(4 * kc + kc * (nch / 2));
+  uint32_t c = 32;
+  while (c < need) c <<= 1;
+  return c;
+}
+
+template <int KC, int S>
+__global__ void __launch_bounds__(XKShape<KC, S>::kThreads, 1)
     xstream_k_kernel(const __grid_constant__ CUtensorMap xmap, XKArgs a) {
+  using Sh = XKShape<KC, S>;
+  constexpr int kXStages = S;
+  constexpr uint32_t kStageBytes = Sh::kStageBytes;
+  constexpr uint32_t kBChunkBytes = Sh::kBChunkBytes;
+  constexpr uint32_t kZBlock = Sh::kZBlock;
+  constexpr int kEpiWarps = Sh::kEpiWarps;
+  constexpr int kEpiThreads = Sh::kEpiThreads;
   extern __shared__ unsigned char dyn[];
-  __shared__ XKShared sh;
+  __shared__ XKShared<S> sh;
+  int* const abort_flag = &sh.abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char* base = dyn + ((1024u - (smem_u32(dyn) & 1023u)) & 1023u);  // 1024-byte aligned
-  unsigned char* sX = base;                                   // kXStages x 24 KB
-  unsigned char* sZ = sX + (size_t)kXStages * kStageBytes;    // [hi/lo][rows 0-63 | 64-127] x 4 KB
+  unsigned char* sX = base;                                   // S stages
+  unsigned char* sZ = sX + (size_t)kXStages * kStageBytes;    // [hi/lo][rows 0-63 | 64-127] x KC x 128 B
   const int64_t ntiles = (a.N + kTR - 1) / kTR;
   const int64_t t0 = ntiles * blockIdx.x / gridDim.x;
   const int64_t t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
@@ -240,16 +282,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     sh.abort = 0;
     fence_mbar_init();
   }
+  const uint32_t tcols = xk_tmem_cols(KC, nch);
   if (warp == 2) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&sh.tmem)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem)),
+                 "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sh.tmem;
-  const uint32_t tm_eta = tmem;        // columns [64 b, 64 b + 64): eta' of buffer b (hi chains, lo chains)
-  const uint32_t tm_xtz = tmem + 128;  // columns [128 + 32 g, 160 + 32 g): X^T Z of feature group g
+  const uint32_t tm_eta = tmem;             // columns [2 KC b, 2 KC (b + 1)): eta' of buffer b (hi chains, lo chains)
+  const uint32_t tm_xtz = tmem + 4 * KC;    // columns [4 KC + KC g, +KC): X^T Z of feature group g
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
@@ -261,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto load_pass = [&](int64_t t, bool with_b) -> bool {
       for (int c = 0; c < nch; ++c, ++q) {
         const int s = q % kXStages;
-        if (!xk_wait(&sh.empty[s], ((q / kXStages) & 1) ^ 1, &sh, a.err)) return false;
+        if (!xk_wait(&sh.empty[s], ((q / kXStages) & 1) ^ 1, abort_flag, a.err)) return false;
         unsigned char* st = sX + (size_t)s * kStageBytes;
         mbar_arrive_expect_tx(&sh.full[s], with_b ? kStageBytes : kXChunkBytes);
         tma_load_2d(st, &xmap, c * kCF, (int)(t * kTR), &sh.full[s], with_b ? pol_keep : pol_done);
@@ -284,8 +328,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    const uint32_t id_eta = idesc_bf16(kTR, 2 * kKc, 0, 0);   // M 128 rows, N 64 (hi, lo), both K-major
-    const uint32_t id_xtz = idesc_bf16(128, kKc, 1, 0);       // M 128 features (MN-major A), N 32 chains
+    const uint32_t id_eta = idesc_bf16(kTR, 2 * KC, 0, 0);   // M 128 rows, N 2 KC (hi, lo), both K-major
+    const uint32_t id_xtz = idesc_bf16(128, KC, 1, 0);       // M 128 features (MN-major A), N KC chains
     // Descriptors are built once: moving a descriptor by b bytes adds b >> 4 to
     // its address field (shared addresses stay below 256 KB, so it cannot carry).
     // This warp shares its sub-partition with four epilogue warps, so every
@@ -305,16 +349,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     // pass 1 of tile number n (within this CTA) into eta buffer n % 2
     auto pass1 = [&](int n) -> bool {
       const int b = n & 1;
-      if (!xk_wait(&sh.eta_empty[b], ((n >> 1) & 1) ^ 1, &sh, a.err)) return false;  // the epilogue read it
+      if (!xk_wait(&sh.eta_empty[b], ((n >> 1) & 1) ^ 1, abort_flag, a.err)) return false;  // the epilogue read it
       tc_fence_after();
       for (int c = 0; c < nch; ++c, ++q) {
         const int s = q % kXStages;
-        if (!xk_wait(&sh.full[s], (q / kXStages) & 1, &sh, a.err)) return false;
+        if (!xk_wait(&sh.full[s], (q / kXStages) & 1, abort_flag, a.err)) return false;
         tc_fence_after();
         const uint64_t dx = dX0 + kStageStep * s, db = dB0 + kStageStep * s;
 #pragma unroll
         for (int kk = 0; kk < kCF / 16; ++kk)
-          mma_bf16(tm_eta + 64 * b, dx + 2 * kk, db + 2 * kk, id_eta, (c > 0 || kk > 0) ? 1 : 0);
+          mma_bf16(tm_eta + 2 * KC * b, dx + 2 * kk, db + 2 * kk, id_eta, (c > 0 || kk > 0) ? 1 : 0);
         mma_commit(&sh.empty[s]);
       }
       mma_commit(&sh.eta_full[b]);
@@ -326,12 +370,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       // pass 1 of the next tile runs while the epilogue draws z of this one
       if (it + 1 < ntl && !(ok = pass1(it + 1))) break;
       // pass 2: X^T Z once the epilogue has written Z^T of this tile
-      if (!(ok = xk_wait(&sh.z_ready, it & 1, &sh, a.err))) break;
+      if (!(ok = xk_wait(&sh.z_ready, it & 1, abort_flag, a.err))) break;
       tc_fence_after();
       for (int g = 0; g < ngrp && ok; ++g) {
         const int s0 = q % kXStages;  // even: chunks 2g and 2g+1 sit in stages s0, s0+1
-        if (!(ok = xk_wait(&sh.full[s0], (q / kXStages) & 1, &sh, a.err))) break;
-        if (!(ok = xk_wait(&sh.full[s0 + 1], ((q + 1) / kXStages) & 1, &sh, a.err))) break;
+        if (!(ok = xk_wait(&sh.full[s0], (q / kXStages) & 1, abort_flag, a.err))) break;
+        if (!(ok = xk_wait(&sh.full[s0 + 1], ((q + 1) / kXStages) & 1, abort_flag, a.err))) break;
         tc_fence_after();
         const uint64_t da = dA0 + kStageStep * s0;
         const int acc0 = it > 0 ? 1 : 0;
@@ -340,8 +384,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           // rows 16kk.., features of both stages (the second 64-feature atom of A
           // is the next stage's X chunk, kStageBytes further)
           const uint64_t ad = da + 128 * kk;
-          mma_bf16(tm_xtz + 32 * g, ad, dZ[0][kk], id_xtz, kk > 0 ? 1 : acc0);
-          mma_bf16(tm_xtz + 32 * g, ad, dZ[1][kk], id_xtz, 1);
+          mma_bf16(tm_xtz + KC * g, ad, dZ[0][kk], id_xtz, kk > 0 ? 1 : acc0);
+          mma_bf16(tm_xtz + KC * g, ad, dZ[1][kk], id_xtz, 1);
         }
         mma_commit(&sh.empty[s0]);
         mma_commit(&sh.empty[s0 + 1]);
@@ -365,11 +409,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int eb = it & 1;  // eta buffer of this tile
       const int yi_t = y_next;
       if (t + 1 < t1 && (t + 1) * kTR + er < a.N) y_next = a.y[(t + 1) * kTR + er];
-      if (!xk_wait(&sh.eta_full[eb], (it >> 1) & 1, &sh, a.err)) break;
+      if (!xk_wait(&sh.eta_full[eb], (it >> 1) & 1, abort_flag, a.err)) break;
       tc_fence_after();
       uint32_t hi[kEpiChains], lo[kEpiChains];
-      tmem_ld8(tm_eta + 64 * eb + lane_off + m0, hi);
-      tmem_ld8(tm_eta + 64 * eb + lane_off + 32 + m0, lo);
+      tmem_ld8(tm_eta + 2 * KC * eb + lane_off + m0, hi);
+      tmem_ld8(tm_eta + 2 * KC * eb + lane_off + KC + m0, lo);
       tmem_ld_wait();
       tc_fence_before();
       mbar_arrive(&sh.eta_empty[eb]);
@@ -377,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool active = i < a.N;
       const int yi = active ? yi_t : 1;
       // Z^T (both parts) for pass 2, once pass 2 of the previous tile is done with it
-      if (!xk_wait(&sh.zt_empty, (it & 1) ^ 1, &sh, a.err)) break;
+      if (!xk_wait(&sh.zt_empty, (it & 1) ^ 1, abort_flag, a.err)) break;
       const int katom = er >> 6, kr = er & 63;
       if (m0 >= a.K) {
         // every chain of this warp is padding (K < 32): zeros, no draws (the branch is warp-uniform)
@@ -420,17 +464,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
       mbar_arrive(&sh.z_ready);
     }
-    // the CTA's X^T Z partial: row = feature 128 g + er, 32 chains; groups split between the parts
-    if (xk_wait(&sh.acc_done, 0, &sh, a.err)) {
+    // the CTA's X^T Z partial: row = feature 128 g + er, KC chains; groups split between the parts
+    if (xk_wait(&sh.acc_done, 0, abort_flag, a.err)) {
       tc_fence_after();
       for (int g = part; g < ngrp; g += kEpiWarps / 4) {
-        uint32_t r[32];
-        tmem_ld32(tm_xtz + 32 * g + lane_off, r);
+        uint32_t r[KC];
+        if constexpr (KC == 32) tmem_ld32(tm_xtz + KC * g + lane_off, r);
+        else tmem_ld16(tm_xtz + KC * g + lane_off, r);
         tmem_ld_wait();
         const int f = 128 * g + er;
-        float* out = a.partials + ((size_t)blockIdx.x * a.fpad + f) * kKc;
+        float* out = a.partials + ((size_t)blockIdx.x * a.fpad + f) * KC;
 #pragma unroll
-        for (int m = 0; m < kKc; m += 4)
+        for (int m = 0; m < KC; m += 4)
           *reinterpret_cast<float4*>(out + m) = make_float4(__uint_as_float(r[m]), __uint_as_float(r[m + 1]),
                                                             __uint_as_float(r[m + 2]), __uint_as_float(r[m + 3]));
       }
@@ -440,42 +485,44 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 2) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
   }
 }
 
 // B^T in the shared-memory layout of pass 1: chunk c holds features 64c..64c+63
-// of 64 rows (rows 0..31: BF16 high parts of the K chains' beta (scaled to
-// the stored X), rows 32..63: the low parts beta - hi), 128-byte swizzled.
-__global__ void bsw_prep_kernel(const double* __restrict__ beta, int64_t beta_stride, int K, int p, int nch,
+// of 2 KC rows (rows 0..KC-1: BF16 high parts of the K chains' beta (scaled
+// to the stored X), rows KC..2KC-1: the low parts beta - hi), 128-byte swizzled.
+__global__ void bsw_prep_kernel(const double* __restrict__ beta, int64_t beta_stride, int K, int p, int nch, int kc,
                                 unsigned char* __restrict__ bsw) {
-  const int64_t n_el = (int64_t)nch * 64 * kCF;
+  const int rows = 2 * kc;
+  const int64_t n_el = (int64_t)nch * rows * kCF;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / (64 * kCF)), rem = (int)(e % (64 * kCF));
+    const int c = (int)(e / (rows * kCF)), rem = (int)(e % (rows * kCF));
     const int n = rem / kCF, k = rem % kCF;
-    const int m = n & 31, f = c * kCF + k;
+    const int m = n % kc, f = c * kCF + k;
     float v = 0.0f;
     if (m < K && f < p) {
       const double b = beta[(int64_t)m * beta_stride + f];
       const __nv_bfloat16 h = __float2bfloat16_rn((float)b);
-      v = n < 32 ? __bfloat162float(h) : (float)(b - (double)__bfloat162float(h));
+      v = n < kc ? __bfloat162float(h) : (float)(b - (double)__bfloat162float(h));
     }
-    *reinterpret_cast<__nv_bfloat16*>(bsw + (size_t)c * kBChunkBytes + sw128_off(n, k)) = __float2bfloat16_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(bsw + (size_t)c * bchunk_bytes(kc) + sw128_off(n, k)) = __float2bfloat16_rn(v);
   }
 }
 
 // X^T z of chain m, feature j: fixed-order FP64 sum over the CTAs' partials.
-// Thread (j, m): lanes run over the 32 chains of one feature, so each CTA's
-// partial row is read as one 128-byte line; four accumulators (CTA index
-// mod 4) are added in a fixed order at the end.
+// Thread (j, m): consecutive lanes run over the KC chains of one feature, so
+// each CTA's partial row is read as whole lines; four accumulators (CTA
+// index mod 4) are added in a fixed order at the end.
+template <int KC>
 __global__ void reduce_k_kernel(const float* __restrict__ part, int grid, int fpad, int p, int K,
                                 double* __restrict__ xtz, int64_t xtz_stride) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = e / kKc, m = e % kKc;
+  const int j = e / KC, m = e % KC;
   if (j >= p) return;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  const float* col = part + (size_t)j * kKc + m;
-  const size_t cs = (size_t)fpad * kKc;
+  const float* col = part + (size_t)j * KC + m;
+  const size_t cs = (size_t)fpad * KC;
   int c = 0;
   for (; c + 3 < grid; c += 4) {
     s0 += (double)__ldg(col + (size_t)c * cs);
@@ -494,21 +541,49 @@ int xstream_k_chunks(int p) {
   return (nch + 1) & ~1;
 }
 
-size_t xstream_k_smem_bytes(int p) {
-  (void)p;
-  return 1024 + (size_t)kXStages * kStageBytes + 4 * (size_t)kZBlock;
+namespace {
+// f(std::integral_constant<int, KC>, std::integral_constant<int, S>) for the
+// instantiated shapes; false for any other.
+template <class F>
+bool with_shape(int kc, int stages, F&& f) {
+#define HS_XK_SHAPE(KC, S)                                                      \
+  if (kc == KC && stages == S) {                                                \
+    f(std::integral_constant<int, KC>{}, std::integral_constant<int, S>{});     \
+    return true;                                                                \
+  }
+  HS_XK_SHAPE(16, 4) HS_XK_SHAPE(16, 6) HS_XK_SHAPE(16, 8)
+  HS_XK_SHAPE(32, 4) HS_XK_SHAPE(32, 6) HS_XK_SHAPE(32, 8)
+#undef HS_XK_SHAPE
+  return false;
+}
+}  // namespace
+
+size_t xstream_k_smem_bytes(int kc, int stages) {
+  size_t b = 0;
+  with_shape(kc, stages, [&](auto KC, auto S) { b = XKShape<decltype(KC)::value, decltype(S)::value>::kSmem; });
+  return b;
 }
 
-bool xstream_k_supported(int p) {
+bool xstream_k_supported(int p, int kc, int stages) {
   const int nch = xstream_k_chunks(p);
-  // TMEM: two eta' buffers of 64 columns + 32 per 128-feature group
-  return p >= 1 && 128 + 32 * (nch / 2) <= 512 && xstream_k_smem_bytes(p) <= 227 * 1024;
+  const size_t smem = xstream_k_smem_bytes(kc, stages);
+  // TMEM: two eta' buffers of 2 KC columns + KC per 128-feature group
+  return p >= 1 && smem > 0 && 4 * kc + kc * (nch / 2) <= 512 && smem <= 227 * 1024;
 }
 
-cudaError_t xstream_k_prepare(int p) {
-  return cudaFuncSetAttribute((const void*)xstream_k_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)xstream_k_smem_bytes(p));
+int xstream_k_default_kc(int K) { return K <= 16 ? 16 : 32; }
+
+cudaError_t xstream_k_prepare(int kc, int stages) {
+  cudaError_t e = cudaErrorInvalidValue;
+  with_shape(kc, stages, [&](auto KC, auto S) {
+    constexpr int c = decltype(KC)::value, st = decltype(S)::value;
+    e = cudaFuncSetAttribute((const void*)xstream_k_kernel<c, st>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)XKShape<c, st>::kSmem);
+  });
+  return e;
 }
+
+size_t xstream_k_bsw_bytes(int p, int kc) { return (size_t)xstream_k_chunks(p) * bchunk_bytes(kc); }
 
 // The tensor map of X (ld columns, N rows, BF16, row stride ld * 2 bytes):
 // boxes of 64 x 128 with 128-byte swizzle; reads outside X return zeros.
@@ -543,23 +618,36 @@ int xstream_k_grid(int64_t N, int num_sms) {
   return (int)(g < 1 ? 1 : g);
 }
 
-size_t xstream_k_partial_floats(int p, int grid) {
-  return (size_t)grid * (size_t)(xstream_k_chunks(p) * kCF) * kKc;
+int64_t xstream_k_tiles(int64_t N) { return (N + kTR - 1) / kTR; }
+
+size_t xstream_k_partial_floats(int p, int grid, int kc) {
+  return (size_t)grid * (size_t)(xstream_k_chunks(p) * kCF) * kc;
 }
 
 cudaError_t xstream_k_enqueue(const void* map, const XKArgs& a, const double* beta, int64_t beta_stride,
                               unsigned char* bsw, int grid, cudaStream_t s) {
-  bsw_prep_kernel<<<64, 256, 0, s>>>(beta, beta_stride, a.K, a.p, a.nch, bsw);
+  if (a.K > a.kc) return cudaErrorInvalidValue;
+  bsw_prep_kernel<<<64, 256, 0, s>>>(beta, beta_stride, a.K, a.p, a.nch, a.kc, bsw);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap m;
   memcpy(&m, map, sizeof(m));
-  xstream_k_kernel<<<grid, kThreads, xstream_k_smem_bytes(a.p), s>>>(m, a);
-  return cudaGetLastError();
+  e = cudaErrorInvalidValue;
+  with_shape(a.kc, a.stages, [&](auto KC, auto S) {
+    using Sh = XKShape<decltype(KC)::value, decltype(S)::value>;
+    xstream_k_kernel<Sh::kKc, Sh::kStages><<<grid, Sh::kThreads, Sh::kSmem, s>>>(m, a);
+    e = cudaGetLastError();
+  });
+  return e;
 }
 
 cudaError_t xstream_k_reduce(const XKArgs& a, int grid, double* xtz, int64_t xtz_stride, cudaStream_t s) {
-  reduce_k_kernel<<<(a.p * kKc + 255) / 256, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, xtz, xtz_stride);
+  if (a.kc == 16)
+    reduce_k_kernel<16><<<(a.p * 16 + 255) / 256, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, xtz, xtz_stride);
+  else if (a.kc == 32)
+    reduce_k_kernel<32><<<(a.p * 32 + 255) / 256, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, xtz, xtz_stride);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

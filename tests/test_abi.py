@@ -128,8 +128,6 @@ def test_tn_sample_rejects_bad_arguments_on_host(lib):
 @pytest.mark.parametrize("field,value,dtype,p,status", [
     ("num_chains", 33, "bf16", 64, -1),      # more than 32 chains
     ("num_chains", -1, "bf16", 64, -1),
-    ("num_chains", 4, "f32", 64, -8),        # the batched form needs BF16 X
-    ("num_chains", 4, "bf16", 1537, -8),     # and p <= 1536 (TMEM columns)
     ("beta_solve", 3, "f32", 64, -1),        # unknown beta form
     ("chol_sched", 4, "f32", 64, -1),        # unknown schedule
 ])
@@ -143,3 +141,27 @@ def test_init_rejects_bad_config_on_host(lib, field, value, dtype, p, status):
     y = np.zeros(4, dtype=np.uint8)
     assert not lib.hs_probit_init_ex(ctypes.byref(cfg), X.ctypes.data, y.ctypes.data, 4, p, 0)
     assert lib.hs_probit_last_error() == status
+
+
+def test_batch_and_launch_shape_reject_bad_arguments_on_host(lib):
+    import paper_1608_04329_gb300 as pkg
+    cfg = pkg._Config()
+    lib.hs_probit_config_default(ctypes.byref(cfg))
+    probs = (pkg._Problem * 2)()
+    X = np.zeros((4, 3), dtype=np.float32)
+    y = np.zeros(4, dtype=np.uint8)
+    probs[0] = pkg._Problem(X.ctypes.data, y.ctypes.data, 4, 3, None)
+    probs[1] = pkg._Problem(X.ctypes.data, y.ctypes.data, 1, 3, None)  # N < 2
+    for args in ((None, 1, probs), (ctypes.byref(cfg), 0, probs), (ctypes.byref(cfg), 1, None),
+                 (ctypes.byref(cfg), 2, probs)):
+        assert not lib.hs_probit_batch_init(*args, 0)
+        assert lib.hs_probit_last_error() == -1
+    assert lib.hs_probit_batch_size(None) == -1
+    assert lib.hs_probit_batch_problem(None, 0) is None
+    assert lib.hs_probit_batch_sweep(None, 1) == -1
+    assert lib.hs_probit_batch_tune(None, 1, None) == -1
+    assert lib.hs_probit_batch_tune_trials(None, None, 0) == -1
+    lib.hs_probit_batch_free(None)
+    ls = pkg._LaunchShape()
+    assert lib.hs_probit_get_launch_shape(None, ctypes.byref(ls)) == -1
+    assert lib.hs_probit_set_launch_shape(None, ctypes.byref(ls)) == -1

@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 import oracle
-from tests.gpu_common import lib_pkg, problem, random_state, x_f64
+from tests.gpu_common import assert_transition_close, lib_pkg, problem, random_state, x_f64
 
 
 def row_abs_dot(X, b, chunk=65536):
@@ -74,7 +74,8 @@ def _batched_transitions(pkg, d, states, seed, chain0=0, **kw):
     return out
 
 
-@pytest.mark.parametrize("N,p,K", [(3001, 200, 5), (1000, 64, 2), (20003, 1000, 32), (257, 1, 3), (4099, 1100, 8)])
+@pytest.mark.parametrize("N,p,K", [(3001, 200, 5), (1000, 64, 2), (20003, 1000, 32), (257, 1, 3), (4099, 1100, 8),
+                                   (9001, 2000, 4), (5003, 3584, 16)])
 def test_batched_chains_match_oracle(pkg, N, p, K):
     d = problem(N, p, min(5, p), "bf16", seed=N % 97)
     X = x_f64(d)
@@ -126,10 +127,37 @@ def test_batched_draw_rings_per_chain(pkg):
     s.close()
 
 
-def test_batched_needs_bf16(pkg):
-    d = problem(1000, 20, 2, "f32", seed=1)
-    with pytest.raises(pkg.HSProbitError):
-        pkg.HSProbit(d["X"], d["y"], num_chains=4)
+@pytest.mark.parametrize("dt,N,p,K,tol", [("f32", 3001, 200, 3, 1e-4), ("f64", 2001, 130, 2, 1e-10),
+                                           ("f32", 1000, 1, 2, 1e-4)])
+def test_chains_without_tensor_core_xstream_match_oracle(pkg, dt, N, p, K, tol):
+    """K chains on F32 or F64 X: one pass of the one-chain X-stream per chain,
+    the rest batched; each chain reproduces the oracle's transition at the
+    one-chain path's tolerance for that X type."""
+    d = problem(N, p, min(5, p), dt, seed=N % 89)
+    X = x_f64(d)
+    G = oracle.gram(X)
+    states = [random_state(p, k=3, seed=300 + m) for m in range(K)]
+    got = _batched_transitions(pkg, d, states, seed=77, chain0=2)
+    for m, st in enumerate(states):
+        ref = oracle.sweep_once(st.copy(), X, d["y"], G, 77, chain=2 + m, keep=True)
+        assert_transition_close(got[m], ref, tol)
+
+
+def test_bf16_chains_past_the_tensor_core_tmem_budget_match_oracle(pkg):
+    """K = 20 chains need 32 chain columns, whose TMEM budget ends at p = 1536:
+    p = 1600 takes the per-chain X-stream, still at the BF16 bound."""
+    N, p, K = 3001, 1600, 20
+    d = problem(N, p, 5, "bf16", seed=4)
+    X = x_f64(d)
+    G = oracle.gram(X)
+    states = [random_state(p, k=2, seed=400 + m) for m in range(K)]
+    s = pkg.HSProbit(d["X"], d["y"], seed=1, num_chains=K)
+    assert s.launch_shape()["xk_chains"] == 0  # no tensor-core X-stream
+    s.close()
+    got = _batched_transitions(pkg, d, states, seed=13)
+    for m, st in enumerate(states):
+        ref = oracle.sweep_once(st.copy(), X, d["y"], G, 13, chain=m, keep=True)
+        assert_transition_close(got[m], ref, 1e-4)
 
 
 def test_batched_long_run_moments_match_oracle_within_mc_error(pkg):
