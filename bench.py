@@ -180,6 +180,45 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _alu_peak(torch, local):
+    """FP32-pair FMAs per second the CUDA cores can issue: SMs x 128 FP32 lanes x
+    max SM clock / 12 FP32 instructions per pair-FMA."""
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz, src = float(json.load(f)["sm_max_mhz"]), "measured"
+    except (OSError, KeyError, ValueError):
+        mhz, src = 2070.0, "nominal"
+    return sms * 128 * mhz * 1e6 / 12.0, f"SMs x 128 FP32 lanes x {src} max SM clock / 12 FP32 instructions per pair-FMA"
+
+
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1e12, "measured"
+    except (OSError, KeyError, ValueError):
+        return 1.9e15, "fallback"
+
+
+def factor_work(p: int, tensor: bool = True):
+    """Algorithmic work of one chain's factorization of the p x p precision
+    matrix (P = 32 ceil(p / 32) padded rows, which are skipped).  Block-column
+    form (blocks of 128 columns): the CUDA cores do the updates inside each
+    block column in FP32 pairs; the tensor cores apply the rank-128 updates of
+    the rest as 21 BF16 digit-pair products per multiply-add.  Returns
+    (CUDA-core pair-FMAs, tensor-core flops)."""
+    if not tensor:
+        return p ** 3 / 6.0, 0.0
+    alu, mac = 0.0, 0.0
+    for c0 in range(0, p, 128):
+        c1 = min(c0 + 128, p)
+        for j in range(c0, c1):
+            alu += (p - j) * (j - c0)          # column j's updates from the block's earlier columns
+        r = p - c1
+        mac += r * (r + 1) / 2.0 * (c1 - c0)   # trailing lower triangle, rank c1 - c0
+    return alu, 2.0 * 21.0 * mac
+
+
 def _traffic(workload: str, record: str = "xstream_traffic.json", sources=XSTREAM_SOURCES):
     """DRAM bytes per X-stream launch from the committed ncu summary, or None
     when the kernel sources changed since the counters were taken."""
@@ -311,12 +350,17 @@ def run_reference(args, wl, dist, rank):
     return 0
 
 
-def run_k_chains(args, wk, pkg, torch, dist, ws, rank, local, chol, one_chain_value):
-    """The batched form: K chains on BF16 X; chain-sweeps/s and the X-stream roofline."""
+def run_k_chains(args, wk, pkg, torch, dist, ws, rank, local, chol, one_chain_value, dk=None, K=None):
+    """K chains on one X: chain-sweeps/s, the X-stream roofline and the
+    factorization's floors.  BF16 X takes the tensor-core X-stream (one pass
+    for every chain); other types one pass per chain."""
     peak, peak_kind = _peaks()
-    dk = make_data(wk)
+    K = K or args.k_chains
+    if dk is None:
+        dk = make_data(wk)
     sk = pkg.HSProbit(dk["X"], dk["y"], seed=0, chain=32 * rank, device=local, use_graph=bool(args.graph),
-                      chol_arith=chol, num_chains=args.k_chains, ring_size=max(args.k_steps + 3, 16))
+                      chol_arith=chol, num_chains=K, ring_size=max(args.k_steps + 3, 16), scales=dk["scales"])
+    shape = sk.launch_shape()
     streamk = torch.cuda.ExternalStream(sk.stream(), device=local)
     sk.sweep(3)
     sk.set_profiling(bool(args.profile))
@@ -338,35 +382,51 @@ def run_k_chains(args, wk, pkg, torch, dist, ws, rank, local, chol, one_chain_va
     sk.set_profiling(False)
     sk.close()
     kx_ms, kx_n = kgroups["xstream"]
-    kbytes = wk["N"] * (wk["p"] * 2 + 1)
+    eb = {"f64": 8, "f32": 4, "bf16": 2, "fp8": 1}[wk["dt"]]
+    tensor_xs = shape["xk_chains"] > 0
+    # algorithmic bytes: X once for all chains on the tensor cores, else once per chain
+    kbytes = (1 if tensor_xs else K) * wk["N"] * (wk["p"] * eb + 1)
     kroof = None
     if kx_n > 0:
         kavg = kx_ms / kx_n
         kach = kbytes / (kavg / 1e3) / 1e9
+        if tensor_xs:
+            rec = _traffic("c2" if wk["N"] == WORKLOADS["c2"]["N"] else "c2s", "xstream_k_traffic.json",
+                           XSTREAM_K_SOURCES)
+            kern = f"xstream_k<{shape['xk_chains']}, {shape['xk_stages']}> (B prep + tensor-core X-stream)"
+        else:
+            rec = _traffic(args.workload) if wk is WORKLOADS.get(args.workload) else None
+            rec = K * rec if rec else None
+            kern = f"xstream ({K} one-chain passes)"
         kroof = {"bound": "hbm", "achieved": kach, "peak": peak, "unit": "GB/s", "frac": kach / peak,
-                 "traffic": _traffic("c2" if wk["N"] == WORKLOADS["c2"]["N"] else "c2s", "xstream_k_traffic.json",
-                                     XSTREAM_K_SOURCES), "peak_source": peak_kind,
-                 "kernel": "xstream_k (B prep + tensor-core X-stream)", "avg_launch_ms": kavg,
-                 "tensor_tflops": 4.0 * wk["N"] * 1024 * 2 * 32 / (kavg / 1e3) / 1e12}
-    # the K factorizations on the CUDA cores: FP32-pair FMAs against the FP32 issue bound
+                 "traffic": rec, "peak_source": peak_kind, "kernel": kern, "avg_launch_ms": kavg}
+        if tensor_xs:
+            kc = shape["xk_chains"]
+            fpad = (wk["p"] + 127) // 128 * 128
+            kroof["tensor_tflops"] = 4.0 * wk["N"] * fpad * 2 * kc / (kavg / 1e3) / 1e12
+    # the K factorizations: block columns of FP32-pair panel work on the CUDA
+    # cores and rank-128 digit products on the tensor cores, chained block
+    # column after block column; the floors are each unit's share at its peak
     kc_ms, kc_n = kgroups["cholesky"]
     kchol = None
     if kc_n > 0:
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        try:
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-                mhz, mhz_src = float(json.load(f)["sm_max_mhz"]), "measured"
-        except (OSError, KeyError, ValueError):
-            mhz, mhz_src = 2070.0, "nominal"
-        alu_peak = sms * 128 * mhz * 1e6 / 12.0 / 1e12
+        alu_peak, alu_src = _alu_peak(torch, local)
+        tc_peak, tc_src = _bf16_peak()
+        alu, tflop = factor_work(wk["p"])
         cavg = kc_ms / kc_n
-        cach = args.k_chains * float(wk["p"]) ** 3 / 6.0 / (cavg / 1e3) / 1e12
-        kchol = {"bound": "alu", "achieved": cach, "peak": alu_peak, "unit": "Tpair-FMA/s", "frac": cach / alu_peak,
-                 "traffic": None, "kernel": "chol_persistent_kernel (K chains, factor only)", "avg_launch_ms": cavg,
-                 "work": "K p^3/6 FP32-pair FMAs per sweep",
-                 "peak_source": f"SMs x 128 FP32 lanes x {mhz_src} max SM clock / 12 FP32 instructions per pair-FMA"}
-    kvalue = ws * args.k_chains * args.k_steps / (kms / 1e3)
-    return {"value": kvalue, "unit": "chain-sweeps/s", "K": args.k_chains, "x_dtype": "bf16",
+        t_alu = K * alu / alu_peak * 1e3
+        t_tc = K * tflop / tc_peak * 1e3
+        kchol = {"bound": "latency", "achieved_ms": cavg, "alu_floor_ms": t_alu, "tensor_floor_ms": t_tc,
+                 "frac": max(t_alu, t_tc) / cavg, "traffic": None,
+                 "kernel": "chol_persistent_kernel + chol_trail_kernel per block column (K chains, factor only)",
+                 "work": {"cuda_core_pair_fma": K * alu, "tensor_flop": K * tflop,
+                          "all_pair_fma_equivalent": K * wk["p"] ** 3 / 6.0},
+                 "alu_peak_pair_fma_s": alu_peak, "alu_peak_source": alu_src,
+                 "tensor_peak_flop_s": tc_peak, "tensor_peak_source": f"{tc_src} cuBLAS bf16",
+                 "note": "the block columns run one after another (each waits for its diagonal chain), "
+                         "so the sum of the floors is not reachable; frac = the larger floor / achieved"}
+    kvalue = ws * K * args.k_steps / (kms / 1e3)
+    return {"value": kvalue, "unit": "chain-sweeps/s", "K": K, "x_dtype": wk["dt"], "launch_shape": shape,
             "steps": args.k_steps, "warmup": 3, "ms_per_sweep": kms / args.k_steps,
             "vs_one_chain_fp32": (kvalue / one_chain_value) if one_chain_value else None,
             "kernel_ms_per_sweep": {g: (v[0] / max(v[1], 1)) for g, v in kgroups.items()},
@@ -432,31 +492,31 @@ def run_uneven_batch(args, pkg, torch, dist, ws, rank, local, chol):
     launches = sum(b.problem(m).launches_per_sweep() for m in range(len(ds)))
     b.close()
     sweeps_s = ws * args.c3_steps / (ms / 1e3)
-    # lower bounds of a sweep: X read once (HBM), and the K factorizations as
-    # FP32-pair FMAs on the CUDA cores (K p^3 / 6 each) at the ALU issue bound
+    # floors of a sweep: X read once (HBM); the K factorizations' panel work on
+    # the CUDA cores and trailing digit products on the tensor cores
     t_hbm = (x_bytes + y_bytes) / (peak * 1e9) * 1e3
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            mhz, mhz_src = float(json.load(f)["sm_max_mhz"]), "measured"
-    except (OSError, KeyError, ValueError):
-        mhz, mhz_src = 2070.0, "nominal"
-    alu_peak = sms * 128 * mhz * 1e6 / 12.0  # pair-FMAs/s
-    pair_fmas = sum(u["K"] * float(p) ** 3 / 6.0 for _, p in sizes)
+    alu_peak, alu_src = _alu_peak(torch, local)
+    tc_peak, tc_src = _bf16_peak()
+    work = [factor_work(p) for _, p in sizes]
+    pair_fmas = u["K"] * sum(a for a, _ in work)
+    tflop = u["K"] * sum(t for _, t in work)
     t_alu = pair_fmas / alu_peak * 1e3
-    bound = max(t_hbm, t_alu)
+    t_tc = tflop / tc_peak * 1e3
+    bound = max(t_hbm, t_alu, t_tc)
     return {"value": sweeps_s * u["n"] * u["K"], "unit": "chain-sweeps/s", "batch_sweeps_per_s": sweeps_s,
             "problems": u["n"], "K": u["K"], "steps": args.c3_steps, "warmup": 6, "ms_per_sweep": ms_sweep,
             "workload": u["name"],
             "realised": {"sum_x_bytes": x_bytes, "sum_4p3_over_3_flop": sum(4.0 * p ** 3 / 3.0 for _, p in sizes),
-                         "sum_K_p3_over_6_pair_fma": pair_fmas, "N_min_max": [min(n for n, _ in sizes),
+                         "sum_K_p3_over_6": u["K"] * sum(float(p) ** 3 / 6.0 for _, p in sizes), "N_min_max": [min(n for n, _ in sizes),
                                                                                 max(n for n, _ in sizes)],
                          "p_min_max": [min(p for _, p in sizes), max(p for _, p in sizes)]},
-            "roofline": {"bound": "hbm" if t_hbm >= t_alu else "alu", "achieved_ms": ms_sweep,
-                         "bound_ms": bound, "frac": bound / ms_sweep, "hbm_ms": t_hbm, "alu_ms": t_alu,
-                         "hbm_peak_gbs": peak, "peak_source": peak_kind,
-                         "alu_peak": f"SMs x 128 FP32 lanes x {mhz_src} max SM clock / 12 FP32 instructions "
-                                     "per pair-FMA"},
+            "roofline": {"bound": ("hbm", "alu", "tensor")[[t_hbm, t_alu, t_tc].index(bound)],
+                         "achieved_ms": ms_sweep, "bound_ms": bound, "frac": bound / ms_sweep, "hbm_ms": t_hbm,
+                         "alu_ms": t_alu, "tensor_ms": t_tc, "hbm_peak_gbs": peak, "peak_source": peak_kind,
+                         "cuda_core_pair_fma": pair_fmas, "tensor_flop": tflop, "alu_peak": alu_src,
+                         "tensor_peak": f"{tc_src} cuBLAS bf16 {tc_peak / 1e12:.0f} TFLOP/s",
+                         "note": "floors of the three units; each problem's block columns run one after "
+                                 "another, so latency, not any floor, is what the sweep meets"},
             "tuner": {"best_ms_per_sweep": best, "trials": trials, "tune_s": t_tune,
                       "xk_chains": sorted({sh["xk_chains"] for sh in shapes}),
                       "xk_stages": sorted({sh["xk_stages"] for sh in shapes})},
@@ -518,6 +578,7 @@ def main(argv=None):
     ap.add_argument("--k-steps", type=int, default=20)
     ap.add_argument("--no-tn", action="store_true", help="skip the standalone sampler comparison")
     ap.add_argument("--no-c3", action="store_true", help="skip the uneven multi-problem batch")
+    ap.add_argument("--c4-chains", type=int, default=8, help="chains of the large correlated workload's K-chain leg")
     ap.add_argument("--c3-steps", type=int, default=50, help="timed sweeps of the uneven batch")
     ap.add_argument("--traffic-from", default=None, metavar="CSV",
                     help="write profiles/<kernel>_traffic.json from an ncu CSV of --workload c1s or c2s and exit")
@@ -621,7 +682,10 @@ def main(argv=None):
 
     # ---- K chains on BF16 X (tensor-core X-stream), same N and p ----
     kch = None
-    if args.k_chains > 1:
+    if wl is WORKLOADS["c4"] and args.c4_chains > 1:
+        # the large correlated workload's own K chains on its FP8 X
+        kch = run_k_chains(args, wl, pkg, torch, dist, ws, rank, local, chol, value, dk=d, K=args.c4_chains)
+    elif args.k_chains > 1:
         kch = run_k_chains(args, WORKLOADS["c2"], pkg, torch, dist, ws, rank, local, chol, value)
 
     c3 = None

@@ -359,10 +359,15 @@ int hs_probit_debug_xtz_chain(hs_probit* h, int chain, double* xtz_out);
 typedef struct hs_launch_shape {
   int32_t xk_chains;    /* chain columns of a tensor-core X-stream tile: 16 (K <= 16) or 32 */
   int32_t xk_stages;    /* shared-memory ring stages of that X-stream: 4, 6 or 8 */
-  int32_t xstream_ctas; /* CTAs of the X-stream: 1 .. the value the handle started with */
+  int32_t xstream_ctas; /* CTAs of the X-stream: 1 .. the value the handle started with (for the
+                           tensor-core X-stream, x 32 / xk_chains, at most one per 128 rows) */
   int32_t chol_ctas;    /* blocks of each factorization launch: K + 1 .. the starting value */
   int32_t trail_ctas;   /* CTAs of the tensor-core trailing updates: 1 .. the starting value */
-  int32_t reserved[3];  /* must be 0 */
+  int32_t xk_ctas_per_sm; /* CTAs per SM the tensor-core X-stream is built for: 1, or 2 with 16
+                             chain columns, 4 stages and p <= 1536 (half the TMEM each) */
+  int32_t overlap;      /* K chains: 1 = the factorization runs beside the X-stream, 2 = after it
+                           (the starting value); one chain always overlaps */
+  int32_t reserved[1];  /* must be 0 */
 } hs_launch_shape;
 
 /* Current shapes (fields that do not apply to the handle read 0). */
@@ -408,20 +413,24 @@ hs_probit* hs_probit_batch_problem(hs_probit_batch* b, int32_t m);
  * are valid). */
 int hs_probit_batch_sweep(hs_probit_batch* b, int64_t n_iter);
 /* The autotuner: times trial launch shapes over `sweeps` sweeps each and
- * keeps the fastest.  Candidates: for each problem, X-stream CTAs and
- * factorization blocks in proportion to its share of the batch's X bytes and
- * factorization flops, at several oversubscription factors, and the
- * tensor-core X-stream's chain columns and ring stages.  Every problem's
+ * keeps the fastest.  Candidates: for each problem, X-stream CTAs, trailing-
+ * update CTAs and factorization blocks in proportion to its share of the
+ * batch's X bytes and factorization work, at four oversubscription factors;
+ * then the factorization blocks' factor alone (1/8 .. 2 of that); then the
+ * tensor-core X-stream's tile (chain columns, ring stages, CTAs per SM); then
+ * the K chains' factorization beside the X-stream instead of after it.  Every problem's
  * state is saved first and restored after, so tuning leaves the chains where
  * they were.  *best_ms receives the best time per sweep (may be NULL). */
 int hs_probit_batch_tune(hs_probit_batch* b, int32_t sweeps, double* best_ms);
 /* One trial of the last hs_probit_batch_tune call. */
 typedef struct hs_tune_trial {
   double ms_per_sweep;  /* measured time per batch sweep */
-  int32_t oversub_x4;   /* 4 x the oversubscription factor of the proportional shares */
+  double oversub;       /* oversubscription factor of the X-stream and trailing-update shares */
+  double chol_oversub;  /* factor of the factorization blocks' shares */
   int32_t xk_chains;    /* tensor-core X-stream chain columns tried (0: unchanged) */
   int32_t xk_stages;    /* its ring stages tried (0: unchanged) */
-  int32_t reserved;
+  int32_t xk_ctas_per_sm; /* its CTAs per SM tried (0: unchanged) */
+  int32_t overlap;      /* launch-shape overlap tried (1 beside, 2 after) */
 } hs_tune_trial;
 /* Copies up to max trials into out (host); returns the number of trials. */
 int32_t hs_probit_batch_tune_trials(const hs_probit_batch* b, hs_tune_trial* out, int32_t max);

@@ -67,7 +67,8 @@ class _StateView(ctypes.Structure):
 
 class _LaunchShape(ctypes.Structure):
     _fields_ = [("xk_chains", ctypes.c_int32), ("xk_stages", ctypes.c_int32), ("xstream_ctas", ctypes.c_int32),
-                ("chol_ctas", ctypes.c_int32), ("trail_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("chol_ctas", ctypes.c_int32), ("trail_ctas", ctypes.c_int32), ("xk_ctas_per_sm", ctypes.c_int32),
+                ("overlap", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class _Problem(ctypes.Structure):
@@ -76,8 +77,9 @@ class _Problem(ctypes.Structure):
 
 
 class _TuneTrial(ctypes.Structure):
-    _fields_ = [("ms_per_sweep", ctypes.c_double), ("oversub_x4", ctypes.c_int32), ("xk_chains", ctypes.c_int32),
-                ("xk_stages", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+    _fields_ = [("ms_per_sweep", ctypes.c_double), ("oversub", ctypes.c_double), ("chol_oversub", ctypes.c_double),
+                ("xk_chains", ctypes.c_int32), ("xk_stages", ctypes.c_int32), ("xk_ctas_per_sm", ctypes.c_int32),
+                ("overlap", ctypes.c_int32)]
 
 
 _LIB = None
@@ -362,7 +364,8 @@ class HSProbit:
         st = self._lib.hs_probit_get_launch_shape(self._h, ctypes.byref(ls))
         if st != 0:
             raise HSProbitError(st, "hs_probit_get_launch_shape")
-        return {f: int(getattr(ls, f)) for f in ("xk_chains", "xk_stages", "xstream_ctas", "chol_ctas", "trail_ctas")}
+        return {f: int(getattr(ls, f)) for f in ("xk_chains", "xk_stages", "xstream_ctas", "chol_ctas", "trail_ctas",
+                                                 "xk_ctas_per_sm", "overlap")}
 
     def set_launch_shape(self, **sizes) -> None:
         """Change launch sizes (keyword per field; omitted fields stay)."""
@@ -501,7 +504,8 @@ class HSProbitBatch:
         n = int(self._lib.hs_probit_batch_tune_trials(self._b, None, 0))
         arr = (_TuneTrial * max(n, 1))()
         self._lib.hs_probit_batch_tune_trials(self._b, arr, n)
-        return [{"ms_per_sweep": t.ms_per_sweep, "oversub": t.oversub_x4 / 4.0, "xk_chains": t.xk_chains,
+        return [{"ms_per_sweep": t.ms_per_sweep, "oversub": t.oversub, "chol_oversub": t.chol_oversub,
+                 "xk_chains": t.xk_chains, "xk_ctas_per_sm": t.xk_ctas_per_sm, "overlap": t.overlap,
                  "xk_stages": t.xk_stages} for t in arr[:n]]
 
     def close(self) -> None:

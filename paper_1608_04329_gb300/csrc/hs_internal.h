@@ -62,6 +62,7 @@ struct XKArgs {
   int K;                  // chains (<= kc)
   int kc;                 // chain columns of the launch shape (16 or 32)
   int stages;             // ring stages of the launch shape (4, 6 or 8)
+  int per_sm;             // CTAs per SM of the launch shape (1, or 2 for kc 16 with 4 stages)
   const void* bsw;        // nch x (kc x 256 B): B^T (BF16 high and low parts), swizzled for the MMA
   float* partials;        // grid x fpad x kc FP32 (written)
   double* z_out;          // K x N (chain-major), or nullptr
@@ -72,11 +73,12 @@ struct XKArgs {
 };
 int xstream_k_chunks(int p);
 // Launch shapes: kc chain columns (16 or 32), stages ring stages (4, 6 or 8).
-bool xstream_k_supported(int p, int kc, int stages);
+// per_sm: CTAs per SM the kernel is compiled for (2 only with kc 16, 4 stages).
+bool xstream_k_supported(int p, int kc, int stages, int per_sm);
 int xstream_k_default_kc(int K);
 constexpr int kXkDefaultStages = 8;
 size_t xstream_k_smem_bytes(int kc, int stages);
-cudaError_t xstream_k_prepare(int kc, int stages);
+cudaError_t xstream_k_prepare(int kc, int stages, int per_sm);
 int xstream_k_grid(int64_t N, int num_sms);
 int64_t xstream_k_tiles(int64_t N);
 size_t xstream_k_partial_floats(int p, int grid, int kc);

@@ -96,7 +96,8 @@ struct hs_probit {
   int64_t* k_scratch = nullptr;             // K: commits of chains 0..K-2 record the sweep here
   int kgrid = 0;                            // batched X-stream CTAs
   bool xk = false;                          // K chains on the tensor-core X-stream (else one pass per chain)
-  int xk_kc = 32, xk_stages = 8;            // its launch shape (chain columns, ring stages)
+  int xk_kc = 32, xk_stages = 8, xk_per_sm = 1;  // its launch shape (chain columns, ring stages, CTAs per SM)
+  bool beside = false;                      // K chains: the factorization beside the X-stream (else after it)
   int grid_max = 0, kgrid_max = 0, trail_max = 0, chol_max = 0;  // launch sizes the buffers were made for
   // draws copied on a side stream while later sweeps compute
   cudaStream_t s_dl = nullptr;
@@ -235,6 +236,7 @@ hs::XKArgs xk_args(hs_probit* h) {
   a.K = h->K;
   a.kc = h->xk_kc;
   a.stages = h->xk_stages;
+  a.per_sm = h->xk_per_sm;
   a.bsw = h->bsw;
   a.partials = h->kpartials;
   a.z_out = h->cfg.debug ? h->z : nullptr;
@@ -407,7 +409,7 @@ cudaError_t enqueue_sweep(hs_probit* h) {
   // small enough to share the SMs).  Several chains on the single-launch
   // schedule: both fill the GPU, so the factorization follows the X-stream
   // explicitly (same total time, and each group's events time only itself).
-  const bool after_xstream = h->K > 1 && h->chol_grid > 0;
+  const bool after_xstream = h->K > 1 && h->chol_grid > 0 && !h->beside;
   auto factorize = [&]() -> cudaError_t {
     cudaError_t ee;
     {
@@ -752,7 +754,7 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   h->K = Kc;
   h->xk_kc = hs::xstream_k_default_kc(Kc);
   h->xk_stages = hs::kXkDefaultStages;
-  h->xk = Kc > 1 && cfg.x_dtype == HS_X_BF16 && hs::xstream_k_supported((int)p, h->xk_kc, h->xk_stages);
+  h->xk = Kc > 1 && cfg.x_dtype == HS_X_BF16 && hs::xstream_k_supported((int)p, h->xk_kc, h->xk_stages, 1);
   h->drained.assign((size_t)Kc, 0);
   h->device = cfg.device;
   h->x_dtype = cfg.x_dtype;
@@ -825,7 +827,7 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   const size_t bc_bytes = (size_t)h->ld * (h->x_dtype == HS_X_F64 ? 8 : 4);
   h->grid = hs::xstream_grid(h->x_dtype, h->p, h->ld, N, num_sms > 0 ? num_sms : 1);
   if (h->xk) {
-    check(hs::xstream_k_prepare(h->xk_kc, h->xk_stages));
+    check(hs::xstream_k_prepare(h->xk_kc, h->xk_stages, 1));
     h->kgrid = hs::xstream_k_grid(N, num_sms > 0 ? num_sms : 1);
   }
   h->chol_words = hs::chol_sync_words(h->P);
@@ -1292,6 +1294,8 @@ int hs_probit_get_launch_shape(const hs_probit* h, hs_launch_shape* out) {
   std::memset(out, 0, sizeof(*out));
   out->xk_chains = h->xk ? h->xk_kc : 0;
   out->xk_stages = h->xk ? h->xk_stages : 0;
+  out->xk_ctas_per_sm = h->xk ? h->xk_per_sm : 0;
+  out->overlap = (h->K == 1 || h->chol_grid == 0 || h->beside) ? 1 : 2;
   out->xstream_ctas = h->xk ? h->kgrid : h->grid;
   out->chol_ctas = h->chol_grid;
   out->trail_ctas = h->tensor_sched ? h->trail_grid : 0;
@@ -1304,22 +1308,29 @@ int hs_probit_set_launch_shape(hs_probit* h, const hs_launch_shape* in) {
     if (r != 0) return HS_EINVAL;
   const int kc = in->xk_chains ? in->xk_chains : h->xk_kc;
   const int st = in->xk_stages ? in->xk_stages : h->xk_stages;
+  const int pm = in->xk_ctas_per_sm ? in->xk_ctas_per_sm : h->xk_per_sm;
   const int xs = in->xstream_ctas ? in->xstream_ctas : (h->xk ? h->kgrid : h->grid);
   const int cg = in->chol_ctas ? in->chol_ctas : h->chol_grid;
   const int tg = in->trail_ctas ? in->trail_ctas : h->trail_grid;
-  if (in->xk_chains < 0 || in->xk_stages < 0 || in->xstream_ctas < 0 || in->chol_ctas < 0 || in->trail_ctas < 0)
+  if (in->xk_chains < 0 || in->xk_stages < 0 || in->xstream_ctas < 0 || in->chol_ctas < 0 || in->trail_ctas < 0 ||
+      in->xk_ctas_per_sm < 0 || in->overlap < 0 || in->overlap > 2)
     return HS_EINVAL;
-  if ((in->xk_chains || in->xk_stages) && !h->xk) return HS_EUNSUPPORTED;
-  if (h->xk && (kc < h->K || !hs::xstream_k_supported(h->p, kc, st))) return HS_EINVAL;
-  if (xs < 1 || xs > (h->xk ? h->kgrid_max : h->grid_max)) return HS_EINVAL;
+  if ((in->xk_chains || in->xk_stages || in->xk_ctas_per_sm) && !h->xk) return HS_EUNSUPPORTED;
+  if (h->xk && (kc < h->K || !hs::xstream_k_supported(h->p, kc, st, pm))) return HS_EINVAL;
+  // the partial sums were sized for the starting grid at 32 chain columns
+  const int64_t xs_max = h->xk ? std::min<int64_t>(hs::xstream_k_tiles(h->N), (int64_t)h->kgrid_max * 32 / kc)
+                               : h->grid_max;
+  if (xs < 1 || xs > xs_max) return HS_EINVAL;
   if (in->chol_ctas && (h->chol_grid == 0 || cg < h->K + 1 || cg > h->chol_max)) return HS_EINVAL;
   if (in->trail_ctas && (!h->tensor_sched || tg < 1 || tg > h->trail_max)) return HS_EINVAL;
   DeviceGuard dg(h->device);
   if (!dg.ok) return HS_ECUDA;
   if (cudaStreamSynchronize(h->s0) != cudaSuccess || cudaStreamSynchronize(h->s1) != cudaSuccess) return HS_ECUDA;
-  if (h->xk && hs::xstream_k_prepare(kc, st) != cudaSuccess) return HS_ECUDA;
+  if (h->xk && hs::xstream_k_prepare(kc, st, pm) != cudaSuccess) return HS_ECUDA;
   h->xk_kc = kc;
   h->xk_stages = st;
+  h->xk_per_sm = pm;
+  if (in->overlap) h->beside = in->overlap == 1;
   if (h->xk) h->kgrid = xs;
   else h->grid = xs;
   h->trail_grid = tg;
@@ -1459,31 +1470,47 @@ int batch_check(hs_probit_batch* b) {
   return first;
 }
 
-// Launch shapes of every problem for oversubscription factor f: X-stream CTAs
-// in proportion to the problem's share of the X bytes, factorization blocks
-// and trailing-update CTAs to its share of the factorization work; kc, stages
-// for the tensor-core X-streams (0: leave as is).
-int batch_apply_shapes(hs_probit_batch* b, double f, int kc, int stages) {
+// Launch shapes of every problem: X-stream CTAs in proportion to the
+// problem's share of the X bytes (oversubscription factor f, times the CTAs
+// per SM of the X-stream tile), trailing-update CTAs to its share of the
+// factorization work (f), factorization blocks to the same share (factor fc:
+// those blocks mostly wait on their diagonal chains, so they want a factor of
+// their own); the tensor-core X-stream tile (kc chain columns, stages, CTAs
+// per SM; kc = 0: the handle's starting tile); overlap as the launch-shape
+// field (1 beside, 2 after).
+int batch_apply_shapes(hs_probit_batch* b, double f, double fc, int kc, int stages, int per_sm, int overlap) {
   for (size_t m = 0; m < b->probs.size(); ++m) {
     hs_probit* h = b->probs[m];
     const double sx = b->wx[m] / b->wx_sum, sc = b->wc[m] / b->wc_sum;
-    auto share = [](double v, int lo, int hi) {
+    auto share = [](double v, int lo, int64_t hi) {
       const long r = std::lround(v);
-      return (int)std::max<long>(lo, std::min<long>(hi, r));
+      return (int)std::max<long>(lo, std::min<long>((long)hi, r));
     };
     hs_launch_shape ls{};
-    ls.xstream_ctas = share(f * b->num_sms * sx, 1, h->xk ? h->kgrid_max : h->grid_max);
-    if (h->chol_grid > 0) ls.chol_ctas = share(f * h->chol_max * sc, h->K + 1, h->chol_max);
-    if (h->tensor_sched) ls.trail_ctas = share(f * b->num_sms * sc, 1, h->trail_max);
-    if (h->xk && kc > 0) {
-      const int c = kc >= h->K ? kc : 32;
-      if (hs::xstream_k_supported(h->p, c, stages)) {
-        ls.xk_chains = c;
-        ls.xk_stages = stages;
+    int c = 0, st = 0, pm = 1;
+    if (h->xk) {
+      c = hs::xstream_k_default_kc(h->K);
+      st = hs::kXkDefaultStages;
+      if (kc > 0) {
+        const int c2 = kc >= h->K ? kc : 32, pm2 = c2 == 16 ? per_sm : 1;
+        if (hs::xstream_k_supported(h->p, c2, stages, pm2)) {
+          c = c2;
+          st = stages;
+          pm = pm2;
+        }
       }
+      ls.xk_chains = c;
+      ls.xk_stages = st;
+      ls.xk_ctas_per_sm = pm;
     }
-    const int st = hs_probit_set_launch_shape(h, &ls);
-    if (st != HS_OK) return st;
+    const int64_t xs_hi = h->xk ? std::min<int64_t>(hs::xstream_k_tiles(h->N), (int64_t)h->kgrid_max * 32 / c)
+                                : h->grid_max;
+    ls.xstream_ctas = share(f * pm * b->num_sms * sx, 1, xs_hi);
+    if (h->chol_grid > 0) ls.chol_ctas = share(fc * h->chol_max * sc, h->K + 1, h->chol_max);
+    if (h->tensor_sched) ls.trail_ctas = share(f * b->num_sms * sc, 1, h->trail_max);
+    ls.overlap = overlap;
+    const int r = hs_probit_set_launch_shape(h, &ls);
+    if (r != HS_OK) return r;
   }
   return HS_OK;
 }
@@ -1571,7 +1598,7 @@ hs_probit_batch* batch_init_impl(const hs_probit_config* cfg, int32_t n, const h
     b->wc_sum += b->wc.back();
   }
   // the starting shapes: every problem's kernels sized to its share of the GPU
-  const int st = batch_apply_shapes(b, 1.0, 0, 0);
+  const int st = batch_apply_shapes(b, 1.0, 1.0, 0, 0, 1, 2);
   if (st != HS_OK) return bail(st);
   g_last_error = HS_OK;
   return b;
@@ -1661,45 +1688,70 @@ int hs_probit_batch_tune(hs_probit_batch* b, int32_t sweeps, double* best_ms) {
     }
     b->trials.clear();
     int status = HS_OK;
-    auto trial = [&](double f, int kc, int stages) -> double {
+    auto trial = [&](double f, double fc, int kc, int stages, int per_sm, int overlap) -> double {
       double ms = -1.0;
       if (status != HS_OK) return ms;
-      status = batch_apply_shapes(b, f, kc, stages);
+      status = batch_apply_shapes(b, f, fc, kc, stages, per_sm, overlap);
       if (status == HS_OK) status = batch_time(b, sweeps, &ms);
       if (status != HS_OK) return -1.0;
       hs_tune_trial t{};
       t.ms_per_sweep = ms;
-      t.oversub_x4 = (int32_t)std::lround(4.0 * f);
+      t.oversub = f;
+      t.chol_oversub = fc;
       t.xk_chains = kc;
       t.xk_stages = stages;
+      t.xk_ctas_per_sm = kc > 0 ? per_sm : 0;
+      t.overlap = overlap;
       b->trials.push_back(t);
       return ms;
     };
-    // oversubscription of the proportional shares, then the X-stream tiles at the best one
+    // oversubscription of the proportional shares, then the factorization's
+    // own factor, then the X-stream tiles, each at the best so far
     const double fs[] = {0.5, 1.0, 2.0, 4.0};
-    double best = -1.0, best_f = 1.0;
+    double best = -1.0, best_f = 1.0, best_fc = 1.0;
     for (double f : fs) {
-      const double ms = trial(f, 0, 0);
+      const double ms = trial(f, f, 0, 0, 1, 2);
       if (ms >= 0 && (best < 0 || ms < best)) {
         best = ms;
-        best_f = f;
+        best_f = best_fc = f;
       }
     }
-    int best_kc = 0, best_st = 0;
-    bool any_xk = false;
-    for (hs_probit* h : b->probs) any_xk = any_xk || h->xk;
+    const double fcs[] = {0.125, 0.25, 0.5, 2.0};
+    const double f0 = best_f;
+    for (double r : fcs) {
+      const double ms = trial(f0, f0 * r, 0, 0, 1, 2);
+      if (ms >= 0 && (best < 0 || ms < best)) {
+        best = ms;
+        best_fc = f0 * r;
+      }
+    }
+    int best_kc = 0, best_st = 0, best_pm = 1, best_ov = 2;
+    bool any_xk = false, any_multi = false;
+    for (hs_probit* h : b->probs) {
+      any_xk = any_xk || h->xk;
+      any_multi = any_multi || (h->K > 1 && h->chol_grid > 0);
+    }
     if (any_xk) {
-      const int shapes[][2] = {{16, 4}, {16, 6}, {16, 8}, {32, 8}};
+      const int shapes[][3] = {{16, 4, 1}, {16, 6, 1}, {16, 8, 1}, {16, 4, 2}, {32, 8, 1}};
       for (const auto& sh : shapes) {
-        const double ms = trial(best_f, sh[0], sh[1]);
+        const double ms = trial(best_f, best_fc, sh[0], sh[1], sh[2], 2);
         if (ms >= 0 && (best < 0 || ms < best)) {
           best = ms;
           best_kc = sh[0];
           best_st = sh[1];
+          best_pm = sh[2];
         }
       }
     }
-    if (status == HS_OK) status = batch_apply_shapes(b, best_f, best_kc, best_st);
+    if (any_multi) {
+      // the K chains' factorization beside the X-stream instead of after it
+      const double ms = trial(best_f, best_fc, best_kc, best_st, best_pm, 1);
+      if (ms >= 0 && (best < 0 || ms < best)) {
+        best = ms;
+        best_ov = 1;
+      }
+    }
+    if (status == HS_OK) status = batch_apply_shapes(b, best_f, best_fc, best_kc, best_st, best_pm, best_ov);
     if (status == HS_OK) {
       const cudaError_t e = batch_build_graph(b);
       if (e != cudaSuccess) status = cuda_status(e);

@@ -377,8 +377,10 @@ int vec_elems() {
 
 // Rows per tile for one 16-byte slice per thread: FP64/FP32 take 16 rows;
 // the narrow formats unpack 8 or 16 values per slice and take fewer rows to
-// stay within the register budget.
-template <int XD> constexpr int rows_s1() { return XD == HS_X_FP8E4M3 ? 4 : XD == HS_X_BF16 ? 8 : 16; }
+// stay within the register budget.  FP8 takes 8 (measured at p = 4000: with 4
+// rows, 16 KB tiles, the per-tile barriers and draws held the kernel to a
+// third of HBM bandwidth).
+template <int XD> constexpr int rows_s1() { return XD == HS_X_FP8E4M3 ? 8 : XD == HS_X_BF16 ? 8 : 16; }
 
 template <int XD>
 cudaError_t launch_dtype(const XStreamArgs& a, int grid, cudaStream_t s) {

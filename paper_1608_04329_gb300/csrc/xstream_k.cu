@@ -238,8 +238,8 @@ __host__ __device__ constexpr uint32_t xk_tmem_cols(int kc, int nch) {
   return c;
 }
 
-template <int KC, int S>
-__global__ void __launch_bounds__(XKShape<KC, S>::kThreads, 1)
+template <int KC, int S, int MINB>
+__global__ void __launch_bounds__(XKShape<KC, S>::kThreads, MINB)
     xstream_k_kernel(const __grid_constant__ CUtensorMap xmap, XKArgs a) {
   using Sh = XKShape<KC, S>;
   constexpr int kXStages = S;
@@ -542,17 +542,19 @@ int xstream_k_chunks(int p) {
 }
 
 namespace {
-// f(std::integral_constant<int, KC>, std::integral_constant<int, S>) for the
-// instantiated shapes; false for any other.
+// f(KC, S, MINB) as std::integral_constant values for the instantiated launch
+// shapes (chain columns, ring stages, CTAs per SM); false for any other.
+// Two CTAs per SM only for the narrow tile with four stages: 89 KB of shared
+// memory and at most 85 registers a thread each.
 template <class F>
-bool with_shape(int kc, int stages, F&& f) {
-#define HS_XK_SHAPE(KC, S)                                                      \
-  if (kc == KC && stages == S) {                                                \
-    f(std::integral_constant<int, KC>{}, std::integral_constant<int, S>{});     \
-    return true;                                                                \
+bool with_shape(int kc, int stages, int per_sm, F&& f) {
+#define HS_XK_SHAPE(KC, S, M)                                                                  \
+  if (kc == KC && stages == S && per_sm == M) {                                                \
+    f(std::integral_constant<int, KC>{}, std::integral_constant<int, S>{}, std::integral_constant<int, M>{}); \
+    return true;                                                                               \
   }
-  HS_XK_SHAPE(16, 4) HS_XK_SHAPE(16, 6) HS_XK_SHAPE(16, 8)
-  HS_XK_SHAPE(32, 4) HS_XK_SHAPE(32, 6) HS_XK_SHAPE(32, 8)
+  HS_XK_SHAPE(16, 4, 1) HS_XK_SHAPE(16, 6, 1) HS_XK_SHAPE(16, 8, 1) HS_XK_SHAPE(16, 4, 2)
+  HS_XK_SHAPE(32, 4, 1) HS_XK_SHAPE(32, 6, 1) HS_XK_SHAPE(32, 8, 1)
 #undef HS_XK_SHAPE
   return false;
 }
@@ -560,24 +562,29 @@ bool with_shape(int kc, int stages, F&& f) {
 
 size_t xstream_k_smem_bytes(int kc, int stages) {
   size_t b = 0;
-  with_shape(kc, stages, [&](auto KC, auto S) { b = XKShape<decltype(KC)::value, decltype(S)::value>::kSmem; });
+  with_shape(kc, stages, 1, [&](auto KC, auto S, auto) { b = XKShape<decltype(KC)::value, decltype(S)::value>::kSmem; });
   return b;
 }
 
-bool xstream_k_supported(int p, int kc, int stages) {
+bool xstream_k_supported(int p, int kc, int stages, int per_sm) {
   const int nch = xstream_k_chunks(p);
+  bool inst = false;
+  with_shape(kc, stages, per_sm, [&](auto, auto, auto) { inst = true; });
   const size_t smem = xstream_k_smem_bytes(kc, stages);
-  // TMEM: two eta' buffers of 2 KC columns + KC per 128-feature group
-  return p >= 1 && smem > 0 && 4 * kc + kc * (nch / 2) <= 512 && smem <= 227 * 1024;
+  // TMEM: two eta' buffers of 2 KC columns + KC per 128-feature group; with
+  // two CTAs per SM each must fit in half of the 512 columns (an allocation
+  // never waits for the other CTA)
+  return p >= 1 && inst && smem > 0 && 4 * kc + kc * (nch / 2) <= 512 / per_sm &&
+         smem * per_sm <= (per_sm == 1 ? 227 * 1024 : 228 * 1024 - 2048);
 }
 
 int xstream_k_default_kc(int K) { return K <= 16 ? 16 : 32; }
 
-cudaError_t xstream_k_prepare(int kc, int stages) {
+cudaError_t xstream_k_prepare(int kc, int stages, int per_sm) {
   cudaError_t e = cudaErrorInvalidValue;
-  with_shape(kc, stages, [&](auto KC, auto S) {
-    constexpr int c = decltype(KC)::value, st = decltype(S)::value;
-    e = cudaFuncSetAttribute((const void*)xstream_k_kernel<c, st>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  with_shape(kc, stages, per_sm, [&](auto KC, auto S, auto M) {
+    constexpr int c = decltype(KC)::value, st = decltype(S)::value, mb = decltype(M)::value;
+    e = cudaFuncSetAttribute((const void*)xstream_k_kernel<c, st, mb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)XKShape<c, st>::kSmem);
   });
   return e;
@@ -633,9 +640,9 @@ cudaError_t xstream_k_enqueue(const void* map, const XKArgs& a, const double* be
   CUtensorMap m;
   memcpy(&m, map, sizeof(m));
   e = cudaErrorInvalidValue;
-  with_shape(a.kc, a.stages, [&](auto KC, auto S) {
+  with_shape(a.kc, a.stages, a.per_sm, [&](auto KC, auto S, auto M) {
     using Sh = XKShape<decltype(KC)::value, decltype(S)::value>;
-    xstream_k_kernel<Sh::kKc, Sh::kStages><<<grid, Sh::kThreads, Sh::kSmem, s>>>(m, a);
+    xstream_k_kernel<Sh::kKc, Sh::kStages, decltype(M)::value><<<grid, Sh::kThreads, Sh::kSmem, s>>>(m, a);
     e = cudaGetLastError();
   });
   return e;

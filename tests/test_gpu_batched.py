@@ -278,3 +278,32 @@ def test_tensor_core_trailing_updates_match_pair_arithmetic(pkg, dt, N, p, K):
         assert np.array_equal(a["lambda_inv2"], b["lambda_inv2"]) and a["tau_inv2"] == b["tau_inv2"]
         db = np.linalg.norm(a["beta"] - b["beta"]) / np.linalg.norm(a["beta"])
         assert db <= 1e-11, (m, db)
+
+
+def test_eight_chains_on_fp8_correlated_design_at_p_4000(pkg):
+    """The large correlated workload's shape with its K = 8 chains at a size
+    the oracle runs in seconds: FP8 e4m3 X with column scales, AR(1) rows,
+    p = 4000, 20 nonzeros U[0.5, 2].  Each chain takes a one-chain FP8 pass
+    (FP32 accumulation) and the block-column factorization; every chain must
+    reproduce the oracle's transition at the FP32 tolerance."""
+    N, p, K = 3000, 4000, 8
+    d = problem(N, p, 20, "fp8", seed=5, mag=(0.5, 2.0), design="ar1")
+    X = x_f64(d)
+    G = oracle.gram(X)
+    states = [random_state(p, k=3, seed=600 + m, scale=0.05) for m in range(K)]
+    s = pkg.HSProbit(d["X"], d["y"], seed=29, scales=d["scales"], debug=True, num_chains=K)
+    try:
+        for m, st in enumerate(states):
+            s.set_state(st.beta, st.lam_inv2, st.nu_inv, st.tau_inv2, st.xi_inv, st.k, chain=m)
+        s.sweep(1)
+        got = []
+        for m in range(K):
+            g = s.get_state(chain=m)
+            g["z"] = s.debug_z(chain=m)
+            g["xtz"] = s.debug_xtz(chain=m)
+            got.append(g)
+    finally:
+        s.close()
+    for m, st in enumerate(states):
+        ref = oracle.sweep_once(st.copy(), X, d["y"], G, 29, chain=m, keep=True)
+        assert_transition_close(got[m], ref, 1e-4)

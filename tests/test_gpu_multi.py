@@ -115,8 +115,9 @@ def test_batch_runs_many_sweeps_and_tuner_restores_state(pkg):
         b.close()
 
 
-@pytest.mark.parametrize("kc,stages", [(16, 4), (16, 6), (16, 8), (32, 4), (32, 6), (32, 8)])
-def test_every_tensor_core_xstream_shape_matches_oracle(pkg, kc, stages):
+@pytest.mark.parametrize("kc,stages,per_sm", [(16, 4, 1), (16, 6, 1), (16, 8, 1), (16, 4, 2), (32, 4, 1),
+                                              (32, 6, 1), (32, 8, 1)])
+def test_every_tensor_core_xstream_shape_matches_oracle(pkg, kc, stages, per_sm):
     N, p, K = 4099, 700, 6
     d = problem(N, p, 5, "bf16", seed=kc + stages)
     X = x_f64(d)
@@ -124,9 +125,9 @@ def test_every_tensor_core_xstream_shape_matches_oracle(pkg, kc, stages):
     states = [random_state(p, k=8, seed=500 + m) for m in range(K)]
     s = pkg.HSProbit(d["X"], d["y"], seed=23, debug=True, num_chains=K)
     try:
-        s.set_launch_shape(xk_chains=kc, xk_stages=stages, xstream_ctas=17)  # of 33 row tiles
+        s.set_launch_shape(xk_chains=kc, xk_stages=stages, xk_ctas_per_sm=per_sm, xstream_ctas=17)  # of 33 tiles
         sh = s.launch_shape()
-        assert (sh["xk_chains"], sh["xk_stages"], sh["xstream_ctas"]) == (kc, stages, 17)
+        assert (sh["xk_chains"], sh["xk_stages"], sh["xk_ctas_per_sm"], sh["xstream_ctas"]) == (kc, stages, per_sm, 17)
         for m, st in enumerate(states):
             s.set_state(st.beta, st.lam_inv2, st.nu_inv, st.tau_inv2, st.xi_inv, st.k, chain=m)
         s.sweep(1)
@@ -159,13 +160,31 @@ def test_factorization_grid_does_not_change_the_transition(pkg):
         assert np.array_equal(a, b)
 
 
+def test_factorization_beside_the_xstream_gives_the_same_transition(pkg):
+    d = problem(5000, 600, 5, "bf16", seed=9)
+    outs = []
+    for overlap in (2, 1):
+        s = pkg.HSProbit(d["X"], d["y"], seed=6, num_chains=4, use_graph=True)
+        try:
+            assert s.launch_shape()["overlap"] == 2
+            s.set_launch_shape(overlap=overlap)
+            assert s.launch_shape()["overlap"] == overlap
+            s.sweep(3)
+            outs.append([s.get_state(chain=m)["beta"] for m in range(4)])
+        finally:
+            s.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
 def test_launch_shape_rejects_out_of_range_sizes(pkg):
     d = problem(2000, 300, 5, "bf16", seed=1)
     s = pkg.HSProbit(d["X"], d["y"], seed=1, num_chains=4)
     try:
         sh = s.launch_shape()
         for bad in ({"xk_chains": 8}, {"xk_stages": 5}, {"xstream_ctas": sh["xstream_ctas"] + 1},
-                    {"chol_ctas": 4}, {"xstream_ctas": -1}):
+                    {"chol_ctas": 4}, {"xstream_ctas": -1}, {"xk_ctas_per_sm": 2, "xk_stages": 8},
+                    {"xk_ctas_per_sm": 3}, {"overlap": 3}):
             with pytest.raises(pkg.HSProbitError):
                 s.set_launch_shape(**bad)
         assert s.launch_shape() == sh
