@@ -306,10 +306,13 @@ int64_t hs_chol_block_task_list(int32_t T, int32_t k0, int32_t k1, int32_t worke
  * A handle made with cfg.num_chains = K > 1 runs K independent chains on the
  * same X.  Chain m uses chain id cfg.chain + m in its Philox counters, so
  * it is the same transition as a one-chain handle with that chain id.  For
- * BF16 X the X-stream of all K chains is one pass over X on the tensor cores
+ * BF16 and FP8 X the X-stream of all K chains runs on the tensor cores
  * (eta = X B and X^T Z as BF16 products, beta and z each split into two BF16
- * parts, FP32 accumulation), for p <= 1536 (K > 16) or p <= 3584 (K <= 16);
- * otherwise it is one pass of the one-chain X-stream per chain.  The
+ * parts, FP8 codes converted to BF16 exactly, FP32 accumulation): one pass
+ * over X for BF16 X with p <= 1536 (K > 16) or p <= 3584 (K <= 16), else
+ * two passes (eta and the z draws, then X^T Z) for p <= 2048 (K > 16) or
+ * p <= 4096 (K <= 16); other cases take one pass of the one-chain X-stream
+ * per chain.  The
  * factorizations of all chains are one launch (on the single-launch
  * schedule, by default without the inverse factor, beta then coming from
  * block substitution: see beta_solve), and the other steps run per chain.
@@ -358,7 +361,8 @@ int hs_probit_debug_xtz_chain(hs_probit* h, int chain, double* xtz_out);
  * the same.  A field of 0 leaves that size as it is. */
 typedef struct hs_launch_shape {
   int32_t xk_chains;    /* chain columns of a tensor-core X-stream tile: 16 (K <= 16) or 32 */
-  int32_t xk_stages;    /* shared-memory ring stages of that X-stream: 4, 6 or 8 */
+  int32_t xk_stages;    /* shared-memory ring stages of that X-stream: 4, 6 or 8 (the two-pass form
+                           has one fixed value per width) */
   int32_t xstream_ctas; /* CTAs of the X-stream: 1 .. the value the handle started with (for the
                            tensor-core X-stream, x 32 / xk_chains, at most one per 128 rows) */
   int32_t chol_ctas;    /* blocks of each factorization launch: K + 1 .. the starting value */

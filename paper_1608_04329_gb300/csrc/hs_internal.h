@@ -70,6 +70,12 @@ struct XKArgs {
   RngKey rng;             // rng.chain is chain 0's id; chain m uses rng.chain + m
   int* err;
   unsigned int* sm_mark;  // or nullptr, as XStreamArgs::sm_mark
+  // the split form (xstream_k_split_enqueue): X stored as FP8 codes or BF16,
+  // column scales (FP8) folded into B^T and into X^T Z, and the Z^T tiles
+  // the first kernel writes for the second
+  int fp8;                // 1: X holds e4m3 codes
+  const float* colscale;  // p column scales, or nullptr
+  void* zt;               // ceil(N / 128) x 4 x kc x 128 B
 };
 int xstream_k_chunks(int p);
 // Launch shapes: kc chain columns (16 or 32), stages ring stages (4, 6 or 8).
@@ -89,6 +95,18 @@ int xstream_k_make_map(const void* X, int64_t N, int ld, void* map_out);
 cudaError_t xstream_k_enqueue(const void* map, const XKArgs& a, const double* beta, int64_t beta_stride,
                               unsigned char* bsw, int grid, cudaStream_t s);
 cudaError_t xstream_k_reduce(const XKArgs& a, int grid, double* xtz, int64_t xtz_stride, cudaStream_t s);
+// The split form: pass 1 (eta = X B, the z draws, Z^T to global memory) and
+// pass 2 (X^T Z) as two kernels, so pass 2's TMEM holds every feature group
+// (p up to 4096 at 16 chain columns, 2048 at 32) and X may be FP8 (converted
+// to BF16 in shared memory, exactly).  X is read twice.
+bool xstream_k_split_supported(int p, int kc);
+cudaError_t xstream_k_split_prepare(int kc, int fp8);
+size_t xstream_k_zt_bytes(int64_t N, int kc);
+int xstream_k_split_stages(int kc);  // the split form's fixed ring stages
+// Tensor map of FP8 X (N rows, ld columns of one byte): boxes of 64 x 128, no swizzle.
+int xstream_k_make_map_fp8(const void* X, int64_t N, int ld, void* map_out);
+cudaError_t xstream_k_split_enqueue(const void* map, const XKArgs& a, const double* beta, int64_t beta_stride,
+                                    unsigned char* bsw, int grid, cudaStream_t s);
 
 // Per-process kernel attributes (shared-memory carveout); call before launching.
 cudaError_t xstream_prepare();

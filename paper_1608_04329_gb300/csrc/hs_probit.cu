@@ -97,6 +97,8 @@ struct hs_probit {
   int kgrid = 0;                            // batched X-stream CTAs
   bool xk = false;                          // K chains on the tensor-core X-stream (else one pass per chain)
   int xk_kc = 32, xk_stages = 8, xk_per_sm = 1;  // its launch shape (chain columns, ring stages, CTAs per SM)
+  bool xk_split = false;                    // as two kernels (FP8 X, or p past the fused kernel's TMEM)
+  void* zt = nullptr;                       // the split form's Z^T tiles
   bool beside = false;                      // K chains: the factorization beside the X-stream (else after it)
   int grid_max = 0, kgrid_max = 0, trail_max = 0, chol_max = 0;  // launch sizes the buffers were made for
   // draws copied on a side stream while later sweeps compute
@@ -237,6 +239,9 @@ hs::XKArgs xk_args(hs_probit* h) {
   a.kc = h->xk_kc;
   a.stages = h->xk_stages;
   a.per_sm = h->xk_per_sm;
+  a.fp8 = h->x_dtype == HS_X_FP8E4M3 ? 1 : 0;
+  a.colscale = h->colscale;
+  a.zt = h->zt;
   a.bsw = h->bsw;
   a.partials = h->kpartials;
   a.z_out = h->cfg.debug ? h->z : nullptr;
@@ -466,8 +471,9 @@ cudaError_t enqueue_sweep(hs_probit* h) {
     const hs::XKArgs xa = xk_args(h);
     {
       ProfSpan sp(h, 0, h->s0);
-      if ((e = hs::xstream_k_enqueue(h->xmap, xa, h->beta, h->p, h->bsw, h->kgrid, h->s0)) != cudaSuccess)
-        return e;
+      e = h->xk_split ? hs::xstream_k_split_enqueue(h->xmap, xa, h->beta, h->p, h->bsw, h->kgrid, h->s0)
+                      : hs::xstream_k_enqueue(h->xmap, xa, h->beta, h->p, h->bsw, h->kgrid, h->s0);
+      if (e != cudaSuccess) return e;
     }
     {
       ProfSpan sp(h, 1, h->s0);
@@ -754,7 +760,16 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   h->K = Kc;
   h->xk_kc = hs::xstream_k_default_kc(Kc);
   h->xk_stages = hs::kXkDefaultStages;
-  h->xk = Kc > 1 && cfg.x_dtype == HS_X_BF16 && hs::xstream_k_supported((int)p, h->xk_kc, h->xk_stages, 1);
+  {
+    // K chains on the tensor cores: the fused kernel for BF16 X within its
+    // TMEM budget, else the split form (BF16 or FP8 X)
+    const bool fused = cfg.x_dtype == HS_X_BF16 && hs::xstream_k_supported((int)p, h->xk_kc, h->xk_stages, 1);
+    const bool split = (cfg.x_dtype == HS_X_BF16 || cfg.x_dtype == HS_X_FP8E4M3) &&
+                       hs::xstream_k_split_supported((int)p, h->xk_kc);
+    h->xk = Kc > 1 && (fused || split);
+    h->xk_split = h->xk && !fused;
+    if (h->xk_split) h->xk_stages = hs::xstream_k_split_stages(h->xk_kc);
+  }
   h->drained.assign((size_t)Kc, 0);
   h->device = cfg.device;
   h->x_dtype = cfg.x_dtype;
@@ -826,7 +841,13 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   const size_t K = (size_t)h->K;
   const size_t bc_bytes = (size_t)h->ld * (h->x_dtype == HS_X_F64 ? 8 : 4);
   h->grid = hs::xstream_grid(h->x_dtype, h->p, h->ld, N, num_sms > 0 ? num_sms : 1);
-  if (h->xk) {
+  if (h->xk_split) {
+    check(hs::xstream_k_split_prepare(h->xk_kc, cfg.x_dtype == HS_X_FP8E4M3 ? 1 : 0));
+    // both widths, so that a tuner may switch
+    if (hs::xstream_k_split_supported((int)p, 32))
+      check(hs::xstream_k_split_prepare(32, cfg.x_dtype == HS_X_FP8E4M3 ? 1 : 0));
+    h->kgrid = hs::xstream_k_grid(N, num_sms > 0 ? num_sms : 1);
+  } else if (h->xk) {
     check(hs::xstream_k_prepare(h->xk_kc, h->xk_stages, 1));
     h->kgrid = hs::xstream_k_grid(N, num_sms > 0 ? num_sms : 1);
   }
@@ -883,6 +904,8 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   } else {
     // sized for the widest launch shape (32 chain columns), so a tuner may switch
     check(h->alloc(&h->bsw, hs::xstream_k_bsw_bytes(h->p, 32)));
+    if (h->xk_split)
+      check(h->alloc(&h->zt, hs::xstream_k_zt_bytes(N, hs::xstream_k_split_supported(h->p, 32) ? 32 : h->xk_kc)));
     check(h->alloc(&h->kpartials, hs::xstream_k_partial_floats(h->p, h->kgrid, 32) * sizeof(float)));
   }
   if (cfg.debug) check(h->alloc(&h->z, K * (size_t)N * sizeof(double)));
@@ -918,7 +941,10 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
     check(cudaMemsetAsync(h->chol_sync, 0, K * h->chol_words * sizeof(unsigned long long), h->s0));
     check(cudaMemsetAsync(h->sm_mark, 0, hs::kSmMarks * sizeof(unsigned int), h->s0));
   }
-  if (h->xk && e == cudaSuccess && hs::xstream_k_make_map(h->X, N, h->ld, h->xmap) != 0) e = cudaErrorInvalidValue;
+  if (h->xk && e == cudaSuccess &&
+      (h->x_dtype == HS_X_FP8E4M3 ? hs::xstream_k_make_map_fp8(h->X, N, h->ld, h->xmap)
+                                  : hs::xstream_k_make_map(h->X, N, h->ld, h->xmap)) != 0)
+    e = cudaErrorInvalidValue;
   if (cfg.x_is_device) check(hs::check_y_launch(h->y, N, h->err, h->s0));
   // ---- cold start (Sect. 6.1): beta = 0, lambda = nu = tau = xi = 1, k = 0, every chain ----
   {
@@ -972,7 +998,7 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   // shrink, factorization (one launch for every chain when single-launch), two draws, commits
   h->launches = 1 + ((h->K > 1 && h->chol_grid > 0) ? chol_l : h->K * chol_l) + 2 +
                 (h->K > 1 ? 2 : 1) +
-                (h->K == 1 ? 2 : h->xk ? 3 : 2 * h->K);
+                (h->K == 1 ? 2 : h->xk_split ? 4 : h->xk ? 3 : 2 * h->K);
   h->grid_max = h->grid;
   h->kgrid_max = h->kgrid;
   h->trail_max = h->trail_grid;
@@ -1307,7 +1333,7 @@ int hs_probit_set_launch_shape(hs_probit* h, const hs_launch_shape* in) {
   for (int r : in->reserved)
     if (r != 0) return HS_EINVAL;
   const int kc = in->xk_chains ? in->xk_chains : h->xk_kc;
-  const int st = in->xk_stages ? in->xk_stages : h->xk_stages;
+  const int st = h->xk_split ? hs::xstream_k_split_stages(kc) : in->xk_stages ? in->xk_stages : h->xk_stages;
   const int pm = in->xk_ctas_per_sm ? in->xk_ctas_per_sm : h->xk_per_sm;
   const int xs = in->xstream_ctas ? in->xstream_ctas : (h->xk ? h->kgrid : h->grid);
   const int cg = in->chol_ctas ? in->chol_ctas : h->chol_grid;
@@ -1316,7 +1342,11 @@ int hs_probit_set_launch_shape(hs_probit* h, const hs_launch_shape* in) {
       in->xk_ctas_per_sm < 0 || in->overlap < 0 || in->overlap > 2)
     return HS_EINVAL;
   if ((in->xk_chains || in->xk_stages || in->xk_ctas_per_sm) && !h->xk) return HS_EUNSUPPORTED;
-  if (h->xk && (kc < h->K || !hs::xstream_k_supported(h->p, kc, st, pm))) return HS_EINVAL;
+  if (h->xk && kc < h->K) return HS_EINVAL;
+  if (h->xk && h->xk_split &&
+      (!hs::xstream_k_split_supported(h->p, kc) || pm != 1 || (in->xk_stages && in->xk_stages != st)))
+    return HS_EINVAL;  // the split form has one tile shape per width
+  if (h->xk && !h->xk_split && !hs::xstream_k_supported(h->p, kc, st, pm)) return HS_EINVAL;
   // the partial sums were sized for the starting grid at 32 chain columns
   const int64_t xs_max = h->xk ? std::min<int64_t>(hs::xstream_k_tiles(h->N), (int64_t)h->kgrid_max * 32 / kc)
                                : h->grid_max;
@@ -1326,7 +1356,7 @@ int hs_probit_set_launch_shape(hs_probit* h, const hs_launch_shape* in) {
   DeviceGuard dg(h->device);
   if (!dg.ok) return HS_ECUDA;
   if (cudaStreamSynchronize(h->s0) != cudaSuccess || cudaStreamSynchronize(h->s1) != cudaSuccess) return HS_ECUDA;
-  if (h->xk && hs::xstream_k_prepare(kc, st, pm) != cudaSuccess) return HS_ECUDA;
+  if (h->xk && !h->xk_split && hs::xstream_k_prepare(kc, st, pm) != cudaSuccess) return HS_ECUDA;
   h->xk_kc = kc;
   h->xk_stages = st;
   h->xk_per_sm = pm;
@@ -1490,8 +1520,8 @@ int batch_apply_shapes(hs_probit_batch* b, double f, double fc, int kc, int stag
     int c = 0, st = 0, pm = 1;
     if (h->xk) {
       c = hs::xstream_k_default_kc(h->K);
-      st = hs::kXkDefaultStages;
-      if (kc > 0) {
+      st = h->xk_split ? hs::xstream_k_split_stages(c) : hs::kXkDefaultStages;
+      if (kc > 0 && !h->xk_split) {
         const int c2 = kc >= h->K ? kc : 32, pm2 = c2 == 16 ? per_sm : 1;
         if (hs::xstream_k_supported(h->p, c2, stages, pm2)) {
           c = c2;

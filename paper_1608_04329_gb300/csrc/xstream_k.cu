@@ -38,6 +38,7 @@
 // down through a shared abort flag.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -489,11 +490,494 @@ __global__ void __launch_bounds__(XKShape<KC, S>::kThreads, MINB)
   }
 }
 
+// ---- the split form: pass 1 and pass 2 as two kernels ------------------------
+// Pass 1 (xk_eta_kernel): per 128-row tile eta' = X [B_hi | B_lo] on the
+// tensor cores, the z draws as in the fused kernel, and Z^T (both BF16 parts,
+// in the swizzled layout pass 2 reads) stored to global memory by one bulk
+// copy per tile.  Pass 2 (xk_xtz_kernel): X^T Z_hi + X^T Z_lo over the same
+// tiles into TMEM, which then holds only the feature groups (KC columns
+// each).  For FP8 X each 64-feature chunk lands by TMA as codes (8 KB, 64-byte
+// rows) and four converter warps rewrite it as BF16 (exact: e4m3 values have
+// 4 significant bits) in the 128-byte-swizzled layout before the MMA reads it;
+// the column scales sit in B^T (pass 1) and in the reduce (pass 2).
+constexpr uint32_t kFp8PairBytes = kTR * 2 * kCF;  // 16 KB: 128 rows x 128 codes (two chunks)
+
+template <int KC, int F8>
+struct XKSplit {
+  static_assert(KC == 16 || KC == 32, "chain columns");
+  static constexpr int kStages = KC == 16 ? 6 : 4;  // BF16 X: one ring (even: pass 2 takes stages in pairs)
+  static constexpr uint32_t kBChunkBytes = 2 * KC * kCF * 2;
+  static constexpr uint32_t kZBlock = KC * 128;
+  static constexpr uint32_t kZTile = 4 * kZBlock;  // [hi/lo][rows 0-63 | 64-127]
+  static constexpr uint32_t kStageEta = kXChunkBytes + kBChunkBytes;
+  static constexpr uint32_t kStageXtz = kXChunkBytes;
+  // FP8 X: a ring of code stages, each two chunks (128 features: TMA boxes
+  // of 128-byte rows; pass 1 also puts the two B^T chunks there), and a ring
+  // of BF16 stages (even: a code stage fills two) the converter warps fill
+  static constexpr uint32_t kCodeEta = kFp8PairBytes + 2 * kBChunkBytes;
+  static constexpr uint32_t kCodeXtz = kFp8PairBytes;
+  static constexpr int kCodeStagesEta = KC == 16 ? 6 : 4;
+  static constexpr int kBfStagesEta = 4;
+  static constexpr int kCodeStagesXtz = KC == 16 ? 7 : 8;
+  static constexpr int kBfStagesXtz = KC == 16 ? 6 : 4;
+  static constexpr int kEpiWarps = 4 * (KC / kEpiChains);
+  static constexpr int kCvtWarps = F8 ? 4 : 0;
+  static constexpr int kThreads = 128 + 32 * (kEpiWarps + kCvtWarps);
+  static constexpr size_t kRingEta = F8 ? (size_t)kCodeStagesEta * kCodeEta + (size_t)kBfStagesEta * kXChunkBytes
+                                        : (size_t)kStages * kStageEta;
+  static constexpr size_t kRingXtz = F8 ? (size_t)kCodeStagesXtz * kCodeXtz + (size_t)kBfStagesXtz * kXChunkBytes
+                                        : (size_t)kStages * kStageXtz;
+  static constexpr size_t kSmemEta = 1024 + kRingEta + 2 * (size_t)kZTile;
+  static constexpr size_t kSmemXtz = 1024 + kRingXtz + 2 * (size_t)kZTile;
+  static_assert(kSmemEta <= 227 * 1024 && kSmemXtz <= 227 * 1024, "stages fit in shared memory");
+  static_assert(kStageEta % 1024 == 0 && kCodeEta % 1024 == 0 && kCodeXtz % 1024 == 0,
+                "stages keep the 1024-byte swizzle alignment");
+};
+
+// FP8 e4m3 codes of two chunks (128 rows of 128 bytes) -> BF16 in the
+// 128-byte-swizzled K-major layout of the MMA, features 0-63 into dst0 and
+// 64-127 into dst1.  Thread t (0..127) takes the 16-byte granules t + 128 j
+// (row G / 8, features 16 (G % 8) ..), so a warp reads 512 contiguous bytes
+// per load and each 16-byte store of a warp fills whole 128-byte wavefronts.
+__device__ __forceinline__ void cvt_pair_fp8(const unsigned char* src, unsigned char* dst0, unsigned char* dst1,
+                                             int t) {
+#pragma unroll
+  for (int jg = 0; jg < 8; ++jg) {
+    const int G = t + 128 * jg;
+    const int row = G >> 3, c16 = G & 7;
+    unsigned char* dst = c16 < 4 ? dst0 : dst1;
+    const int f0 = 16 * (c16 & 3);
+    const uint4 v = *reinterpret_cast<const uint4*>(src + (size_t)G * 16);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t o[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const __nv_fp8x2_storage_t pr = (__nv_fp8x2_storage_t)((w[i] >> (16 * h)) & 0xFFFFu);
+        const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pr, __NV_E4M3);
+        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&hr));
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(f.x, f.y);
+        o[2 * i + h] = *reinterpret_cast<const uint32_t*>(&b2);
+      }
+    }
+    *reinterpret_cast<uint4*>(dst + sw128_off(row, f0)) = make_uint4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<uint4*>(dst + sw128_off(row, f0 + 8)) = make_uint4(o[4], o[5], o[6], o[7]);
+  }
+}
+
+// Shared-memory to global bulk copy of one tile's Z^T (bulk-group completion).
+__device__ __forceinline__ void bulk_s2g(void* gdst, const void* ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
+               "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+template <int KC, int F8>
+__global__ void __launch_bounds__(XKSplit<KC, F8>::kThreads, 1)
+    xk_eta_kernel(const __grid_constant__ CUtensorMap xmap, XKArgs a) {
+  using Sp = XKSplit<KC, F8>;
+  // BF16 X: one ring of S stages (X chunk, B^T chunk).  FP8 X: CS code
+  // stages (codes, B^T chunk) and BS BF16 stages.
+  constexpr int S = Sp::kStages, CS = Sp::kCodeStagesEta, BS = Sp::kBfStagesEta;
+  constexpr int NF = F8 ? CS : S, NB = F8 ? BS : 1;  // barrier array sizes
+  constexpr uint32_t kStage = Sp::kStageEta, kCode = Sp::kCodeEta, kBChunkBytes = Sp::kBChunkBytes,
+                     kZBlock = Sp::kZBlock, kZTile = Sp::kZTile;
+  constexpr int kEpiWarps = Sp::kEpiWarps, kEpiThreads = 32 * kEpiWarps;
+  extern __shared__ unsigned char dyn[];
+  __shared__ uint64_t full[NF], empty[NF], bfull[NB], bempty[NB], eta_full[2], eta_empty[2], z_ready[2],
+      zt_empty[2], mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_v;
+  int* const abort_flag = &abort_v;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* base = dyn + ((1024u - (smem_u32(dyn) & 1023u)) & 1023u);
+  unsigned char* bf = base + (size_t)CS * kCode;  // FP8: the BF16 ring after the code ring
+  unsigned char* sZ = base + Sp::kRingEta;        // two tiles of Z^T
+  const int64_t ntiles = (a.N + kTR - 1) / kTR;
+  const int64_t t0 = ntiles * blockIdx.x / gridDim.x;
+  const int64_t t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+  const int nch = a.nch;
+  const uint32_t nq = (uint32_t)((t1 - t0) * nch);  // chunks this CTA loads
+
+  if (tid == 0) {
+    if (a.sm_mark) {
+      unsigned int smid;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      if (smid < (unsigned)kSmMarks) a.sm_mark[smid] = (unsigned int)(*a.k_dev + 1);
+    }
+    for (int s = 0; s < NF; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < NB; ++s) {
+      mbar_init(&bfull[s], 128);
+      mbar_init(&bempty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&eta_full[b], 1);
+      mbar_init(&eta_empty[b], kEpiThreads);
+      mbar_init(&z_ready[b], kEpiThreads);
+      mbar_init(&zt_empty[b], 1);
+    }
+    mbar_init(&mma_done, 1);
+    abort_v = 0;
+    fence_mbar_init();
+  }
+  constexpr uint32_t tcols = 4 * KC < 32 ? 32 : 4 * KC;  // two eta' buffers of 2 KC columns
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tm_eta = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer: X chunk and its B^T chunk (FP8: two of each) ----------------
+    const uint64_t pol = l2_policy_evict_first();  // X is read once by this kernel
+    uint32_t q = 0;  // stage fills
+    bool ok = true;
+    for (int64_t t = t0; t < t1 && ok; ++t) {
+      for (int c = 0; c < nch; c += F8 ? 2 : 1, ++q) {
+        const int s = q % NF;
+        if (!(ok = xk_wait(&empty[s], ((q / NF) & 1) ^ 1, abort_flag, a.err))) break;
+        const unsigned char* bsw = static_cast<const unsigned char*>(a.bsw) + (size_t)c * kBChunkBytes;
+        if constexpr (F8) {
+          unsigned char* st = base + (size_t)s * kCode;
+          mbar_arrive_expect_tx(&full[s], kFp8PairBytes + 2 * kBChunkBytes);
+          tma_load_2d(st, &xmap, c * kCF, (int)(t * kTR), &full[s], pol);  // 128 codes x 128 rows
+          bulk_g2s(st + kFp8PairBytes, bsw, 2 * kBChunkBytes, &full[s]);
+        } else {
+          unsigned char* st = base + (size_t)s * kStage;
+          mbar_arrive_expect_tx(&full[s], kXChunkBytes + kBChunkBytes);
+          tma_load_2d(st, &xmap, c * kCF, (int)(t * kTR), &full[s], pol);
+          bulk_g2s(st + kXChunkBytes, bsw, kBChunkBytes, &full[s]);
+        }
+      }
+    }
+    const uint32_t nd = q < (uint32_t)NF ? q : (uint32_t)NF;
+    for (uint32_t d = 1; d <= nd; ++d) {
+      const uint32_t qq = q - d;
+      mbar_wait(&full[qq % NF], (qq / NF) & 1, 2000000000ull);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer: pass 1 ----------------
+    const uint32_t id_eta = idesc_bf16(kTR, 2 * KC, 0, 0);
+    uint32_t q = 0;  // chunks
+    bool ok = true;
+    for (int64_t n = 0; t0 + n < t1 && ok; ++n) {
+      const int b = (int)(n & 1);
+      if (!(ok = xk_wait(&eta_empty[b], ((n >> 1) & 1) ^ 1, abort_flag, a.err))) break;
+      tc_fence_after();
+      for (int c = 0; c < nch; ++c, ++q) {
+        uint32_t xa, ba;  // shared addresses of the BF16 X chunk and of the B^T chunk
+        if constexpr (F8) {
+          const int sb = q % NB;
+          if (!(ok = xk_wait(&bfull[sb], (q / NB) & 1, abort_flag, a.err))) break;
+          xa = smem_u32(bf) + (uint32_t)sb * kXChunkBytes;
+          ba = smem_u32(base) + (uint32_t)((q / 2) % NF) * kCode + kFp8PairBytes + (q & 1) * kBChunkBytes;
+        } else {
+          if (!(ok = xk_wait(&full[q % NF], (q / NF) & 1, abort_flag, a.err))) break;
+          xa = smem_u32(base) + (uint32_t)(q % NF) * kStage;
+          ba = xa + kXChunkBytes;
+        }
+        tc_fence_after();
+        const uint64_t dx = sw128_desc(xa, 16, 1024), db = sw128_desc(ba, 16, 1024);
+#pragma unroll
+        for (int kk = 0; kk < kCF / 16; ++kk)
+          mma_bf16(tm_eta + 2 * KC * b, dx + 2 * kk, db + 2 * kk, id_eta, (c > 0 || kk > 0) ? 1 : 0);
+        if constexpr (F8) {
+          mma_commit(&bempty[q % NB]);
+          if (q & 1) mma_commit(&empty[(q / 2) % NF]);  // both chunks of the code stage read
+        } else {
+          mma_commit(&empty[q % NF]);
+        }
+      }
+      if (!ok) break;
+      mma_commit(&eta_full[b]);
+    }
+    mma_commit(&mma_done);
+    mbar_wait(&mma_done, 0, 2000000000ull);  // nothing in flight when the CTA leaves
+  } else if (warp == 3 && lane == 0) {
+    // ---------------- Z^T storer: one bulk copy per tile ----------------
+    for (int64_t n = 0; t0 + n < t1; ++n) {
+      const int zb = (int)(n & 1);
+      if (!xk_wait(&z_ready[zb], (n >> 1) & 1, abort_flag, a.err)) break;
+      bulk_s2g(static_cast<unsigned char*>(a.zt) + (size_t)(t0 + n) * kZTile, sZ + (size_t)zb * kZTile, kZTile);
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the source may be rewritten
+      mbar_arrive(&zt_empty[zb]);
+    }
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the writes are done before the CTA leaves
+  } else if (F8 && warp >= 4 + kEpiWarps) {
+    // ---------------- converter warps: codes -> BF16 ----------------
+    const int ct = tid - 32 * (4 + kEpiWarps);
+    for (uint32_t r = 0; r < nq / 2; ++r) {  // code stage r: chunks 2r, 2r + 1
+      const int s = r % NF, sb = (2 * r) % NB;   // NB even: the pair is sb, sb + 1
+      if (!xk_wait(&full[s], (r / NF) & 1, abort_flag, a.err)) break;
+      if (!xk_wait(&bempty[sb], (((2 * r) / NB) & 1) ^ 1, abort_flag, a.err)) break;
+      if (!xk_wait(&bempty[sb + 1], (((2 * r + 1) / NB) & 1) ^ 1, abort_flag, a.err)) break;
+      cvt_pair_fp8(base + (size_t)s * kCode, bf + (size_t)sb * kXChunkBytes, bf + (size_t)(sb + 1) * kXChunkBytes,
+                   ct);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+      mbar_arrive(&bfull[sb]);
+      mbar_arrive(&bfull[sb + 1]);
+    }
+  } else if (warp >= 4 && warp < 4 + kEpiWarps) {
+    // ---------------- epilogue: z draws and Z^T, as in the fused kernel ----------------
+    const int quad = warp & 3, part = (warp - 4) >> 2;
+    const int er = 32 * quad + lane;
+    const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
+    const int m0 = kEpiChains * part;
+    const uint32_t sweep = (uint32_t)(*a.k_dev + 1);
+    int it = 0;
+    int y_next = (t0 < t1 && t0 * kTR + er < a.N) ? a.y[t0 * kTR + er] : 1;
+    for (int64_t t = t0; t < t1; ++t, ++it) {
+      const int eb = it & 1;
+      const int yi_t = y_next;
+      if (t + 1 < t1 && (t + 1) * kTR + er < a.N) y_next = a.y[(t + 1) * kTR + er];
+      if (!xk_wait(&eta_full[eb], (it >> 1) & 1, abort_flag, a.err)) break;
+      tc_fence_after();
+      uint32_t hi[kEpiChains], lo[kEpiChains];
+      tmem_ld8(tm_eta + 2 * KC * eb + lane_off + m0, hi);
+      tmem_ld8(tm_eta + 2 * KC * eb + lane_off + KC + m0, lo);
+      tmem_ld_wait();
+      tc_fence_before();
+      mbar_arrive(&eta_empty[eb]);
+      const int64_t i = t * kTR + er;
+      const bool active = i < a.N;
+      const int yi = active ? yi_t : 1;
+      if (!xk_wait(&zt_empty[eb], ((it >> 1) & 1) ^ 1, abort_flag, a.err)) break;
+      unsigned char* zt = sZ + (size_t)eb * kZTile;
+      const int katom = er >> 6, kr = er & 63;
+      if (m0 >= a.K) {
+#pragma unroll
+        for (int mm = 0; mm < kEpiChains; ++mm) {
+          const uint32_t o = sw128_off(m0 + mm, kr);
+          *reinterpret_cast<uint16_t*>(zt + (size_t)(0 * 2 + katom) * kZBlock + o) = 0;
+          *reinterpret_cast<uint16_t*>(zt + (size_t)(1 * 2 + katom) * kZBlock + o) = 0;
+        }
+      } else {
+#pragma unroll
+        for (int mm = 0; mm < kEpiChains; ++mm) {
+          const int m = m0 + mm;
+          const float eta = __uint_as_float(hi[mm]) + __uint_as_float(lo[mm]);
+          const bool on = active && m < a.K;
+          float u = 0.5f, uc = 0.5f;
+          if (on) {
+            const Rng r{a.rng.k0, a.rng.k1, a.rng.chain + (uint32_t)m, a.rng.problem};
+            const uint4 wd = r.words((uint32_t)i, sweep, kPurZ);
+            unit_pair_f(wd.x, wd.y, u, uc);
+          }
+          const float ms = on ? (yi ? eta : -eta) : 0.0f;
+          float zp = tn_main_k(ms, u, uc);
+          const bool tail = on && ms < TnMath<float>::kTail;
+          if (tail) zp = tn_tail<float>(ms, u, uc);
+          zp = zp > TnMath<float>::tiny() ? zp : TnMath<float>::tiny();
+          float zz = on ? (yi ? zp : -zp) : 0.0f;
+          if (on && !isfinite(zz)) {
+            set_error(a.err, kErrNonFinite);
+            zz = 0.0f;
+          }
+          if (on && a.z_out) a.z_out[(size_t)m * a.N + i] = (double)zz;
+          const __nv_bfloat16 zh = __float2bfloat16_rn(zz);
+          const __nv_bfloat16 zl = __float2bfloat16_rn(zz - __bfloat162float(zh));
+          const uint32_t o = sw128_off(m, kr);
+          *reinterpret_cast<__nv_bfloat16*>(zt + (size_t)(0 * 2 + katom) * kZBlock + o) = zh;
+          *reinterpret_cast<__nv_bfloat16*>(zt + (size_t)(1 * 2 + katom) * kZBlock + o) = zl;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> bulk copy reads
+      mbar_arrive(&z_ready[eb]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm_eta), "r"(tcols));
+  }
+}
+
+template <int KC, int F8>
+__global__ void __launch_bounds__(XKSplit<KC, F8>::kThreads, 1)
+    xk_xtz_kernel(const __grid_constant__ CUtensorMap xmap, XKArgs a) {
+  using Sp = XKSplit<KC, F8>;
+  // BF16 X: one ring of S stages (X chunks).  FP8 X: CS code stages and BS
+  // BF16 stages (BS even: pass 2 takes BF16 stages in pairs).
+  constexpr int S = Sp::kStages, CS = Sp::kCodeStagesXtz, BS = Sp::kBfStagesXtz;
+  constexpr int NF = F8 ? CS : S, NB = F8 ? BS : 1;
+  constexpr int NP = F8 ? BS : S;  // the ring the MMA reads in pairs
+  constexpr uint32_t kStage = Sp::kStageXtz, kCode = Sp::kCodeXtz, kZBlock = Sp::kZBlock, kZTile = Sp::kZTile;
+  constexpr int kEpiWarps = Sp::kEpiWarps;
+  extern __shared__ unsigned char dyn[];
+  __shared__ uint64_t full[NF], empty[NF], bfull[NB], bempty[NB], zfull[2], zempty[2], acc_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_v;
+  int* const abort_flag = &abort_v;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* base = dyn + ((1024u - (smem_u32(dyn) & 1023u)) & 1023u);
+  unsigned char* bf = base + (size_t)CS * kCode;  // FP8: the BF16 ring after the code ring
+  unsigned char* sZ = base + Sp::kRingXtz;
+  const int64_t ntiles = (a.N + kTR - 1) / kTR;
+  const int64_t t0 = ntiles * blockIdx.x / gridDim.x;
+  const int64_t t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+  const int nch = a.nch;
+  const int ngrp = nch / 2;
+  const uint32_t nq = (uint32_t)((t1 - t0) * nch);
+
+  if (tid == 0) {
+    for (int s = 0; s < NF; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], F8 ? 128 : 1);  // FP8: the converter frees a code stage once it has read it
+    }
+    for (int s = 0; s < NB; ++s) {
+      mbar_init(&bfull[s], 128);
+      mbar_init(&bempty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&zfull[b], 1);
+      mbar_init(&zempty[b], 1);
+    }
+    mbar_init(&acc_done, 1);
+    abort_v = 0;
+    fence_mbar_init();
+  }
+  uint32_t tcols = 32;
+  while (tcols < (uint32_t)(KC * ngrp)) tcols <<= 1;
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tm_xtz = tmem_base;  // columns [KC g, KC (g + 1)): X^T Z of feature group g
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer: the tile's Z^T, then its X chunks ----------------
+    const uint64_t pol = l2_policy_evict_first();
+    uint32_t q = 0;
+    int64_t nz = 0;
+    bool ok = true;
+    for (int64_t t = t0; t < t1 && ok; ++t, ++nz) {
+      const int zb = (int)(nz & 1);
+      if (!(ok = xk_wait(&zempty[zb], ((nz >> 1) & 1) ^ 1, abort_flag, a.err))) break;
+      mbar_arrive_expect_tx(&zfull[zb], kZTile);
+      bulk_g2s(sZ + (size_t)zb * kZTile, static_cast<const unsigned char*>(a.zt) + (size_t)t * kZTile, kZTile,
+               &zfull[zb]);
+      for (int c = 0; c < nch; c += F8 ? 2 : 1, ++q) {  // FP8: a code stage holds two chunks
+        const int s = q % NF;
+        if (!(ok = xk_wait(&empty[s], ((q / NF) & 1) ^ 1, abort_flag, a.err))) break;
+        mbar_arrive_expect_tx(&full[s], F8 ? kFp8PairBytes : kXChunkBytes);
+        tma_load_2d(base + (size_t)s * (F8 ? kCode : kStage), &xmap, c * kCF, (int)(t * kTR), &full[s], pol);
+      }
+    }
+    const uint32_t nd = q < (uint32_t)NF ? q : (uint32_t)NF;
+    for (uint32_t d = 1; d <= nd; ++d) {
+      const uint32_t qq = q - d;
+      mbar_wait(&full[qq % NF], (qq / NF) & 1, 2000000000ull);
+    }
+    for (int64_t d = nz - 1; d >= 0 && d >= nz - 2; --d) mbar_wait(&zfull[d & 1], (d >> 1) & 1, 2000000000ull);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer: pass 2 ----------------
+    const uint32_t id_xtz = idesc_bf16(128, KC, 1, 0);
+    // the two 64-feature atoms of A are consecutive stages of the ring read in pairs
+    const uint32_t pbase = F8 ? smem_u32(bf) : smem_u32(base);
+    constexpr uint32_t pstride = F8 ? kXChunkBytes : kStage;
+    const uint64_t dA0 = sw128_desc(pbase, pstride, 1024);
+    constexpr uint64_t kStep = pstride >> 4;
+    uint32_t q = 0;
+    bool ok = true;
+    for (int64_t n = 0; t0 + n < t1 && ok; ++n) {
+      const int zb = (int)(n & 1);
+      if (!(ok = xk_wait(&zfull[zb], (n >> 1) & 1, abort_flag, a.err))) break;
+      tc_fence_after();
+      const uint32_t zbase = smem_u32(sZ + (size_t)zb * kZTile);
+      for (int g = 0; g < ngrp && ok; ++g) {
+        const int s0 = q % NP;  // even: chunks 2g and 2g+1 sit in stages s0, s0+1
+        uint64_t* const w0 = F8 ? &bfull[s0] : &full[s0];
+        uint64_t* const w1 = F8 ? &bfull[s0 + 1] : &full[s0 + 1];
+        if (!(ok = xk_wait(w0, (q / NP) & 1, abort_flag, a.err))) break;
+        if (!(ok = xk_wait(w1, ((q + 1) / NP) & 1, abort_flag, a.err))) break;
+        tc_fence_after();
+        const uint64_t da = dA0 + kStep * s0;
+        const int acc0 = n > 0 ? 1 : 0;
+#pragma unroll
+        for (int kk = 0; kk < kTR / 16; ++kk) {
+          const uint64_t ad = da + 128 * kk;
+          const uint32_t zo = (uint32_t)(kk / 4) * kZBlock + (uint32_t)(kk % 4) * 32;
+          mma_bf16(tm_xtz + KC * g, ad, sw128_desc(zbase + zo, 16, 1024), id_xtz, kk > 0 ? 1 : acc0);
+          mma_bf16(tm_xtz + KC * g, ad, sw128_desc(zbase + 2 * kZBlock + zo, 16, 1024), id_xtz, 1);
+        }
+        if constexpr (F8) {
+          mma_commit(&bempty[s0]);
+          mma_commit(&bempty[s0 + 1]);
+        } else {
+          mma_commit(&empty[s0]);
+          mma_commit(&empty[s0 + 1]);
+        }
+        q += 2;
+      }
+      if (!ok) break;
+      mma_commit(&zempty[zb]);
+    }
+    mma_commit(&acc_done);
+    mbar_wait(&acc_done, 0, 2000000000ull);  // nothing in flight when the CTA leaves
+  } else if (F8 && warp >= 4 + kEpiWarps) {
+    // ---------------- converter warps: codes -> BF16 ----------------
+    const int ct = tid - 32 * (4 + kEpiWarps);
+    for (uint32_t r = 0; r < nq / 2; ++r) {  // code stage r: chunks 2r, 2r + 1
+      const int s = r % NF, sb = (2 * r) % NB;   // NB even: the pair is sb, sb + 1
+      if (!xk_wait(&full[s], (r / NF) & 1, abort_flag, a.err)) break;
+      if (!xk_wait(&bempty[sb], (((2 * r) / NB) & 1) ^ 1, abort_flag, a.err)) break;
+      if (!xk_wait(&bempty[sb + 1], (((2 * r + 1) / NB) & 1) ^ 1, abort_flag, a.err)) break;
+      cvt_pair_fp8(base + (size_t)s * kCode, bf + (size_t)sb * kXChunkBytes, bf + (size_t)(sb + 1) * kXChunkBytes,
+                   ct);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic accesses before async-proxy ones
+      mbar_arrive(&empty[s]);  // the codes have been read
+      mbar_arrive(&bfull[sb]);
+      mbar_arrive(&bfull[sb + 1]);
+    }
+  } else if (warp >= 4 && warp < 4 + kEpiWarps) {
+    // ---------------- the CTA's X^T Z partial ----------------
+    const int quad = warp & 3, part = (warp - 4) >> 2;
+    const int er = 32 * quad + lane;
+    const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
+    if (xk_wait(&acc_done, 0, abort_flag, a.err)) {
+      tc_fence_after();
+      for (int g = part; g < ngrp; g += kEpiWarps / 4) {
+        uint32_t r[KC];
+        if constexpr (KC == 32) tmem_ld32(tm_xtz + KC * g + lane_off, r);
+        else tmem_ld16(tm_xtz + KC * g + lane_off, r);
+        tmem_ld_wait();
+        const int f = 128 * g + er;
+        float* out = a.partials + ((size_t)blockIdx.x * a.fpad + f) * KC;
+#pragma unroll
+        for (int m = 0; m < KC; m += 4)
+          *reinterpret_cast<float4*>(out + m) = make_float4(__uint_as_float(r[m]), __uint_as_float(r[m + 1]),
+                                                            __uint_as_float(r[m + 2]), __uint_as_float(r[m + 3]));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm_xtz), "r"(tcols));
+  }
+}
+
 // B^T in the shared-memory layout of pass 1: chunk c holds features 64c..64c+63
-// of 2 KC rows (rows 0..KC-1: BF16 high parts of the K chains' beta (scaled
-// to the stored X), rows KC..2KC-1: the low parts beta - hi), 128-byte swizzled.
+// of 2 KC rows (rows 0..KC-1: BF16 high parts of the K chains' beta (times
+// the column scale of FP8 X, so that the codes multiply it), rows
+// KC..2KC-1: the low parts beta - hi), 128-byte swizzled.
 __global__ void bsw_prep_kernel(const double* __restrict__ beta, int64_t beta_stride, int K, int p, int nch, int kc,
-                                unsigned char* __restrict__ bsw) {
+                                const float* __restrict__ colscale, unsigned char* __restrict__ bsw) {
   const int rows = 2 * kc;
   const int64_t n_el = (int64_t)nch * rows * kCF;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
@@ -502,7 +986,7 @@ __global__ void bsw_prep_kernel(const double* __restrict__ beta, int64_t beta_st
     const int m = n % kc, f = c * kCF + k;
     float v = 0.0f;
     if (m < K && f < p) {
-      const double b = beta[(int64_t)m * beta_stride + f];
+      const double b = beta[(int64_t)m * beta_stride + f] * (colscale ? (double)colscale[f] : 1.0);
       const __nv_bfloat16 h = __float2bfloat16_rn((float)b);
       v = n < kc ? __bfloat162float(h) : (float)(b - (double)__bfloat162float(h));
     }
@@ -516,7 +1000,7 @@ __global__ void bsw_prep_kernel(const double* __restrict__ beta, int64_t beta_st
 // index mod 4) are added in a fixed order at the end.
 template <int KC>
 __global__ void reduce_k_kernel(const float* __restrict__ part, int grid, int fpad, int p, int K,
-                                double* __restrict__ xtz, int64_t xtz_stride) {
+                                const float* __restrict__ colscale, double* __restrict__ xtz, int64_t xtz_stride) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = e / KC, m = e % KC;
   if (j >= p) return;
@@ -531,7 +1015,7 @@ __global__ void reduce_k_kernel(const float* __restrict__ part, int grid, int fp
     s3 += (double)__ldg(col + (size_t)(c + 3) * cs);
   }
   for (; c < grid; ++c) s0 += (double)__ldg(col + (size_t)c * cs);
-  if (m < K) xtz[(int64_t)m * xtz_stride + j] = (s0 + s1) + (s2 + s3);
+  if (m < K) xtz[(int64_t)m * xtz_stride + j] = ((s0 + s1) + (s2 + s3)) * (colscale ? (double)colscale[j] : 1.0);
 }
 
 }  // namespace
@@ -618,6 +1102,90 @@ int xstream_k_make_map(const void* X, int64_t N, int ld, void* map_out) {
   return r == CUDA_SUCCESS ? 0 : -1;
 }
 
+namespace {
+template <class F>
+bool with_split(int kc, int fp8, F&& f) {
+  if (kc == 16 && !fp8) f(std::integral_constant<int, 16>{}, std::integral_constant<int, 0>{});
+  else if (kc == 16 && fp8) f(std::integral_constant<int, 16>{}, std::integral_constant<int, 1>{});
+  else if (kc == 32 && !fp8) f(std::integral_constant<int, 32>{}, std::integral_constant<int, 0>{});
+  else if (kc == 32 && fp8) f(std::integral_constant<int, 32>{}, std::integral_constant<int, 1>{});
+  else return false;
+  return true;
+}
+}  // namespace
+
+bool xstream_k_split_supported(int p, int kc) {
+  // pass 2's TMEM: KC columns per 128-feature group
+  return p >= 1 && (kc == 16 || kc == 32) && kc * (xstream_k_chunks(p) / 2) <= 512;
+}
+
+cudaError_t xstream_k_split_prepare(int kc, int fp8) {
+  cudaError_t e = cudaErrorInvalidValue;
+  with_split(kc, fp8, [&](auto KC, auto F) {
+    constexpr int c = decltype(KC)::value, f8 = decltype(F)::value;
+    using Sp = XKSplit<c, f8>;
+    e = cudaFuncSetAttribute((const void*)xk_eta_kernel<c, f8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Sp::kSmemEta);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)xk_xtz_kernel<c, f8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)Sp::kSmemXtz);
+  });
+  return e;
+}
+
+int xstream_k_split_stages(int kc) { return kc == 16 ? XKSplit<16, 0>::kStages : XKSplit<32, 0>::kStages; }
+
+size_t xstream_k_zt_bytes(int64_t N, int kc) { return (size_t)((N + kTR - 1) / kTR) * 4 * (size_t)kc * 128; }
+
+cudaError_t xstream_k_split_enqueue(const void* map, const XKArgs& a, const double* beta, int64_t beta_stride,
+                                    unsigned char* bsw, int grid, cudaStream_t s) {
+  if (a.K > a.kc || !a.zt) return cudaErrorInvalidValue;
+  bsw_prep_kernel<<<64, 256, 0, s>>>(beta, beta_stride, a.K, a.p, a.nch, a.kc, a.colscale, bsw);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap m;
+  memcpy(&m, map, sizeof(m));
+  e = cudaErrorInvalidValue;
+  with_split(a.kc, a.fp8, [&](auto KC, auto F) {
+    constexpr int c = decltype(KC)::value, f8 = decltype(F)::value;
+    using Sp = XKSplit<c, f8>;
+    xk_eta_kernel<c, f8><<<grid, Sp::kThreads, Sp::kSmemEta, s>>>(m, a);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      xk_xtz_kernel<c, f8><<<grid, Sp::kThreads, Sp::kSmemXtz, s>>>(m, a);
+      e = cudaGetLastError();
+    }
+  });
+  return e;
+}
+
+int xstream_k_make_map_fp8(const void* X, int64_t N, int ld, void* map_out) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult qr;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess || !fn)
+      return -1;
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  // rows of ld one-byte codes (ld a multiple of 16); boxes of 128 codes x 128
+  // rows (two 64-feature chunks, whole 128-byte lines of each row), no
+  // swizzle (the converter warps read the rows); reads outside X return zeros
+  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)N};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * kCF), (cuuint32_t)kTR};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                            const_cast<void*>(X), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
+}
+
 int xstream_k_grid(int64_t N, int num_sms) {
   const int64_t ntiles = (N + kTR - 1) / kTR;
   int64_t g = num_sms > 1 ? (int64_t)num_sms - 1 : 1;
@@ -634,7 +1202,7 @@ size_t xstream_k_partial_floats(int p, int grid, int kc) {
 cudaError_t xstream_k_enqueue(const void* map, const XKArgs& a, const double* beta, int64_t beta_stride,
                               unsigned char* bsw, int grid, cudaStream_t s) {
   if (a.K > a.kc) return cudaErrorInvalidValue;
-  bsw_prep_kernel<<<64, 256, 0, s>>>(beta, beta_stride, a.K, a.p, a.nch, a.kc, bsw);
+  bsw_prep_kernel<<<64, 256, 0, s>>>(beta, beta_stride, a.K, a.p, a.nch, a.kc, nullptr, bsw);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap m;
@@ -650,9 +1218,11 @@ cudaError_t xstream_k_enqueue(const void* map, const XKArgs& a, const double* be
 
 cudaError_t xstream_k_reduce(const XKArgs& a, int grid, double* xtz, int64_t xtz_stride, cudaStream_t s) {
   if (a.kc == 16)
-    reduce_k_kernel<16><<<(a.p * 16 + 255) / 256, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, xtz, xtz_stride);
+    reduce_k_kernel<16><<<(a.p * 16 + 255) / 256, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, a.colscale, xtz,
+                                                                xtz_stride);
   else if (a.kc == 32)
-    reduce_k_kernel<32><<<(a.p * 32 + 255) / 256, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, xtz, xtz_stride);
+    reduce_k_kernel<32><<<(a.p * 32 + 255) / 256, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, a.colscale, xtz,
+                                                                xtz_stride);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

@@ -143,21 +143,22 @@ def test_chains_without_tensor_core_xstream_match_oracle(pkg, dt, N, p, K, tol):
         assert_transition_close(got[m], ref, tol)
 
 
-def test_bf16_chains_past_the_tensor_core_tmem_budget_match_oracle(pkg):
-    """K = 20 chains need 32 chain columns, whose TMEM budget ends at p = 1536:
-    p = 1600 takes the per-chain X-stream, still at the BF16 bound."""
-    N, p, K = 3001, 1600, 20
-    d = problem(N, p, 5, "bf16", seed=4)
+@pytest.mark.parametrize("N,p,K", [(3001, 1600, 20), (4099, 4000, 4), (1000, 2048, 32)])
+def test_bf16_chains_past_the_fused_kernels_tmem_budget_match_oracle(pkg, N, p, K):
+    """Past the fused kernel's TMEM budget (p = 1536 at 32 chain columns,
+    3584 at 16) the tensor-core X-stream runs as two kernels, pass 1 writing
+    Z^T for pass 2; each chain stays within the batched form's BF16 bound."""
+    d = problem(N, p, 5, "bf16", seed=p % 13)
     X = x_f64(d)
     G = oracle.gram(X)
-    states = [random_state(p, k=2, seed=400 + m) for m in range(K)]
+    states = [random_state(p, k=2, seed=400 + m, scale=0.2) for m in range(K)]
     s = pkg.HSProbit(d["X"], d["y"], seed=1, num_chains=K)
-    assert s.launch_shape()["xk_chains"] == 0  # no tensor-core X-stream
+    assert s.launch_shape()["xk_chains"] == (16 if K <= 16 else 32)
     s.close()
     got = _batched_transitions(pkg, d, states, seed=13)
     for m, st in enumerate(states):
         ref = oracle.sweep_once(st.copy(), X, d["y"], G, 13, chain=m, keep=True)
-        assert_transition_close(got[m], ref, 1e-4)
+        assert_batched_close(got[m], ref, X, st.beta)
 
 
 def test_batched_long_run_moments_match_oracle_within_mc_error(pkg):
@@ -283,9 +284,10 @@ def test_tensor_core_trailing_updates_match_pair_arithmetic(pkg, dt, N, p, K):
 def test_eight_chains_on_fp8_correlated_design_at_p_4000(pkg):
     """The large correlated workload's shape with its K = 8 chains at a size
     the oracle runs in seconds: FP8 e4m3 X with column scales, AR(1) rows,
-    p = 4000, 20 nonzeros U[0.5, 2].  Each chain takes a one-chain FP8 pass
-    (FP32 accumulation) and the block-column factorization; every chain must
-    reproduce the oracle's transition at the FP32 tolerance."""
+    p = 4000, 20 nonzeros U[0.5, 2].  The X-stream runs on the tensor cores
+    as two kernels, the FP8 codes converted to BF16 in shared memory (exact)
+    and the column scales folded into B^T and X^T Z; every chain must stay
+    within the batched form's BF16 bound of the oracle's transition."""
     N, p, K = 3000, 4000, 8
     d = problem(N, p, 20, "fp8", seed=5, mag=(0.5, 2.0), design="ar1")
     X = x_f64(d)
@@ -306,4 +308,28 @@ def test_eight_chains_on_fp8_correlated_design_at_p_4000(pkg):
         s.close()
     for m, st in enumerate(states):
         ref = oracle.sweep_once(st.copy(), X, d["y"], G, 29, chain=m, keep=True)
-        assert_transition_close(got[m], ref, 1e-4)
+        assert_batched_close(got[m], ref, X, st.beta)
+
+
+@pytest.mark.parametrize("N,p,K", [(3001, 300, 4), (2000, 1000, 24)])
+def test_fp8_chains_on_the_tensor_cores_match_oracle(pkg, N, p, K):
+    """FP8 X with column scales and K chains at sizes the fused kernel would
+    take for BF16: the split form at 16 and 32 chain columns."""
+    d = problem(N, p, 5, "fp8", seed=K)
+    X = x_f64(d)
+    G = oracle.gram(X)
+    states = [random_state(p, k=4, seed=700 + m, scale=0.2) for m in range(K)]
+    s = pkg.HSProbit(d["X"], d["y"], seed=31, scales=d["scales"], debug=True, num_chains=K)
+    try:
+        assert s.launch_shape()["xk_chains"] == (16 if K <= 16 else 32)
+        for m, st in enumerate(states):
+            s.set_state(st.beta, st.lam_inv2, st.nu_inv, st.tau_inv2, st.xi_inv, st.k, chain=m)
+        s.sweep(1)
+        for m, st in enumerate(states):
+            g = s.get_state(chain=m)
+            g["z"] = s.debug_z(chain=m)
+            g["xtz"] = s.debug_xtz(chain=m)
+            ref = oracle.sweep_once(st.copy(), X, d["y"], G, 31, chain=m, keep=True)
+            assert_batched_close(g, ref, X, st.beta)
+    finally:
+        s.close()
