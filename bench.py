@@ -46,6 +46,9 @@ WORKLOADS = {
     "c4": dict(N=4_000_000, p=4000, nz=20, dt="fp8", design="ar1", mag=(0.5, 2.0),
                name="horseshoe-probit sweep, N=4e6, p=4000, X rows N(0, Toeplitz 0.5^|i-j|) fp8 e4m3 with column "
                     "scales (16 GB), 20 nonzeros U[0.5,2], 1 chain"),
+    "c4s": dict(N=200_000, p=4000, nz=20, dt="fp8", design="ar1", mag=(0.5, 2.0),
+                name="horseshoe-probit sweep, N=2e5, p=4000, X rows N(0, Toeplitz 0.5^|i-j|) fp8 e4m3 with column "
+                     "scales (profiling case, 800 MB)"),
 }
 UNEVEN = dict(n=64, N=(10_000, 200_000), p=(50, 2000), K=4, dt="bf16", nz_frac=0.01,
               name="uneven multi-problem batch: 64 probit problems, N log-uniform [1e4, 2e5], p log-uniform "
@@ -465,6 +468,7 @@ def run_uneven_batch(args, pkg, torch, dist, ws, rank, local, chol):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees these sweeps only
     with ClockSampler(local) as clk:
         clk.mark(True)
         e0.record(root)
@@ -472,6 +476,7 @@ def run_uneven_batch(args, pkg, torch, dist, ws, rank, local, chol):
         e1.record(root)
         torch.cuda.synchronize()
         clk.mark(False)
+    torch.cuda.profiler.stop()
     barrier(dist)
     ms = max_over_ranks(dist, e0.elapsed_time(e1))
     ms_sweep = ms / args.c3_steps
@@ -527,6 +532,61 @@ def run_uneven_batch(args, pkg, torch, dist, ws, rank, local, chol):
             "gpu_launches_per_sweep": launches, "init_s": t_init, "gen_s": t_gen, "clocks": clk.summary()}
 
 
+def run_c3_line(args, dist, rank, ws, local):
+    """``--workload c3``: the uneven batch alone, as its own bench line (our
+    arm), or the oracle on a bounded sample of its problems (reference arm)."""
+    import hs_synth
+    u = UNEVEN
+    metric = "chain-sweeps/s of the uneven 64-problem batch (K = 4 each)"
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        import oracle
+        sizes = hs_synth.uneven_sizes(u["n"], u["N"], u["p"], seed=0)
+        done, t, used = 0, 0.0, 0
+        for m, (N, p) in enumerate(sizes):
+            if t >= args.ref_budget:
+                break
+            d = hs_synth.make_problem(N, p, max(1, round(u["nz_frac"] * p)), u["dt"], seed=1000 + m)
+            X = oracle.fmt.stored_to_f64(d["X"], d["x_dtype"], d["scales"])
+            G = oracle.gram(X)  # untimed, as the library's init
+            for c in range(u["K"]):
+                st = oracle.init_state(p)
+                t0 = time.perf_counter()
+                oracle.sweep_once(st, X, d["y"], G, 0, chain=c, problem=m)
+                t += time.perf_counter() - t0
+                done += 1
+            used += 1
+        rate = done / t
+        line = {"metric": metric, "value": rate, "unit": "chain-sweeps/s", "n_gpus": 0, "steps": done,
+                "warmup": 0, "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": u["name"]}, "impl": "reference",
+                "cpu_baseline": {"value": rate, "unit": "chain-sweeps/s", "cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": f"one FP64 oracle sweep of each of the {u['K']} chains of the first "
+                                           f"{used} problems (Gram untimed), within {args.ref_budget:.0f} s"},
+                "e2e": {"value": rate, "unit": "chain-sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+    import torch
+    import paper_1608_04329_gb300 as pkg
+    pkg.load_library()
+    torch.cuda.set_device(local)
+    chol = pkg.CHOL_F64 if args.chol == "f64" else pkg.CHOL_DF32
+    c3 = run_uneven_batch(args, pkg, torch, dist, ws, rank, local, chol)
+    if rank == 0:
+        line = {"metric": metric, "value": c3["value"], "unit": c3["unit"], "n_gpus": ws, "steps": c3["steps"],
+                "warmup": c3["warmup"], "ms_per_step": c3["ms_per_sweep"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": c3["workload"], "l2": "inputs larger than L2 (2.9 GB of X), no flush"},
+                "roofline": c3["roofline"], "e2e": c3["e2e"], "gpu_launches": c3["gpu_launches_per_sweep"] * c3["steps"],
+                "clocks": c3["clocks"], "uneven_batch": c3}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_tn_compare(d, pkg, torch, local, reps=20):
     """The latent draw alone, both samplers, on this workload's mu* = y* x_i beta_true
     (N draws): time per launch (CUDA events), proposals per draw, and how long a
@@ -564,7 +624,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS) + ["c3"],
+                    help="c3: the uneven multi-problem batch alone")
     ap.add_argument("--graph", type=int, default=1)
     ap.add_argument("--chol", default="df32", choices=["f64", "df32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -587,8 +648,10 @@ def main(argv=None):
     if args.traffic_from:
         print(json.dumps(write_traffic_record(args.traffic_from, args.workload, args.traffic_command)))
         return 0
-    wl = WORKLOADS[args.workload]
     dist, rank, ws, local = _dist()
+    if args.workload == "c3":
+        return run_c3_line(args, dist, rank, ws, local)
+    wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         rc = run_reference(args, wl, dist, rank)
         if dist is not None:
@@ -682,7 +745,7 @@ def main(argv=None):
 
     # ---- K chains on BF16 X (tensor-core X-stream), same N and p ----
     kch = None
-    if wl is WORKLOADS["c4"] and args.c4_chains > 1:
+    if args.workload in ("c4", "c4s") and args.c4_chains > 1:
         # the large correlated workload's own K chains on its FP8 X
         kch = run_k_chains(args, wl, pkg, torch, dist, ws, rank, local, chol, value, dk=d, K=args.c4_chains)
     elif args.k_chains > 1:

@@ -537,8 +537,11 @@ struct XKSplit {
 // FP8 e4m3 codes of two chunks (128 rows of 128 bytes) -> BF16 in the
 // 128-byte-swizzled K-major layout of the MMA, features 0-63 into dst0 and
 // 64-127 into dst1.  Thread t (0..127) takes the 16-byte granules t + 128 j
-// (row G / 8, features 16 (G % 8) ..), so a warp reads 512 contiguous bytes
-// per load and each 16-byte store of a warp fills whole 128-byte wavefronts.
+// (row G / 8, features 16 (G % 8) ..), so eight consecutive lanes read one
+// 128-byte row.  Each granule gives two 16-byte outputs; the lanes writing
+// dst1 store theirs in the opposite order, so the eight lanes of a quarter
+// warp hit eight different swizzled granules (dst0 and dst1 are 16 KB apart,
+// on the same banks) and no store conflicts.
 __device__ __forceinline__ void cvt_pair_fp8(const unsigned char* src, unsigned char* dst0, unsigned char* dst1,
                                              int t) {
 #pragma unroll
@@ -561,8 +564,10 @@ __device__ __forceinline__ void cvt_pair_fp8(const unsigned char* src, unsigned 
         o[2 * i + h] = *reinterpret_cast<const uint32_t*>(&b2);
       }
     }
-    *reinterpret_cast<uint4*>(dst + sw128_off(row, f0)) = make_uint4(o[0], o[1], o[2], o[3]);
-    *reinterpret_cast<uint4*>(dst + sw128_off(row, f0 + 8)) = make_uint4(o[4], o[5], o[6], o[7]);
+    const uint4 lo = make_uint4(o[0], o[1], o[2], o[3]), hi = make_uint4(o[4], o[5], o[6], o[7]);
+    const bool up = c16 >= 4;
+    *reinterpret_cast<uint4*>(dst + sw128_off(row, up ? f0 + 8 : f0)) = up ? hi : lo;
+    *reinterpret_cast<uint4*>(dst + sw128_off(row, up ? f0 : f0 + 8)) = up ? lo : hi;
   }
 }
 
