@@ -88,6 +88,24 @@ def test_one_chain_f32_batch_matches_oracle(pkg):
         assert_transition_close(got[m][0], ref, 1e-4)
 
 
+def test_fp8_batch_with_column_scales_matches_oracle(pkg):
+    """Uneven FP8 problems, each with its own column scales (hs_problem.x_scales),
+    two chains each: the two-pass tensor-core X-stream per problem."""
+    sizes = [(3001, 130), (5000, 700), (700, 16)]
+    ds = _make(sizes, "fp8", 60)
+    b = pkg.HSProbitBatch([(d["X"], d["y"], d["scales"]) for d in ds], seed=7, num_chains=2, debug=True)
+    try:
+        states, got = _batch_transitions(b, ds, 2, 1100)
+    finally:
+        b.close()
+    for m, d in enumerate(ds):
+        X = x_f64(d)
+        G = oracle.gram(X)
+        for c in range(2):
+            ref = oracle.sweep_once(states[m][c].copy(), X, d["y"], G, 7, chain=c, problem=m, keep=True)
+            assert_batched_close(got[m][c], ref, X, states[m][c].beta)
+
+
 def test_batch_runs_many_sweeps_and_tuner_restores_state(pkg):
     ds = _make(UNEVEN, "bf16", 7)
     b = pkg.HSProbitBatch([(d["X"], d["y"]) for d in ds], seed=5, num_chains=4, ring_size=16)
