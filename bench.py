@@ -521,7 +521,10 @@ def run_uneven_batch(args, pkg, torch, dist, ws, rank, local, chol):
                          "cuda_core_pair_fma": pair_fmas, "tensor_flop": tflop, "alu_peak": alu_src,
                          "tensor_peak": f"{tc_src} cuBLAS bf16 {tc_peak / 1e12:.0f} TFLOP/s",
                          "note": "floors of the three units; each problem's block columns run one after "
-                                 "another, so latency, not any floor, is what the sweep meets"},
+                                 "another, so latency, not any floor, is what the sweep meets",
+                         # context: the same factorizations as native FP64 Cholesky (sum K p^3 / 3 FMAs)
+                         # on GB300's FP64 pipe at its nominal 1.25 TFLOP/s
+                         "fp64_pipe_ms": sum(u["K"] * 2.0 * float(p) ** 3 / 3.0 for _, p in sizes) / 1.25e12 * 1e3},
             "tuner": {"best_ms_per_sweep": best, "trials": trials, "tune_s": t_tune,
                       "xk_chains": sorted({sh["xk_chains"] for sh in shapes}),
                       "xk_stages": sorted({sh["xk_stages"] for sh in shapes})},

@@ -333,3 +333,71 @@ def test_fp8_chains_on_the_tensor_cores_match_oracle(pkg, N, p, K):
             assert_batched_close(g, ref, X, st.beta)
     finally:
         s.close()
+
+
+def _posterior_means(pkg, X_store, y, scales, warm, seed, n, K, **kw):
+    s = pkg.HSProbit(X_store, y, seed=seed, scales=scales, num_chains=K, ring_size=n, **kw)
+    try:
+        for m in range(K):
+            s.set_state(warm["beta"], warm["lambda_inv2"], warm["nu_inv"], warm["tau_inv2"], warm["xi_inv"], 0,
+                        chain=m)
+        s.sweep(n)
+        return [s.draws(chain=m)["beta"] for m in range(K)]
+    finally:
+        s.close()
+
+
+def test_fp8_chains_posterior_mean_error_vs_fp64_oracle():
+    """The large correlated workload's form (FP8 X with column scales, AR(1)
+    rows, K = 8 chains on the two-pass tensor-core X-stream) at a size the
+    oracle runs in seconds (N = 2e4, p = 300): coupled chains (same seed and
+    chain ids) from one warm state, 250 sweeps; the posterior mean of beta is
+    within 1e-3 of the FP64 oracle's on the same stored X."""
+    pkg = lib_pkg()
+    N, p, seed, n, K = 20000, 300, 9, 250, 8
+    d = problem(N, p, 5, "fp8", seed=41, mag=(0.5, 2.0), design="ar1")
+    X = x_f64(d)
+    G = oracle.gram(X)
+    w = oracle.init_state(p)
+    for _ in range(400):
+        w = oracle.sweep_once(w, X, d["y"], G, seed, chain=100)
+    warm = {"beta": w.beta, "lambda_inv2": w.lam_inv2, "nu_inv": w.nu_inv, "tau_inv2": w.tau_inv2,
+            "xi_inv": w.xi_inv}
+    w.k = 0
+    gpu = _posterior_means(pkg, d["X"], d["y"], d["scales"], warm, seed, n, K)
+    ora = [oracle.run(w.copy(), X, d["y"], G, seed, n, chain=m)[1] for m in range(K)]
+    m_gpu = np.mean([g.mean(0) for g in gpu], axis=0)
+    m_ora = np.mean([o.mean(0) for o in ora], axis=0)
+    err = np.abs(m_gpu - m_ora).max()
+    se = (np.stack([g.mean(0) for g in gpu]).std(0, ddof=1) / np.sqrt(K)).max()
+    print(f"posterior-mean error of {K} FP8 chains: max |dbeta| = {err:.3e} against the FP64 oracle on the stored "
+          f"X ({n} coupled sweeps); Monte Carlo standard error of the estimate {se:.3e}")
+    assert err <= 1e-3, err
+
+
+def test_fp8_chains_posterior_mean_error_vs_fp64_x_at_p_4000():
+    """At the large workload's p = 4000 (N = 2e5, where the oracle is too slow
+    for long runs) the reference is the library's FP64-X path, itself held to
+    the oracle's transition at 1e-10: the same stored values as FP64 X (one
+    FP64 X-stream pass per chain), the same seed, chain ids and warm state.
+    The posterior means of the K = 8 FP8 chains over 150 coupled sweeps stay
+    within 1e-3 of it."""
+    pkg = lib_pkg()
+    N, p, seed, n, K = 200_000, 4000, 3, 150, 8
+    d = problem(N, p, 20, "fp8", seed=5, mag=(0.5, 2.0), design="ar1")
+    X = x_f64(d)
+    ref0 = pkg.HSProbit(X, d["y"], seed=seed, chain=100)
+    try:
+        ref0.sweep(100)
+        warm = ref0.get_state()
+    finally:
+        ref0.close()
+    fp64 = _posterior_means(pkg, X, d["y"], None, warm, seed, n, K)
+    fp8 = _posterior_means(pkg, d["X"], d["y"], d["scales"], warm, seed, n, K)
+    m64 = np.mean([g.mean(0) for g in fp64], axis=0)
+    m8 = np.mean([g.mean(0) for g in fp8], axis=0)
+    err = np.abs(m8 - m64).max()
+    se = (np.stack([g.mean(0) for g in fp64]).std(0, ddof=1) / np.sqrt(K)).max()
+    print(f"posterior-mean error of {K} FP8 chains at N = {N}, p = {p}: max |dbeta| = {err:.3e} against the "
+          f"FP64-X path ({n} coupled sweeps); Monte Carlo standard error {se:.3e}")
+    assert err <= 1e-3, err
