@@ -847,6 +847,32 @@ __device__ __forceinline__ void block_publish(unsigned long long* p, unsigned lo
 // Tile moves of data other blocks write during this launch go through L2.
 // Up to three tiles per call, all global loads issued before the shared
 // stores; 16-byte accesses (two FP32 pairs); blockDim.x must be 256.
+// Tile traffic of the factorization through L2 with an evict-last policy: the
+// working set (a few P x P pair matrices) is small against L2, while the
+// X-stream beside it streams X through L2 with an evict-first policy.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float4 ld_keep(const float4* a, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(a), "l"(pol)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_keep(float4* a, float4 v, uint64_t pol) {
+  asm volatile("st.global.cg.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st_keep2(float2* a, float2 v, uint64_t pol) {
+  asm volatile("st.global.cg.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol)
+               : "memory");
+}
+
 struct TileRef {
   const df2* M;
   int ti, tj;
@@ -855,13 +881,15 @@ struct TileRef {
 };
 template <int NT>
 __device__ __forceinline__ void tiles_load_cg(const TileRef (&t)[NT], int P) {
+  const uint64_t pol = l2_keep_policy();
   float4 v[NT][2];
 #pragma unroll
   for (int n = 0; n < NT; ++n)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int e = threadIdx.x + h * 256, r = e >> 4, c = (e & 15) * 2;
-      v[n][h] = __ldcg(reinterpret_cast<const float4*>(t[n].M + (size_t)(t[n].ti * NB + r) * P + t[n].tj * NB + c));
+      v[n][h] = ld_keep(reinterpret_cast<const float4*>(t[n].M + (size_t)(t[n].ti * NB + r) * P + t[n].tj * NB + c),
+                        pol);
     }
 #pragma unroll
   for (int n = 0; n < NT; ++n)
@@ -879,12 +907,14 @@ __device__ __forceinline__ void tiles_load_cg(const TileRef (&t)[NT], int P) {
     }
 }
 __device__ __forceinline__ void tile_store_cg(df2* M, int P, int ti, int tj, const df2 (*T)[NB + 1], bool transposed) {
+  const uint64_t pol = l2_keep_policy();
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int e = threadIdx.x + h * 256, r = e >> 4, c = (e & 15) * 2;
     const df2 x0 = transposed ? T[c][r] : T[r][c];
     const df2 x1 = transposed ? T[c + 1][r] : T[r][c + 1];
-    __stcg(reinterpret_cast<float4*>(M + (size_t)(ti * NB + r) * P + tj * NB + c), make_float4(x0.hi, x0.lo, x1.hi, x1.lo));
+    st_keep(reinterpret_cast<float4*>(M + (size_t)(ti * NB + r) * P + tj * NB + c),
+            make_float4(x0.hi, x0.lo, x1.hi, x1.lo), pol);
   }
 }
 
@@ -913,13 +943,15 @@ struct Grp {
 
 template <int NT>
 __device__ __forceinline__ void gload_cg(const Grp& g, const TileRef (&t)[NT], int P) {
+  const uint64_t pol = l2_keep_policy();
   float4 v[NT][4];
 #pragma unroll
   for (int n = 0; n < NT; ++n)
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       const int e = g.t + h * 128, r = e >> 4, c = (e & 15) * 2;
-      v[n][h] = __ldcg(reinterpret_cast<const float4*>(t[n].M + (size_t)(t[n].ti * NB + r) * P + t[n].tj * NB + c));
+      v[n][h] = ld_keep(reinterpret_cast<const float4*>(t[n].M + (size_t)(t[n].ti * NB + r) * P + t[n].tj * NB + c),
+                        pol);
     }
 #pragma unroll
   for (int n = 0; n < NT; ++n)
@@ -948,12 +980,14 @@ __device__ __forceinline__ void gzero(const Grp& g, df2 (*T)[NB + 1]) {
 }
 __device__ __forceinline__ void gstore_cg(const Grp& g, df2* M, int P, int ti, int tj, const df2 (*T)[NB + 1],
                                           bool transposed) {
+  const uint64_t pol = l2_keep_policy();
 #pragma unroll
   for (int h = 0; h < 4; ++h) {
     const int e = g.t + h * 128, r = e >> 4, c = (e & 15) * 2;
     const df2 x0 = transposed ? T[c][r] : T[r][c];
     const df2 x1 = transposed ? T[c + 1][r] : T[r][c + 1];
-    __stcg(reinterpret_cast<float4*>(M + (size_t)(ti * NB + r) * P + tj * NB + c), make_float4(x0.hi, x0.lo, x1.hi, x1.lo));
+    st_keep(reinterpret_cast<float4*>(M + (size_t)(ti * NB + r) * P + tj * NB + c),
+            make_float4(x0.hi, x0.lo, x1.hi, x1.lo), pol);
   }
 }
 // C = As Bt (set) or C -= As Bt (sub), Bt[q][c]; thread: rows ty + 8i, columns tx, tx + 16.
@@ -1016,6 +1050,7 @@ __device__ __forceinline__ void gmma(const Grp& g, df2 (*C)[NB + 1], const df2 (
 // Thread: rows ty + 8i, columns tx, tx + 16; rows >= rows are padding.
 __device__ __forceinline__ void gmma_update_store(const Grp& g, const df2 (*W)[NB + 1], const df2 (*As)[NB + 1],
                                                   const df2 (*Bs)[NB + 1], int rows, df2* M, int P, int ti, int tj) {
+  const uint64_t pol = l2_keep_policy();
   const int tx = g.t & 15, ty = g.t >> 4;
   const int ni = rows > ty ? (rows - ty + 7) >> 3 : 0;
   float h[4][2], l[4][2];
@@ -1054,7 +1089,8 @@ __device__ __forceinline__ void gmma_update_store(const Grp& g, const df2 (*W)[N
     for (int j = 0; j < 2; ++j) {
       const int r = ty + 8 * i, c = tx + 16 * j;
       const df2 v = df_sub(W[r][c], df_renorm(h[i][j], l[i][j]));
-      __stcg(reinterpret_cast<float2*>(M + (size_t)(ti * NB + r) * P + tj * NB + c), make_float2(v.hi, v.lo));
+      st_keep2(reinterpret_cast<float2*>(M + (size_t)(ti * NB + r) * P + tj * NB + c), make_float2(v.hi, v.lo),
+               pol);
     }
 }
 // Thread 0 of the group waits for every *p[n] >= target[n] (one relaxed read of
