@@ -1000,27 +1000,39 @@ __global__ void bsw_prep_kernel(const double* __restrict__ beta, int64_t beta_st
 }
 
 // X^T z of chain m, feature j: fixed-order FP64 sum over the CTAs' partials.
-// Thread (j, m): consecutive lanes run over the KC chains of one feature, so
-// each CTA's partial row is read as whole lines; four accumulators (CTA
-// index mod 4) are added in a fixed order at the end.
+// One block per feature, 256 threads = KC chains x (256 / KC) groups: thread
+// (g, m) adds the partial rows of CTAs g, g + G, g + 2G, ... (each warp reads
+// whole lines of consecutive chains) in four interleaved accumulators, then
+// the G group sums are added in group order, so the result is the same every
+// sweep.
 template <int KC>
-__global__ void reduce_k_kernel(const float* __restrict__ part, int grid, int fpad, int p, int K,
-                                const float* __restrict__ colscale, double* __restrict__ xtz, int64_t xtz_stride) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = e / KC, m = e % KC;
-  if (j >= p) return;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+__global__ void __launch_bounds__(256) reduce_k_kernel(const float* __restrict__ part, int grid, int fpad, int p, int K,
+                                                       const float* __restrict__ colscale, double* __restrict__ xtz,
+                                                       int64_t xtz_stride) {
+  constexpr int G = 256 / KC;
+  __shared__ double s_grp[G][KC];
+  const int j = blockIdx.x;
+  const int m = threadIdx.x % KC, g = threadIdx.x / KC;
   const float* col = part + (size_t)j * KC + m;
   const size_t cs = (size_t)fpad * KC;
-  int c = 0;
-  for (; c + 3 < grid; c += 4) {
-    s0 += (double)__ldg(col + (size_t)c * cs);
-    s1 += (double)__ldg(col + (size_t)(c + 1) * cs);
-    s2 += (double)__ldg(col + (size_t)(c + 2) * cs);
-    s3 += (double)__ldg(col + (size_t)(c + 3) * cs);
+  // four accumulators (the group's CTAs taken round-robin), added in a fixed order
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int c = g;
+  for (; c + 3 * G < grid; c += 4 * G) {
+    a0 += (double)__ldg(col + (size_t)c * cs);
+    a1 += (double)__ldg(col + (size_t)(c + G) * cs);
+    a2 += (double)__ldg(col + (size_t)(c + 2 * G) * cs);
+    a3 += (double)__ldg(col + (size_t)(c + 3 * G) * cs);
   }
-  for (; c < grid; ++c) s0 += (double)__ldg(col + (size_t)c * cs);
-  if (m < K) xtz[(int64_t)m * xtz_stride + j] = ((s0 + s1) + (s2 + s3)) * (colscale ? (double)colscale[j] : 1.0);
+  for (; c < grid; c += G) a0 += (double)__ldg(col + (size_t)c * cs);
+  s_grp[g][m] = (a0 + a1) + (a2 + a3);
+  __syncthreads();
+  if (g == 0 && m < K) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < G; ++q) t += s_grp[q][m];
+    xtz[(int64_t)m * xtz_stride + j] = t * (colscale ? (double)colscale[j] : 1.0);
+  }
 }
 
 }  // namespace
@@ -1223,11 +1235,9 @@ cudaError_t xstream_k_enqueue(const void* map, const XKArgs& a, const double* be
 
 cudaError_t xstream_k_reduce(const XKArgs& a, int grid, double* xtz, int64_t xtz_stride, cudaStream_t s) {
   if (a.kc == 16)
-    reduce_k_kernel<16><<<(a.p * 16 + 255) / 256, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, a.colscale, xtz,
-                                                                xtz_stride);
+    reduce_k_kernel<16><<<a.p, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, a.colscale, xtz, xtz_stride);
   else if (a.kc == 32)
-    reduce_k_kernel<32><<<(a.p * 32 + 255) / 256, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, a.colscale, xtz,
-                                                                xtz_stride);
+    reduce_k_kernel<32><<<a.p, 256, 0, s>>>(a.partials, grid, a.fpad, a.p, a.K, a.colscale, xtz, xtz_stride);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
