@@ -150,3 +150,29 @@ def test_pair_factorization_on_an_ill_conditioned_design(pkg):
     got = gpu_transition(pkg, d, st, 17)
     ref = oracle.sweep_once(st.copy(), X, d["y"], G, 17, keep=True)
     assert_transition_close(got, ref, 1e-10)
+
+
+@pytest.mark.parametrize("dt,p,K", [("bf16", 304, 4), ("bf16", 2000, 4), ("fp8", 512, 3)])  # rows of 16-byte slices
+def test_adopted_x_with_chains_on_the_tensor_cores_gives_the_copied_transition(pkg, dt, p, K):
+    """K chains on an adopted device X (the tensor-core X-streams read the
+    caller's buffer through their tensor maps): the same transition bit for
+    bit as on the library's copy (fused form at p = 304, two-pass form at
+    p = 2000 and for FP8 with column scales)."""
+    import torch
+    d = problem(3001, p, 5, dt, seed=p)
+    sts = [random_state(p, k=3, seed=40 + m) for m in range(K)]
+    outs = []
+    for adopt in (False, True):
+        X = torch.from_numpy(d["X"]).cuda()
+        y = torch.from_numpy(d["y"]).cuda()
+        sc = torch.from_numpy(d["scales"]).cuda() if d["scales"] is not None else None
+        s = pkg.HSProbit(X, y, seed=12, debug=True, num_chains=K, adopt=adopt, scales=sc)
+        try:
+            for m, st in enumerate(sts):
+                s.set_state(st.beta, st.lam_inv2, st.nu_inv, st.tau_inv2, st.xi_inv, st.k, chain=m)
+            s.sweep(2)
+            outs.append([(s.get_state(chain=m)["beta"], s.debug_z(chain=m)) for m in range(K)])
+        finally:
+            s.close()
+    for (b0, z0), (b1, z1) in zip(*outs):
+        assert np.array_equal(z0, z1) and np.array_equal(b0, b1)
