@@ -409,8 +409,10 @@ hs_probit_batch* hs_probit_batch_init(const hs_probit_config* cfg, int32_t n, co
                                       uint64_t seed);
 /* Number of problems, or HS_EINVAL. */
 int32_t hs_probit_batch_size(const hs_probit_batch* b);
-/* Problem m's handle (owned by the batch): draws, get/set_state and the
- * debug copies work on it as on any handle.  NULL if m is out of range. */
+/* Problem m's handle (owned by the batch): draws, get/set_state, launch
+ * shapes (the batch recaptures its graph after a change) and the debug copies
+ * work on it as on any handle; hs_probit_free ignores it (the batch releases
+ * it).  NULL if m is out of range. */
 hs_probit* hs_probit_batch_problem(hs_probit_batch* b, int32_t m);
 /* n_iter sweeps of every problem.  HS_ESTATE if a problem is in an error
  * state; otherwise the first failing problem's status (the others' states

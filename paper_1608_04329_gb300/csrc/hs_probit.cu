@@ -108,6 +108,7 @@ struct hs_probit {
   // launch shapes set by a batch (hs_probit_batch_*): no cooperative launch, no
   // chain SM isolation, and the factorization's grid chosen by the batch's tuner
   bool batch_member = false;
+  uint64_t shape_epoch = 0;                 // bumped by every launch-shape change (a batch recaptures)
   unsigned char* bsw = nullptr;             // B^T of the batched X-stream
   float* kpartials = nullptr;
   alignas(64) unsigned char xmap[128];      // tensor map of X (batched X-stream)
@@ -1379,7 +1380,8 @@ int hs_probit_set_launch_shape(hs_probit* h, const hs_launch_shape* in) {
         return HS_ECUDA;
     }
   }
-  // a captured sweep holds the old shapes
+  // a captured sweep holds the old shapes (a batch holding this problem recaptures on the epoch)
+  ++h->shape_epoch;
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
   h->gexec = nullptr;
@@ -1424,7 +1426,7 @@ int hs_probit_debug_wait_timeout(hs_probit* h, int64_t max_spins) {
 }
 
 void hs_probit_free(hs_probit* h) {
-  if (!h) return;
+  if (!h || h->batch_member) return;  // a batch's problems are released with the batch
   DeviceGuard dg(h->device);
   destroy(h);
 }
@@ -1445,6 +1447,7 @@ struct hs_probit_batch {
   std::vector<double> wx, wc;  // each problem's X bytes and factorization work (K P^3)
   double wx_sum = 0, wc_sum = 0;
   std::vector<hs_tune_trial> trials;
+  uint64_t shape_epochs = 0;  // sum of the problems' shape epochs when the graph was captured
 };
 
 namespace {
@@ -1461,6 +1464,8 @@ void batch_drop_graph(hs_probit_batch* b) {
 // branches.
 cudaError_t batch_build_graph(hs_probit_batch* b) {
   batch_drop_graph(b);
+  b->shape_epochs = 0;
+  for (hs_probit* h : b->probs) b->shape_epochs += h->shape_epoch;
   cudaError_t e = cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   cudaError_t e2 = cudaEventRecord(b->ev_start, b->root);
@@ -1568,7 +1573,10 @@ int batch_time(hs_probit_batch* b, int sweeps, double* ms) {
 void batch_destroy(hs_probit_batch* b) {
   if (b->root) cudaStreamSynchronize(b->root);
   batch_drop_graph(b);
-  for (hs_probit* h : b->probs) hs_probit_free(h);
+  for (hs_probit* h : b->probs) {
+    DeviceGuard dg(h->device);
+    destroy(h);
+  }
   for (cudaEvent_t ev : b->ev_done)
     if (ev) cudaEventDestroy(ev);
   if (b->ev_start) cudaEventDestroy(b->ev_start);
@@ -1668,7 +1676,9 @@ int hs_probit_batch_sweep(hs_probit_batch* b, int64_t n_iter) {
       if (cudaStreamSynchronize(h->s0) != cudaSuccess || cudaStreamSynchronize(h->s1) != cudaSuccess)
         return HS_ECUDA;
     }
-    if (!b->gexec) {
+    uint64_t epochs = 0;
+    for (hs_probit* h : b->probs) epochs += h->shape_epoch;
+    if (!b->gexec || epochs != b->shape_epochs) {
       const cudaError_t e = batch_build_graph(b);
       if (e != cudaSuccess) return cuda_status(e);
     }

@@ -88,6 +88,30 @@ def test_one_chain_f32_batch_matches_oracle(pkg):
         assert_transition_close(got[m][0], ref, 1e-4)
 
 
+def test_batch_member_shape_change_and_free_are_safe(pkg):
+    """A launch-shape change on one problem makes the batch recapture its
+    graph and keep sweeping; hs_probit_free on a problem's handle is ignored
+    (the batch owns it)."""
+    ds = _make([(3000, 200), (2500, 90)], "bf16", 3)
+    outs = []
+    for change_after in (True, False):
+        b = pkg.HSProbitBatch([(d["X"], d["y"]) for d in ds], seed=2, num_chains=2)
+        try:
+            h = b.problem(0)
+            if not change_after:
+                h.set_launch_shape(xstream_ctas=5)
+            b.sweep(2)
+            if change_after:
+                h.set_launch_shape(xstream_ctas=5)
+            b.sweep(2)
+            pkg.load_library().hs_probit_free(h._h)  # ignored: the handle still works
+            outs.append(h.get_state(chain=1))
+            assert outs[-1]["k"] == 4
+        finally:
+            b.close()
+    assert np.all(np.isfinite(outs[0]["beta"])) and np.all(np.isfinite(outs[1]["beta"]))
+
+
 def test_fp8_batch_with_column_scales_matches_oracle(pkg):
     """Uneven FP8 problems, each with its own column scales (hs_problem.x_scales),
     two chains each: the two-pass tensor-core X-stream per problem."""
