@@ -184,7 +184,7 @@ struct CholArgs {
   // the ntasks entries of order, and writes the six BF16 digit planes of every
   // factor tile it forms below row tile k1 (digits: nchains x 6 planes of P x P).
   int k0, k1;                   // 0, 0: the whole matrix in one launch
-  int ntasks;                   // > 0: entries of order (block-column launches)
+  int ntasks;                   // entries of order (when order is given)
   void* digits;                 // or nullptr
   // block-column launches: per-SM claim and role words (2 x kSmMarks, zeroed
   // once) for placing the chains on SMs of their own; or nullptr
@@ -210,7 +210,8 @@ int chol_persistent_grid(int device, int nchains = 1);
 // `workers` concurrent task slots (a topological order; see linalg.cu).
 std::vector<int> chol_task_order(int T, int workers, bool inverse);
 // The same list with each entry decoded for the kernel: kind (0 C, 1 X, 2 UA,
-// 3 UB) | k << 2 | i << 10 | j << 18 (T <= 256).
+// 3 UB) | k << 2 | i << 10 | j << 18 (T <= 256); a C(i,k) entry carries
+// j = k + 1: the task also applies UA(i,k+1,k), which the list leaves out.
 std::vector<int> chol_task_codes(int T, int workers, bool inverse);
 
 // Task list of one block-column launch (tile columns [k0, k1) of T): C(i, k) and

@@ -81,6 +81,7 @@ struct hs_probit {
   int chol_grid = 0;                        // its blocks; 0: one launch per block column
   size_t chol_words = 0;                    // scheduling words per chain
   int* chol_order = nullptr;                // worker task list of the single-launch factorization
+  int chol_ntasks = 0;                      // its length
   // HS_SCHED_TENSOR: block-column launches and tensor-core trailing updates
   bool tensor_sched = false;
   void* digits = nullptr;                   // K x 6 digit planes of P x P BF16
@@ -308,6 +309,7 @@ hs::CholArgs chol_args(hs_probit* h, int m) {
   a.nchains = 1;
   a.sync_words = h->chol_words;
   a.order = h->chol_order;
+  a.ntasks = h->chol_ntasks;
   a.inverse = h->chol_inverse ? 1 : 0;
   a.cooperative = h->batch_member ? 0 : 1;
   return a;
@@ -884,6 +886,7 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
     check(h->alloc(&h->chol_sync, K * h->chol_words * sizeof(unsigned long long)));
     check(h->alloc(&h->sm_mark, hs::kSmMarks * sizeof(unsigned int)));
     order = single_task_list(h);
+    h->chol_ntasks = (int)order.size();
     if (!order.empty()) check(h->alloc(&h->chol_order, order.size() * sizeof(int)));
   }
   if (h->tensor_sched) {
@@ -1370,6 +1373,7 @@ int hs_probit_set_launch_shape(hs_probit* h, const hs_launch_shape* in) {
     h->chol_grid = cg;
     if (h->chol_order) {
       const std::vector<int> order = single_task_list(h);
+      if ((int)order.size() != h->chol_ntasks) return HS_EINVAL;
       if (cudaMemcpy(h->chol_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
         return HS_ECUDA;
     }

@@ -718,6 +718,10 @@ __global__ void __launch_bounds__(256) step_df_kernel(CholArgs a, int k) {
 //   X(k,j)   X_kj = L_kk^{-1} B_kj                   j < k
 //   UA(i,j,k) A_ij -= L_ik L_jk^T   k < j <= i, except the diagonal tile's last update
 //   UB(i,j,k) B_ij -= L_ik X_kj     i > k, j <= k
+// A task list from the host merges each UA(i,k+1,k) into C(i,k) (code j =
+// k + 1): the task keeps L_ik in shared memory and applies the next update
+// of its own tile row, so every row's path C(i,k) -> UA(i,k+1,k) -> C(i,k+1)
+// takes one task per step instead of two.
 // Without the inverse factor (CholArgs::inverse == 0) the X and UB tasks are
 // left out, so the launch does half the tile products; the chain still forms
 // every L_kk^{-1}, and the C tasks and the chain also store L_ik^T at tile
@@ -1345,7 +1349,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
     __syncthreads();
     // a block-column launch runs exactly its list (which may be empty: a
     // last block column of one tile has no worker task)
-    const int total1 = a.k1 > 0 ? a.ntasks : s_step0[T];
+    const int total1 = a.order ? a.ntasks : s_step0[T];
     const long long total = (long long)total1 * nch;  // task t: chain t % nch, its list entry t / nch
     const int gi = threadIdx.x >> 7;                  // two groups of four warps, one task each
     const Grp g{(int)(threadIdx.x & 127), 1 + gi};
@@ -1435,6 +1439,23 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
         if (!inv) gstore_cg(g, LinvT, P, k, i, gX2, true);
         if (cv.dig && i >= ke) tile_digits_store(g.t, 128, gX2, cv.dig, P, i, k);
         gpublish(g, &ps.flagL[i * T + k], e);
+        if (j != k + 1) continue;
+        // the merged UA(i,k+1,k): A_{i,k+1} -= L_ik L_{k+1,k}^T with L_ik still in gX2
+        // (the chain publishes L_{k+1,k}; tile (i, k+1) after updates 0..k-1)
+        const unsigned long long* const wq2[2] = {&ps.flagL[(k + 1) * T + k], &ps.cntA[i * T + k + 1]};
+        const unsigned long long wu2[2] = {e, k >= 1 ? done_k : 0ull};
+        if (!gwait<2>(g, wq2, wu2, ps0, e, a.err)) break;
+        if (k == 0 && !a.prebuilt) {
+          gload_gram(g, gW, cx, i, k + 1);
+          const TileRef t1[1] = {{A, k + 1, k, false, gX1}};
+          gload_cg<1>(g, t1, P);
+        } else {
+          const TileRef t2[2] = {{A, i, k + 1, false, gW}, {A, k + 1, k, false, gX1}};
+          gload_cg<2>(g, t2, P);
+        }
+        g.sync();
+        gmma_update_store(g, gW, gX2, gX1, tile_rows(cx.p, i), A, P, i, k + 1);
+        gpublish(g, &ps.cntA[i * T + k + 1], done_k + 1);
         continue;
       }
       if (kind == 1) {
@@ -1937,10 +1958,21 @@ struct HostIds {
 std::vector<int> chol_task_order(int T, int workers, bool inverse) {
   const HostIds id(T, inverse);
   const int n = id.s0[T];
-  std::vector<int> canonical(n);
-  for (int t = 0; t < n; ++t) canonical[t] = t;
-  if (n == 0 || workers < 1) return canonical;
   const int N = n + 2 * T;  // chain nodes: n + 2k (L_kk^{-1}), n + 2k + 1 (L_{k+1,k}, next diagonal)
+  // Each panel task C(i,k) also applies UA(i,k+1,k), the next update of its
+  // own tile row, from the L_ik it still holds (one task instead of two on
+  // every row's path C(i,k) -> UA(i,k+1,k) -> C(i,k+1)); rep maps a merged
+  // update to its C task.  The canonical order without the merged updates
+  // is still topological (a C task is listed at the start of its step).
+  std::vector<int> rep(N);
+  for (int v = 0; v < N; ++v) rep[v] = v;
+  for (int k = 0; k + 2 < T; ++k)
+    for (int i = k + 2; i < T; ++i) rep[id.UA(i, k + 1, k)] = id.C(i, k);
+  std::vector<int> canonical;
+  for (int t = 0; t < n; ++t)
+    if (rep[t] == t) canonical.push_back(t);
+  const int nlive = (int)canonical.size();
+  if (nlive == 0 || workers < 1) return canonical;
   auto Li = [&](int k) { return n + 2 * k; };
   auto Ln = [&](int k) { return n + 2 * k + 1; };
   std::vector<std::vector<int>> deps(N);
@@ -1975,18 +2007,33 @@ std::vector<int> chol_task_order(int T, int workers, bool inverse) {
       }
     }
   }
-  // durations (us, measured on GB300): diagonal tile 10, panel tile and next diagonal 6, tile task 6
+  // the merged updates' inputs join their C tasks; readers of either read the C task
+  for (int v = 0; v < N; ++v) {
+    if (rep[v] == v) continue;
+    for (int d : deps[v]) deps[rep[v]].push_back(d);
+    deps[v].clear();
+  }
+  for (int v = 0; v < N; ++v) {
+    std::vector<int> dd;
+    for (int d : deps[v]) {
+      if (d < 0 || d >= N) return canonical;
+      const int r = rep[d];
+      if (r != v && std::find(dd.begin(), dd.end(), r) == dd.end()) dd.push_back(r);
+    }
+    deps[v].swap(dd);
+  }
+  // durations (us, measured on GB300): diagonal tile 10, panel tile and next
+  // diagonal 6, tile task 6, a C task with its merged update 12
   std::vector<double> dur(N, 6.0);
+  for (int k = 0; k + 2 < T; ++k)
+    for (int i = k + 2; i < T; ++i) dur[id.C(i, k)] = 12.0;
   for (int k = 0; k < T; ++k) {
     dur[Li(k)] = 10.0;
     dur[Ln(k)] = 6.0;
   }
   std::vector<std::vector<int>> succ(N);
   for (int v = 0; v < N; ++v)
-    for (int d : deps[v]) {
-      if (d < 0 || d >= N) return canonical;
-      succ[d].push_back(v);
-    }
+    for (int d : deps[v]) succ[d].push_back(v);
   // bottom levels in reverse topological order
   std::vector<int> cnt(N), topo;
   topo.reserve(N);
@@ -2019,11 +2066,11 @@ std::vector<int> chol_task_order(int T, int workers, bool inverse) {
   using EV = std::pair<double, int>;
   std::priority_queue<EV, std::vector<EV>, std::greater<EV>> ev;
   for (int v = 0; v < N; ++v)
-    if (rem[v] == 0) {
+    if (rem[v] == 0 && rep[v] == v) {
       if (v >= n) chain_ready.push(v); else ready.push({-bl[v], v});
     }
   std::vector<int> out;
-  out.reserve(n);
+  out.reserve(nlive);
   std::vector<double> start(N, -1.0);
   double now = 0.0;
   int free_w = workers;
@@ -2054,11 +2101,11 @@ std::vector<int> chol_task_order(int T, int workers, bool inverse) {
         if (w >= n) chain_ready.push(w); else ready.push({-bl[w], w});
       }
   }
-  if ((int)out.size() != n) return canonical;
-  // check: a permutation, and every node starts no earlier than its inputs
+  if ((int)out.size() != nlive) return canonical;
+  // check: a permutation of the live tasks, and every node starts no earlier than its inputs
   std::vector<char> seen(n, 0);
   for (int v : out) {
-    if (v < 0 || v >= n || seen[v]) return canonical;
+    if (v < 0 || v >= n || rep[v] != v || seen[v]) return canonical;
     seen[v] = 1;
   }
   for (int v = 0; v < N; ++v)
@@ -2073,6 +2120,7 @@ std::vector<int> chol_task_codes(int T, int workers, bool inverse) {
   for (int& t : order) {
     int kind, i, j, k;
     id.decode(t, kind, i, j, k);
+    if (kind == 0) j = k + 1;  // C(i,k) with its merged update UA(i,k+1,k)
     t = kind | (k << 2) | (i << 10) | (j << 18);
   }
   return order;

@@ -9,7 +9,8 @@ Tasks of step k (tile size 32, T tiles): C(i,k) L_ik = A_ik L_kk^{-T} for
 i >= k+2 (the chain forms L_{k+1,k}); UA(i,j,k) A_ij -= L_ik L_jk^T for
 k < j <= i except (k+1, k+1) (the chain applies that one); with the inverse
 factor also X(k,j) = L_kk^{-1} B_kj for j < k and UB(i,j,k) B_ij -= L_ik X_kj
-for i > k, j <= k.
+for i > k, j <= k.  In the single launch's list each C(i,k) also applies
+UA(i,k+1,k) (code j = k + 1), which the list then leaves out.
 """
 import ctypes
 
@@ -62,25 +63,44 @@ def _deps(task):
     return d
 
 
+def _merged(task):
+    """The list entry that performs a task: UA(i,k+1,k) (i >= k+2) is done by C(i,k)."""
+    kind, i, j, k = task
+    if kind == 2 and j == k + 1 and i >= k + 2:
+        return (0, i, k, k)
+    return task
+
+
 @pytest.mark.parametrize("inv", [0, 1])
 @pytest.mark.parametrize("T", [1, 2, 3, 4, 7, 16, 32, 40])
 @pytest.mark.parametrize("workers", [1, 7, 300])
 def test_task_list_is_complete_and_topological(lib, T, inv, workers):
     n = lib.hs_chol_task_list(T, workers, inv, None, 0)
-    want = _tasks(T, inv)
+    every = _tasks(T, inv)
+    want = {t for t in every if _merged(t) == t}
     assert n == len(want)
     codes = np.zeros(max(n, 1), dtype=np.int32)
     assert lib.hs_chol_task_list(T, workers, inv, codes.ctypes.data, n) == n
     got = []
     for c in codes[:n].tolist():
         kind, k, i, j = c & 3, (c >> 2) & 0xFF, (c >> 10) & 0xFF, (c >> 18) & 0xFF
-        got.append((kind, i, j, k) if kind in (1, 2, 3) else (kind, i, k, k))
+        if kind == 0:
+            assert j == k + 1, "a C entry of the single launch carries its merged update"
+            got.append((0, i, k, k))
+        else:
+            got.append((kind, i, j, k))
     assert len(set(got)) == n and set(got) == want
     pos = {t: p for p, t in enumerate(got)}
-    for t in got:
+    # every task of the blocked factorization, merged or not, runs after the
+    # entries it reads (a merged update reads its own C task's output in place)
+    for t in every:
+        mt = _merged(t)
         for d in _deps(t):
-            assert d in pos, (t, d)
-            assert pos[d] < pos[t], (t, d)
+            md = _merged(d)
+            if md == mt:
+                assert mt != t and d == mt, (t, d)  # the merged update reads its own C task
+            else:
+                assert pos[md] < pos[mt], (t, d)
 
 
 def test_task_list_rejects_bad_arguments(lib):
