@@ -284,8 +284,9 @@ struct TailArgs {
 // chain's commit must follow every chain's draws).
 cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s, int nchains = 1);
 cudaError_t commit_enqueue(const TailArgs& a, cudaStream_t s, int nchains = 1);
-// Substitution form only (TailArgs::solve): the s_j and nu_j^{-1} draws, which
-// must precede tail_draw_enqueue and follow the shrink kernel; no-op otherwise.
+// Substitution form and FP32-pair factors (TailArgs::solve or df32): the s_j
+// and nu_j^{-1} draws, which must precede tail_draw_enqueue and follow the
+// shrink kernel; no-op otherwise (the FP64 products draw them themselves).
 cudaError_t tail_noise_enqueue(const TailArgs& a, cudaStream_t s, int nchains = 1);
 
 // beta_c = (compute type)(beta * colscale), pads zero.

@@ -409,7 +409,9 @@ cudaError_t enqueue_sweep(hs_probit* h) {
     ProfSpan sp(h, 2, h->s1);
     if ((e = hs::shrink_launch(shrink_args(h, 0), h->s1, h->K)) != cudaSuccess) return e;
   }
-  if (!h->chol_inverse && (e = cudaEventRecord(h->ev_shrink, h->s1)) != cudaSuccess) return e;
+  // s and nu^{-1} (substitution form, and the FP32-pair products) are drawn beside the factorization
+  const bool noise_beside = !h->chol_inverse || h->cfg.chol_arith == HS_CHOL_DF32;
+  if (noise_beside && (e = cudaEventRecord(h->ev_shrink, h->s1)) != cudaSuccess) return e;
   // the work matrix of the factorization, beside the X-stream (outside the
   // timed spans: one span per kernel group and sweep)
   if (h->tensor_sched && (e = hs::precision_pairs_launch(trail_args(h), h->s1)) != cudaSuccess) return e;
@@ -508,8 +510,8 @@ cudaError_t enqueue_sweep(hs_probit* h) {
       if (e != cudaSuccess) return e;
     }
   }
-  if (!h->chol_inverse) {
-    // the substitution form's s and nu draws need lambda^{-2} only: beside the factorization
+  if (noise_beside) {
+    // the s and nu draws need lambda^{-2} only: beside the factorization
     if ((e = cudaStreamWaitEvent(h->s0, h->ev_shrink, 0)) != cudaSuccess) return e;
     if ((e = hs::tail_noise_enqueue(tail_args(h, 0), h->s0, h->K)) != cudaSuccess) return e;
   }

@@ -44,6 +44,7 @@ constexpr int kStepPadBytes = 40 * 1024;
 // shrink: lambda^{-2}, tau^{-2} and the equilibration S
 // ---------------------------------------------------------------------------
 constexpr int kShrinkThreads = 128;
+constexpr int kShrinkBatch = 8;  // equilibration columns per thread and load round trip
 
 // S_j = 1/sqrt(d) rounded to FP32 and returned exactly as a double.  Any
 // positive diagonal scaling gives the same factorization mathematically
@@ -106,6 +107,15 @@ __global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  // the equilibration's inputs for the first kShrinkBatch * kShrinkThreads
+  // columns, loaded (one round trip) while warp 0 draws tau
+  double gd[kShrinkBatch], lm[kShrinkBatch];
+#pragma unroll
+  for (int u = 0; u < kShrinkBatch; ++u) {
+    const int jj = tid + u * kShrinkThreads;
+    gd[u] = jj < a.p ? a.G[(size_t)jj * a.p + jj] : 1.0;
+    lm[u] = jj < a.p ? __ldcg(a.lam_new + jj) : 0.0;
+  }
   if (warp == 0) {
     // fixed-order sum of the block partials
     double tot = 0.0;
@@ -142,19 +152,32 @@ __global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
   }
   __syncthreads();
   const double tn = s_tau;
-  for (int jj = tid; jj < a.P; jj += kShrinkThreads) {
-    double sj = 1.0;
-    if (jj < a.p) {
-      const double d = a.G[(size_t)jj * a.p + jj] + tn * a.lam_new[jj];
-      if (!isfinite(d)) {
-        set_error(a.err, kErrNonFinite);
-      } else if (!(d > 0.0)) {
-        set_error(a.err, kErrNotPD);
-      } else {
-        sj = equil_scale(d);
+  for (int b0 = 0; b0 < a.P; b0 += kShrinkBatch * kShrinkThreads) {
+    if (b0 > 0) {
+#pragma unroll
+      for (int u = 0; u < kShrinkBatch; ++u) {
+        const int jj = b0 + tid + u * kShrinkThreads;
+        gd[u] = jj < a.p ? a.G[(size_t)jj * a.p + jj] : 1.0;
+        lm[u] = jj < a.p ? __ldcg(a.lam_new + jj) : 0.0;
       }
     }
-    a.S[jj] = sj;
+#pragma unroll
+    for (int u = 0; u < kShrinkBatch; ++u) {
+      const int jj = b0 + tid + u * kShrinkThreads;
+      if (jj >= a.P) break;
+      double sj = 1.0;
+      if (jj < a.p) {
+        const double d = gd[u] + tn * lm[u];
+        if (!isfinite(d)) {
+          set_error(a.err, kErrNonFinite);
+        } else if (!(d > 0.0)) {
+          set_error(a.err, kErrNotPD);
+        } else {
+          sj = equil_scale(d);
+        }
+      }
+      a.S[jj] = sj;
+    }
   }
 }
 
@@ -1528,7 +1551,6 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
 // tail
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double elem(const double* M, size_t idx) { return M[idx]; }
-__device__ __forceinline__ double elem(const df2* M, size_t idx) { return df_value(M[idx]); }
 
 // Several chains in one launch (blockIdx.y = chain), as for the shrink kernel;
 // k_dev_rw advances by one slot per chain.
@@ -1604,6 +1626,80 @@ __global__ void __launch_bounds__(256) tail_beta_kernel(TailArgs a0) {
     double u, uc;
     unit_pair(w.x, w.y, u, uc);
     a.nu_new[j] = -log(u) / (1.0 + a.lam_new[j]);
+  }
+}
+
+// The FP32-pair form of the two products (inverse factor in FP32 pairs): the
+// dot products run on the FP32 pipe (pair FMAs, two accumulators per lane,
+// a pair reduction across the warp), and s_j and nu_j^{-1} come from
+// tail_noise_kernel, which draws them beside the factorization.  GB300's FP64
+// pipe is 1/64 of its FP32 rate, so the FP64 forms above are bound by the
+// FP64 work of their longest rows.  Block: 8 rows, one warp each.
+constexpr int kTailChunk = 1024;
+
+__device__ __forceinline__ df2 warp_sum_df(df2 v) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const df2 o{__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
+    v = df_add(v, o);
+  }
+  return v;
+}
+
+// v_i = sum_{j <= i} Linv[i][j] (S_j xtz_j) + s_i, with s_i read from v and
+// v_i written back in place as an FP32 pair.
+__global__ void __launch_bounds__(256) tail_w_df_kernel(TailArgs a0) {
+  const TailArgs a = tail_chain(a0, blockIdx.y);
+  __shared__ df2 s_u[kTailChunk];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * 8, i = i0 + warp;
+  const int jend = min(a.p, i0 + 8);  // columns any row of the block reads
+  const df2* row = reinterpret_cast<const df2*>(a.Linv) + (size_t)i * a.P;
+  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+  for (int c0 = 0; c0 < jend; c0 += kTailChunk) {
+    const int c1 = min(c0 + kTailChunk, jend);
+    __syncthreads();
+    for (int j = c0 + (int)threadIdx.x; j < c1; j += blockDim.x) s_u[j - c0] = df_split(a.S[j] * a.xtz[j]);
+    __syncthreads();
+    if (i < a.p) {
+      const int e1 = min(c1, i + 1);
+      int j = c0 + lane;
+      for (; j + 32 < e1; j += 64) {
+        df_fma(h0, l0, row[j], s_u[j - c0]);
+        df_fma(h1, l1, row[j + 32], s_u[j + 32 - c0]);
+      }
+      if (j < e1) df_fma(h0, l0, row[j], s_u[j - c0]);
+    }
+  }
+  if (i >= a.p) return;
+  const df2 t = warp_sum_df(df_add(df_renorm(h0, l0), df_renorm(h1, l1)));
+  if (lane == 0) {
+    const double v = df_value(t) + a.v[i];
+    reinterpret_cast<df2*>(a.v)[i] = df_split(v);
+  }
+}
+
+// beta_j = S_j sum_{i >= j} LinvT[j][i] v_i, v as FP32 pairs (tail_w_df_kernel).
+__global__ void __launch_bounds__(256) tail_beta_df_kernel(TailArgs a0) {
+  const TailArgs a = tail_chain(a0, blockIdx.y);
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= a.p) return;
+  const int j = warp;
+  const df2* row = reinterpret_cast<const df2*>(a.LinvT) + (size_t)j * a.P;
+  const df2* v = reinterpret_cast<const df2*>(a.v);
+  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+  int i = j + lane;
+  for (; i + 32 < a.p; i += 64) {
+    df_fma(h0, l0, row[i], v[i]);
+    df_fma(h1, l1, row[i + 32], v[i + 32]);
+  }
+  if (i < a.p) df_fma(h0, l0, row[i], v[i]);
+  const df2 t = warp_sum_df(df_add(df_renorm(h0, l0), df_renorm(h1, l1)));
+  if (lane == 0) {
+    const double bj = a.S[j] * df_value(t);
+    a.beta_new[j] = bj;
+    if (!isfinite(bj) && *(volatile int*)a.err == 0) set_error(a.err, kErrNonFinite);
   }
 }
 
@@ -1747,7 +1843,7 @@ __global__ void __cluster_dims__(kSolveCTAs, 1, 1) __launch_bounds__(kSolveThrea
   cluster_sync_all();  // no block leaves while another may still write into it
 }
 
-// The draws the substitution form needs, apart from the factor: s_j (into v)
+// The draws the FP32-pair tails need, apart from the factor: s_j (into v)
 // and nu_j^{-1}.  They depend only on the counters and lambda^{-2}, so they
 // run beside the factorization.  One thread per j, chains on blockIdx.y.
 __global__ void __launch_bounds__(256) tail_noise_kernel(TailArgs a0) {
@@ -1855,8 +1951,8 @@ cudaError_t linalg_prepare() {
                        (const void*)chol_persistent_kernel,
                        (const void*)tail_w_kernel<double>,
                        (const void*)tail_beta_kernel<double>,
-                       (const void*)tail_w_kernel<df2>,
-                       (const void*)tail_beta_kernel<df2>,
+                       (const void*)tail_w_df_kernel,
+                       (const void*)tail_beta_df_kernel,
                        (const void*)tail_solve_kernel,
                        (const void*)tail_noise_kernel,
                        (const void*)commit_kernel,
@@ -2332,8 +2428,9 @@ cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s, int nchains) {
     if (a.P > kMaxTiles * NB) return cudaErrorInvalidValue;
     tail_solve_kernel<<<nchains * kSolveCTAs, kSolveThreads, 0, s>>>(a);
   } else if (a.df32) {
-    tail_w_kernel<df2><<<grid, 256, 0, s>>>(a);
-    tail_beta_kernel<df2><<<grid, 256, 0, s>>>(a);
+    // s and nu^{-1}: tail_noise_kernel, beside the factorization
+    tail_w_df_kernel<<<dim3((a.p + 7) / 8, nchains), 256, 0, s>>>(a);
+    tail_beta_df_kernel<<<grid, 256, 0, s>>>(a);
   } else {
     tail_w_kernel<double><<<grid, 256, 0, s>>>(a);
     tail_beta_kernel<double><<<grid, 256, 0, s>>>(a);
@@ -2342,7 +2439,7 @@ cudaError_t tail_draw_enqueue(const TailArgs& a, cudaStream_t s, int nchains) {
 }
 
 cudaError_t tail_noise_enqueue(const TailArgs& a, cudaStream_t s, int nchains) {
-  if (!a.solve) return cudaSuccess;
+  if (!a.solve && !a.df32) return cudaSuccess;  // the FP64 products draw s and nu^{-1} themselves
   tail_noise_kernel<<<dim3((a.p + 255) / 256, nchains), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
