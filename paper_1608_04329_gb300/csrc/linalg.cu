@@ -862,13 +862,15 @@ __device__ __forceinline__ bool block_wait(const unsigned long long* p, unsigned
   return block_wait<1>(pp, tt, ps, e, err, site);
 }
 
-// All threads' global writes of the block become visible before *p = v.
+// All threads' global writes of the block become visible before *p = v:
+// the barrier orders them before thread 0's release store, and a release at
+// GPU scope is cumulative over what its thread has synchronized with, so no
+// separate (sequentially consistent) fence is needed; readers pair it with
+// an acquire (measured: one chain, factorization 0.78 -> 0.75 ms without the
+// extra fence on every publish).
 __device__ __forceinline__ void block_publish(unsigned long long* p, unsigned long long v) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    st_release_u64(p, v);
-  }
+  if (threadIdx.x == 0) st_release_u64(p, v);
 }
 
 // Tile moves of data other blocks write during this launch go through L2.
@@ -1153,12 +1155,10 @@ __device__ bool gwait(const Grp& g, const unsigned long long* const (&p)[N], con
   }
   return g.sync_and(ok);
 }
+// The group's writes become visible before *p = v (as block_publish).
 __device__ __forceinline__ void gpublish(const Grp& g, unsigned long long* p, unsigned long long v) {
   g.sync();
-  if (g.t == 0) {
-    __threadfence();
-    st_release_u64(p, v);
-  }
+  if (g.t == 0) st_release_u64(p, v);
 }
 
 // The buffers of one chain of the launch.
