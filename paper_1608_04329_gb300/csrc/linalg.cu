@@ -820,10 +820,14 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 }
 
 // Thread 0 waits until *p[n] >= target[n] for every n; the block then
-// proceeds together.  The words are read together (relaxed) and one
-// acquire fence follows, so a task whose inputs are ready pays one L2 round
-// trip.  Returns false (in every thread) if a wait ran out (2 s; the
-// timeout bit is set and the abort word raised) or another block gave up.
+// proceeds together.  The words are read together with acquire loads (no
+// separate fence: the load that sees the target orders the block's later
+// reads, through the barrier; measured: one chain, factorization 0.745 ->
+// 0.711 ms against relaxed reads and a trailing fence), so a task whose
+// inputs are ready pays one L2 round trip; each poll reads the flag and the
+// abort word together.  Returns false (in every thread) if a wait ran out
+// (2 s; the timeout bit is set and the abort word raised) or another block
+// gave up.
 template <int N>
 __device__ bool block_wait(const unsigned long long* const (&p)[N], const unsigned long long (&target)[N],
                            const PSync& ps, unsigned long long e, int* err, int site = kSiteChainStep) {
@@ -831,13 +835,17 @@ __device__ bool block_wait(const unsigned long long* const (&p)[N], const unsign
   if (threadIdx.x == 0) {
     unsigned long long v[N];
 #pragma unroll
-    for (int n = 0; n < N; ++n) v[n] = ld_relaxed_u64(p[n]);
+    for (int n = 0; n < N; ++n) v[n] = ld_acquire_u64(p[n]);
 #pragma unroll
     for (int n = 0; n < N; ++n) {
       if (ok && v[n] < target[n]) {
         const uint64_t t0 = global_ns();
-        while (ld_relaxed_u64(p[n]) < target[n]) {
-          if (ld_relaxed_u64(ps.abort) >= e) {
+        for (;;) {
+          // the flag and the abort word in one round trip
+          const unsigned long long fv = ld_acquire_u64(p[n]);
+          const unsigned long long av = ld_relaxed_u64(ps.abort);
+          if (fv >= target[n]) break;
+          if (av >= e) {
             ok = 0;
             break;
           }
@@ -851,7 +859,6 @@ __device__ bool block_wait(const unsigned long long* const (&p)[N], const unsign
         }
       }
     }
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
   }
   return __syncthreads_and(ok) != 0;
 }
@@ -1122,8 +1129,8 @@ __device__ __forceinline__ void gmma_update_store(const Grp& g, const df2 (*W)[N
                pol);
     }
 }
-// Thread 0 of the group waits for every *p[n] >= target[n] (one relaxed read of
-// all, then an acquire fence); bounded as block_wait.
+// Thread 0 of the group waits for every *p[n] >= target[n] (acquire loads of
+// all at once, then polls); bounded as block_wait.
 template <int N>
 __device__ bool gwait(const Grp& g, const unsigned long long* const (&p)[N], const unsigned long long (&target)[N],
                       const PSync& ps, unsigned long long e, int* err) {
@@ -1131,13 +1138,16 @@ __device__ bool gwait(const Grp& g, const unsigned long long* const (&p)[N], con
   if (g.t == 0) {
     unsigned long long v[N];
 #pragma unroll
-    for (int n = 0; n < N; ++n) v[n] = ld_relaxed_u64(p[n]);
+    for (int n = 0; n < N; ++n) v[n] = ld_acquire_u64(p[n]);
 #pragma unroll
     for (int n = 0; n < N; ++n) {
       if (ok && v[n] < target[n]) {
         const uint64_t t0 = global_ns();
-        while (ld_relaxed_u64(p[n]) < target[n]) {
-          if (ld_relaxed_u64(ps.abort) >= e) {
+        for (;;) {
+          const unsigned long long fv = ld_acquire_u64(p[n]);
+          const unsigned long long av = ld_relaxed_u64(ps.abort);
+          if (fv >= target[n]) break;
+          if (av >= e) {
             ok = 0;
             break;
           }
@@ -1151,7 +1161,6 @@ __device__ bool gwait(const Grp& g, const unsigned long long* const (&p)[N], con
         }
       }
     }
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
   }
   return g.sync_and(ok);
 }
