@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // the tile has taken every update of this block column
       if (live) {
-        __threadfence();
+        // the warp's stores, ordered by the warp barrier before lane 0's release
         __syncwarp();
         if (lane == 0) {
           unsigned long long* const cntA = a.sync + (size_t)m * a.sync_words + kSyncHeader;

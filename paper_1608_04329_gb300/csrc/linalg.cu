@@ -101,12 +101,14 @@ __global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
     double bp = 0.0;
     for (int w = 0; w < kShrinkThreads / 32; ++w) bp += s_part[w];
     a.part[blockIdx.x] = bp;
-    __threadfence();
-    s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1);
+    // release (the block's lambda^{-2} and its partial, ordered by the
+    // barrier) and acquire (the last block reads every block's) in one atomic
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(a.ticket) : "memory");
+    s_last = (old == gridDim.x - 1);
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
   // the equilibration's inputs for the first kShrinkBatch * kShrinkThreads
   // columns, loaded (one round trip) while warp 0 draws tau
   double gd[kShrinkBatch], lm[kShrinkBatch];
