@@ -494,7 +494,10 @@ __device__ __forceinline__ void tile_store(df2* M, int P, int ti, int tj, const 
 }
 
 // C = As Bt (set) or C -= As Bt (sub); Bt[q][c].  Rows {ty, ty+16}, cols {tx, tx+16}.
-template <bool kSub>
+// kLower: only the lower triangle of C is wanted (a symmetric update whose
+// upper part nobody reads): the block (ty, tx + 16), strictly upper for every
+// thread, is skipped and C keeps its old values there.
+template <bool kSub, bool kLower = false>
 __device__ __forceinline__ void tile_mma(df2 (*C)[NB + 1], const df2 (*As)[NB + 1], const df2 (*Bt)[NB + 1]) {
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   float h[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, l[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
@@ -503,7 +506,7 @@ __device__ __forceinline__ void tile_mma(df2 (*C)[NB + 1], const df2 (*As)[NB + 
     const df2 a0 = As[ty][q], a1 = As[ty + 16][q];
     const df2 b0 = Bt[q][tx], b1 = Bt[q][tx + 16];
     df_fma(h[0][0], l[0][0], a0, b0);
-    df_fma(h[0][1], l[0][1], a0, b1);
+    if (!kLower) df_fma(h[0][1], l[0][1], a0, b1);
     df_fma(h[1][0], l[1][0], a1, b0);
     df_fma(h[1][1], l[1][1], a1, b1);
   }
@@ -512,6 +515,7 @@ __device__ __forceinline__ void tile_mma(df2 (*C)[NB + 1], const df2 (*As)[NB + 
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
+      if (kLower && i == 0 && j == 1) continue;
       const df2 v = df_renorm(h[i][j], l[i][j]);
       df2& dst = C[ty + 16 * i][tx + 16 * j];
       dst = kSub ? df_sub(dst, v) : v;
@@ -570,17 +574,21 @@ __device__ void potri16_df(df2 (*W)[NB + 1], df2 (*Ui)[NB + 1], int o, df2* s_pi
 }
 
 // One entry of a 16 x 16 product of tile blocks, sum_{q in [q0, q1)} a(q) b(q),
-// with two accumulators (even and odd q).
+// with four accumulators (q mod 4).  The loop is unrolled over all 16 q with
+// the terms outside [q0, q1) multiplied as zeros (which leave a pair sum
+// unchanged), so the shared-memory loads of several q are in flight at once
+// instead of one trip of a data-dependent loop at a time.
 template <typename FA, typename FB>
 __device__ __forceinline__ df2 dot16(int q0, int q1, FA fa, FB fb) {
-  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-  int q = q0;
-  for (; q + 1 < q1; q += 2) {
-    df_fma(h0, l0, fa(q), fb(q));
-    df_fma(h1, l1, fa(q + 1), fb(q + 1));
+  float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const df2 x = fa(q), y = fb(q);
+    const bool in = q >= q0 && q < q1;
+    df_fma(h[q & 3], l[q & 3], in ? x : df2{0.0f, 0.0f}, y);
   }
-  if (q < q1) df_fma(h0, l0, fa(q), fb(q));
-  return df_add(df_renorm(h0, l0), df_renorm(h1, l1));
+  return df_add(df_add(df_renorm(h[0], l[0]), df_renorm(h[1], l[1])),
+                df_add(df_renorm(h[2], l[2]), df_renorm(h[3], l[3])));
 }
 
 // Inverse Cholesky factor of a 32 x 32 tile, L^{-1} with D = L L^T, by 2 x 2
@@ -1369,7 +1377,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
       if (last) break;
       for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) sX2[t & 31][t >> 5] = sLi[t >> 5][t & 31];
       __syncthreads();
-      tile_mma<true>(sD, sLi, sX2);  // D_{k+1} = A_{k+1,k+1} - L_{k+1,k} L_{k+1,k}^T
+      tile_mma<true, true>(sD, sLi, sX2);  // D_{k+1} = A_{k+1,k+1} - L_{k+1,k} L_{k+1,k}^T (lower part)
     }
   } else if (s_role == 0) {
     // ---------------- workers: tasks in list order from a shared counter ----------------
