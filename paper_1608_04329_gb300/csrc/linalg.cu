@@ -497,14 +497,16 @@ __device__ __forceinline__ void tile_store(df2* M, int P, int ti, int tj, const 
 // kLower: only the lower triangle of C is wanted (a symmetric update whose
 // upper part nobody reads): the block (ty, tx + 16), strictly upper for every
 // thread, is skipped and C keeps its old values there.
-template <bool kSub, bool kLower = false>
+// kBRows: the second operand is given by rows, Bs[c][q] (C = As Bs^T), which
+// spares a transposition pass (rows tx of a half-warp fall on distinct banks).
+template <bool kSub, bool kLower = false, bool kBRows = false>
 __device__ __forceinline__ void tile_mma(df2 (*C)[NB + 1], const df2 (*As)[NB + 1], const df2 (*Bt)[NB + 1]) {
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   float h[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, l[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll 4
   for (int q = 0; q < NB; ++q) {
     const df2 a0 = As[ty][q], a1 = As[ty + 16][q];
-    const df2 b0 = Bt[q][tx], b1 = Bt[q][tx + 16];
+    const df2 b0 = kBRows ? Bt[tx][q] : Bt[q][tx], b1 = kBRows ? Bt[tx + 16][q] : Bt[q][tx + 16];
     df_fma(h[0][0], l[0][0], a0, b0);
     if (!kLower) df_fma(h[0][1], l[0][1], a0, b1);
     df_fma(h[1][0], l[1][0], a1, b0);
@@ -542,13 +544,7 @@ __device__ void potri16_df(df2 (*W)[NB + 1], df2 (*Ui)[NB + 1], int o, df2* s_pi
   __syncthreads();
   for (int c = 0; c < 16; ++c) {
     df2 d = W[o + c][o + c];
-    const bool bad = !(d.hi > 0.0f) || !isfinite(d.hi);
-    if (bad) d = df2{1.0f, 0.0f};
-    if (tid == 0) {
-      if (bad && report && *(volatile int*)err == 0)
-        set_error(err, isfinite(W[o + c][o + c].hi) ? kErrNotPD : kErrNonFinite);
-      s_piv[o + c] = d;
-    }
+    if (!(d.hi > 0.0f) || !isfinite(d.hi)) d = df2{1.0f, 0.0f};
     const bool trailing = q > c;
     const df2 wr = W[o + r][o + c];
     const df2 y = trailing ? W[o + q][o + c] : Ui[o + c][o + q];
@@ -563,9 +559,23 @@ __device__ void potri16_df(df2 (*W)[NB + 1], df2 (*Ui)[NB + 1], int o, df2* s_pi
     }
     __syncthreads();
   }
+  // W_cc is not written after step c - 1: the pivots are checked here, the
+  // first bad one reported, each replaced by 1 as in the loop
+  if (tid == 0 && report) {
+    for (int c = 0; c < 16; ++c) {
+      const float dh = W[o + c][o + c].hi;
+      if (!(dh > 0.0f) || !isfinite(dh)) {
+        if (*(volatile int*)err == 0) set_error(err, isfinite(dh) ? kErrNotPD : kErrNonFinite);
+        break;
+      }
+    }
+  }
   if (tid < 16) {
+    df2 d = W[o + tid][o + tid];
+    if (!(d.hi > 0.0f) || !isfinite(d.hi)) d = df2{1.0f, 0.0f};
+    s_piv[o + tid] = d;
     df2 sq;
-    df_sqrt_rsqrt_fast(s_piv[o + tid], sq, s_rs[o + tid]);
+    df_sqrt_rsqrt_fast(d, sq, s_rs[o + tid]);
   }
   __syncthreads();
   const df2 u = Ui[o + r][o + q];
@@ -1375,9 +1385,7 @@ __global__ void __launch_bounds__(256, 4) chol_persistent_kernel(CholArgs a) {
       if (last && cv.dig) tile_digits_store(threadIdx.x, blockDim.x, sLi, cv.dig, P, k + 1, k);
       block_publish(&ps.flagL[(k + 1) * T + k], e);
       if (last) break;
-      for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) sX2[t & 31][t >> 5] = sLi[t >> 5][t & 31];
-      __syncthreads();
-      tile_mma<true, true>(sD, sLi, sX2);  // D_{k+1} = A_{k+1,k+1} - L_{k+1,k} L_{k+1,k}^T (lower part)
+      tile_mma<true, true, true>(sD, sLi, sLi);  // D_{k+1} = A_{k+1,k+1} - L_{k+1,k} L_{k+1,k}^T (lower part)
     }
   } else if (s_role == 0) {
     // ---------------- workers: tasks in list order from a shared counter ----------------
