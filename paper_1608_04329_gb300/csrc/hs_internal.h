@@ -147,7 +147,7 @@ struct ShrinkArgs {
   double* tau_new;        // written (one value)
   const double* G;        // p x p (diagonal read)
   double* S;              // P: 1/sqrt(A_jj) rounded to FP32 (1 for padded j)
-  double* part;           // ceil(p / 128) block partial sums (scratch)
+  double* part;           // ceil(p / 128) block partial sums and the Gamma variate (scratch)
   unsigned int* ticket;   // zero between sweeps (scratch)
   int* err;
   int update_mask;        // HS_UPD_* bits of the variables drawn (the others keep their values)

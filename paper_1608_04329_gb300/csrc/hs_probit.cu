@@ -282,7 +282,7 @@ hs::ShrinkArgs shrink_args(hs_probit* h, int m) {
   a.tau_new = h->tau_new + m;
   a.G = h->G;
   a.S = h->S + (size_t)m * h->P;
-  a.part = h->shrink_part + m * shrink_blocks(h);
+  a.part = h->shrink_part + m * (shrink_blocks(h) + 1);
   a.ticket = h->shrink_ticket + m;
   a.err = h->err;
   return a;
@@ -881,7 +881,7 @@ static hs_probit* init_ex_impl(const hs_probit_config* cfg_in, const void* X, co
   check(h->alloc(&h->LinvT, K * P2 * sizeof(double)));
   check(h->alloc(&h->xtz, K * pd));
   check(h->alloc(&h->v, K * (size_t)h->P * sizeof(double)));
-  check(h->alloc(&h->shrink_part, K * shrink_blocks(h) * sizeof(double)));
+  check(h->alloc(&h->shrink_part, K * (shrink_blocks(h) + 1) * sizeof(double)));
   check(h->alloc(&h->shrink_ticket, K * sizeof(unsigned int)));
   std::vector<int> order;
   if (h->chol_grid > 0) {

@@ -44,7 +44,6 @@ constexpr int kStepPadBytes = 40 * 1024;
 // shrink: lambda^{-2}, tau^{-2} and the equilibration S
 // ---------------------------------------------------------------------------
 constexpr int kShrinkThreads = 128;
-constexpr int kShrinkBatch = 8;  // equilibration columns per thread and load round trip
 
 // S_j = 1/sqrt(d) rounded to FP32 and returned exactly as a double.  Any
 // positive diagonal scaling gives the same factorization mathematically
@@ -69,23 +68,55 @@ __device__ __forceinline__ ShrinkArgs shrink_chain(ShrinkArgs a, int m) {
   a.lam_new += m * p;
   a.tau_new += m;
   a.S += (size_t)m * a.P;
-  a.part += (size_t)m * gridDim.x;
+  a.part += (size_t)m * (gridDim.x + 1);  // per chain: the block partials, then the Gamma variate
   a.ticket += m;
   return a;
 }
 
+// Cheng (1977) GB for shape a = (p + 1) / 2 >= 1, one proposal per lane and
+// round, the first accepted (round, lane) kept.  The accept test does not
+// involve the rate, so this runs beside the lambda draws (warp 0 of block 0).
+__device__ bool gamma_cheng_warp(const Rng& rng, uint32_t sweep, int p, int lane, double& g) {
+  const double sh = 0.5 * (double)(p + 1);
+  const double lam = sqrt(2.0 * sh - 1.0);
+  const double bconst = sh - 1.3862943611198906;  // a - ln 4
+  const double cconst = sh + lam;
+  g = sh;
+  for (int r = 0; r < 64; ++r) {
+    const uint4 w = rng.words((uint32_t)(r * 32 + lane), sweep, kPurTau);
+    double u1, uc1, u2, uc2;
+    unit_pair(w.x, w.y, u1, uc1);
+    unit_pair(w.z, w.w, u2, uc2);
+    const double V = (log(u1) - log(uc1)) / lam;
+    const double X = sh * exp(V);
+    const bool acc = bconst + cconst * V - X >= 2.0 * log(u1) + log(u2);
+    const unsigned m = __ballot_sync(0xffffffffu, acc);
+    if (m) {
+      g = __shfl_sync(0xffffffffu, X, __ffs(m) - 1);
+      return true;
+    }
+  }
+  return false;
+}
+
+// lambda^{-2} (one thread per j), the equilibration S, and tau^{-2}: block 0
+// draws the Gamma variate and stores it past the block partials; the last
+// block to finish sums the partials in a fixed order and applies the rate.
+// S_j = 1/sqrt(G_jj + tau lambda_j^{-2}) takes the current tau^{-2}, so every
+// block forms its own S without waiting for the new one: any positive
+// diagonal scaling gives the same factorization (L = S^{-1} L~), and the
+// ratio of the new to the current tau^{-2} keeps the scaled diagonal near 1.
 __global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
   const ShrinkArgs a = shrink_chain(a0, blockIdx.y);
   __shared__ double s_part[kShrinkThreads / 32];
-  __shared__ double s_tau;
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t sweep = (uint32_t)(*a.k_dev + 1);
   const Rng rng{a.rng.k0, a.rng.k1, a.rng.chain, a.rng.problem};
+  const double tau = a.scal[0];
   const int j = blockIdx.x * kShrinkThreads + tid;
   double part = 0.0;
   if (j < a.p) {
-    const double tau = a.scal[0];
     const uint4 w = rng.words((uint32_t)j, sweep, kPurLambda);
     double u, uc;
     unit_pair(w.x, w.y, u, uc);
@@ -93,6 +124,26 @@ __global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
     const double l = (a.update_mask & HS_UPD_LAMBDA) ? -log(u) / (a.nu[j] + tau * bj * bj * 0.5) : a.lam[j];
     a.lam_new[j] = l;
     part = l * bj * bj;
+    double sj = 1.0;
+    const double d = a.G[(size_t)j * a.p + j] + tau * l;
+    if (!isfinite(d)) {
+      set_error(a.err, kErrNonFinite);
+    } else if (!(d > 0.0)) {
+      set_error(a.err, kErrNotPD);
+    } else {
+      sj = equil_scale(d);
+    }
+    a.S[j] = sj;
+  } else if (j < a.P) {
+    a.S[j] = 1.0;  // padding past p
+  }
+  if (blockIdx.x == 0 && warp == 0) {
+    double g;
+    const bool found = gamma_cheng_warp(rng, sweep, a.p, lane, g);
+    if (lane == 0) {
+      if (!found) set_error(a.err, kErrGamma);
+      a.part[gridDim.x] = g;
+    }
   }
   part = warp_sum(part);
   if (lane == 0) s_part[warp] = part;
@@ -101,85 +152,21 @@ __global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
     double bp = 0.0;
     for (int w = 0; w < kShrinkThreads / 32; ++w) bp += s_part[w];
     a.part[blockIdx.x] = bp;
-    // release (the block's lambda^{-2} and its partial, ordered by the
-    // barrier) and acquire (the last block reads every block's) in one atomic
+    // release (the block's writes, ordered by the barrier) and acquire (the
+    // last block reads every block's partial and block 0's variate) in one atomic
     unsigned int old;
     asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(a.ticket) : "memory");
     s_last = (old == gridDim.x - 1);
   }
   __syncthreads();
-  if (!s_last) return;
-  // the equilibration's inputs for the first kShrinkBatch * kShrinkThreads
-  // columns, loaded (one round trip) while warp 0 draws tau
-  double gd[kShrinkBatch], lm[kShrinkBatch];
-#pragma unroll
-  for (int u = 0; u < kShrinkBatch; ++u) {
-    const int jj = tid + u * kShrinkThreads;
-    gd[u] = jj < a.p ? a.G[(size_t)jj * a.p + jj] : 1.0;
-    lm[u] = jj < a.p ? __ldcg(a.lam_new + jj) : 0.0;
-  }
-  if (warp == 0) {
-    // fixed-order sum of the block partials
-    double tot = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) tot += *(volatile double*)&a.part[b];
-    tot = warp_sum(tot);
-    // Cheng (1977) GB for shape a = (p + 1) / 2 >= 1.
-    const double sh = 0.5 * (double)(a.p + 1);
-    const double lam = sqrt(2.0 * sh - 1.0);
-    const double bconst = sh - 1.3862943611198906;  // a - ln 4
-    const double cconst = sh + lam;
-    double g = sh;
-    bool found = false;
-    for (int r = 0; r < 64 && !found; ++r) {
-      const uint4 w = rng.words((uint32_t)(r * 32 + lane), sweep, kPurTau);
-      double u1, uc1, u2, uc2;
-      unit_pair(w.x, w.y, u1, uc1);
-      unit_pair(w.z, w.w, u2, uc2);
-      const double V = (log(u1) - log(uc1)) / lam;
-      const double X = sh * exp(V);
-      const bool acc = bconst + cconst * V - X >= 2.0 * log(u1) + log(u2);
-      const unsigned m = __ballot_sync(0xffffffffu, acc);
-      if (m) {
-        g = __shfl_sync(0xffffffffu, X, __ffs(m) - 1);
-        found = true;
-      }
-    }
-    if (lane == 0) {
-      if (!found) set_error(a.err, kErrGamma);
-      const double t = (a.update_mask & HS_UPD_TAU) ? g / (a.scal[1] + 0.5 * tot) : a.scal[0];
-      *a.tau_new = t;
-      s_tau = t;
-      *a.ticket = 0u;  // ready for the next sweep
-    }
-  }
-  __syncthreads();
-  const double tn = s_tau;
-  for (int b0 = 0; b0 < a.P; b0 += kShrinkBatch * kShrinkThreads) {
-    if (b0 > 0) {
-#pragma unroll
-      for (int u = 0; u < kShrinkBatch; ++u) {
-        const int jj = b0 + tid + u * kShrinkThreads;
-        gd[u] = jj < a.p ? a.G[(size_t)jj * a.p + jj] : 1.0;
-        lm[u] = jj < a.p ? __ldcg(a.lam_new + jj) : 0.0;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kShrinkBatch; ++u) {
-      const int jj = b0 + tid + u * kShrinkThreads;
-      if (jj >= a.P) break;
-      double sj = 1.0;
-      if (jj < a.p) {
-        const double d = gd[u] + tn * lm[u];
-        if (!isfinite(d)) {
-          set_error(a.err, kErrNonFinite);
-        } else if (!(d > 0.0)) {
-          set_error(a.err, kErrNotPD);
-        } else {
-          sj = equil_scale(d);
-        }
-      }
-      a.S[jj] = sj;
-    }
+  if (!s_last || warp != 0) return;
+  double tot = 0.0;
+  for (int b = lane; b < (int)gridDim.x; b += 32) tot += __ldcg(a.part + b);
+  tot = warp_sum(tot);
+  if (lane == 0) {
+    const double g = __ldcg(a.part + gridDim.x);
+    *a.tau_new = (a.update_mask & HS_UPD_TAU) ? g / (a.scal[1] + 0.5 * tot) : a.scal[0];
+    *a.ticket = 0u;  // ready for the next sweep
   }
 }
 
