@@ -151,6 +151,8 @@ struct ShrinkArgs {
   unsigned int* ticket;   // zero between sweeps (scratch)
   int* err;
   int update_mask;        // HS_UPD_* bits of the variables drawn (the others keep their values)
+  int unit_diag;          // 1: S from the new tau^{-2} (unit diagonal, for the digit planes of the
+                          // tensor-core trailing updates); 0: from the current tau^{-2}
 };
 // nchains > 1: chains 0..nchains-1 at fixed strides past a's buffers (blockIdx.y = chain)
 cudaError_t shrink_launch(const ShrinkArgs& a, cudaStream_t s, int nchains = 1);

@@ -285,6 +285,7 @@ hs::ShrinkArgs shrink_args(hs_probit* h, int m) {
   a.part = h->shrink_part + m * (shrink_blocks(h) + 1);
   a.ticket = h->shrink_ticket + m;
   a.err = h->err;
+  a.unit_diag = h->tensor_sched ? 1 : 0;
   return a;
 }
 

@@ -73,6 +73,20 @@ __device__ __forceinline__ ShrinkArgs shrink_chain(ShrinkArgs a, int m) {
   return a;
 }
 
+// S_j for the diagonal d = G_jj + tau lambda_j^{-2} (1 and an error bit when
+// d is not positive and finite).
+__device__ __forceinline__ double shrink_scale(double d, int* err) {
+  if (!isfinite(d)) {
+    set_error(err, kErrNonFinite);
+    return 1.0;
+  }
+  if (!(d > 0.0)) {
+    set_error(err, kErrNotPD);
+    return 1.0;
+  }
+  return equil_scale(d);
+}
+
 // Cheng (1977) GB for shape a = (p + 1) / 2 >= 1, one proposal per lane and
 // round, the first accepted (round, lane) kept.  The accept test does not
 // involve the rate, so this runs beside the lambda draws (warp 0 of block 0).
@@ -102,13 +116,17 @@ __device__ bool gamma_cheng_warp(const Rng& rng, uint32_t sweep, int p, int lane
 // lambda^{-2} (one thread per j), the equilibration S, and tau^{-2}: block 0
 // draws the Gamma variate and stores it past the block partials; the last
 // block to finish sums the partials in a fixed order and applies the rate.
-// S_j = 1/sqrt(G_jj + tau lambda_j^{-2}) takes the current tau^{-2}, so every
-// block forms its own S without waiting for the new one: any positive
-// diagonal scaling gives the same factorization (L = S^{-1} L~), and the
-// ratio of the new to the current tau^{-2} keeps the scaled diagonal near 1.
+// Without the digit planes of the tensor-core trailing updates
+// (ShrinkArgs::unit_diag == 0) S_j = 1/sqrt(G_jj + tau lambda_j^{-2}) takes
+// the current tau^{-2}, so every block forms its own S without waiting for
+// the new one: any positive diagonal scaling gives the same factorization
+// (L = S^{-1} L~), and the FP32-pair arithmetic needs only range.  The digit
+// planes need a unit diagonal (every factor entry in [-1, 1]), so there the
+// last block forms S from the new tau^{-2}.
 __global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
   const ShrinkArgs a = shrink_chain(a0, blockIdx.y);
   __shared__ double s_part[kShrinkThreads / 32];
+  __shared__ double s_tau;
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t sweep = (uint32_t)(*a.k_dev + 1);
@@ -124,17 +142,8 @@ __global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
     const double l = (a.update_mask & HS_UPD_LAMBDA) ? -log(u) / (a.nu[j] + tau * bj * bj * 0.5) : a.lam[j];
     a.lam_new[j] = l;
     part = l * bj * bj;
-    double sj = 1.0;
-    const double d = a.G[(size_t)j * a.p + j] + tau * l;
-    if (!isfinite(d)) {
-      set_error(a.err, kErrNonFinite);
-    } else if (!(d > 0.0)) {
-      set_error(a.err, kErrNotPD);
-    } else {
-      sj = equil_scale(d);
-    }
-    a.S[j] = sj;
-  } else if (j < a.P) {
+    if (!a.unit_diag) a.S[j] = shrink_scale(a.G[(size_t)j * a.p + j] + tau * l, a.err);
+  } else if (j < a.P && !a.unit_diag) {
     a.S[j] = 1.0;  // padding past p
   }
   if (blockIdx.x == 0 && warp == 0) {
@@ -159,15 +168,24 @@ __global__ void __launch_bounds__(kShrinkThreads) shrink_kernel(ShrinkArgs a0) {
     s_last = (old == gridDim.x - 1);
   }
   __syncthreads();
-  if (!s_last || warp != 0) return;
-  double tot = 0.0;
-  for (int b = lane; b < (int)gridDim.x; b += 32) tot += __ldcg(a.part + b);
-  tot = warp_sum(tot);
-  if (lane == 0) {
-    const double g = __ldcg(a.part + gridDim.x);
-    *a.tau_new = (a.update_mask & HS_UPD_TAU) ? g / (a.scal[1] + 0.5 * tot) : a.scal[0];
-    *a.ticket = 0u;  // ready for the next sweep
+  if (!s_last) return;
+  if (warp == 0) {
+    double tot = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) tot += __ldcg(a.part + b);
+    tot = warp_sum(tot);
+    if (lane == 0) {
+      const double g = __ldcg(a.part + gridDim.x);
+      const double t = (a.update_mask & HS_UPD_TAU) ? g / (a.scal[1] + 0.5 * tot) : a.scal[0];
+      *a.tau_new = t;
+      s_tau = t;
+      *a.ticket = 0u;  // ready for the next sweep
+    }
   }
+  if (!a.unit_diag) return;
+  __syncthreads();
+  const double tn = s_tau;
+  for (int jj = tid; jj < a.P; jj += kShrinkThreads)
+    a.S[jj] = jj < a.p ? shrink_scale(a.G[(size_t)jj * a.p + jj] + tn * __ldcg(a.lam_new + jj), a.err) : 1.0;
 }
 
 // ---------------------------------------------------------------------------

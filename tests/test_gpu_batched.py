@@ -281,6 +281,40 @@ def test_tensor_core_trailing_updates_match_pair_arithmetic(pkg, dt, N, p, K):
         assert db <= 1e-11, (m, db)
 
 
+@pytest.mark.parametrize("K", [1, 4])
+def test_tensor_core_trailing_updates_after_a_large_jump_of_tau(pkg, K):
+    """The digit planes of the tensor-core trailing updates represent factor
+    entries in [-1, 1] exactly; a unit diagonal of the equilibrated precision
+    matrix (S formed from the new tau^{-2} on that schedule) bounds every
+    entry by its row norm, 1, for any design.  From a state whose tau^{-2} is
+    far below its conditional (tau^{-2} = 1e-4, small beta, large
+    lambda^{-2}) the new tau^{-2} is over 1e3 times the current one and
+    tau lambda^{-2} dominates the diagonal; the single-launch schedule (whose
+    pair arithmetic needs only range, so it equilibrates with the current
+    tau^{-2}) and the block-column schedule must still agree to the pair
+    arithmetic's precision."""
+    N, p = 2000, 520
+    d = problem(N, p, 5, "bf16", seed=p + 1)
+    r = np.random.default_rng(5)
+    states = [oracle.State(r.normal(0, 0.01, p), np.full(p, 1e3) * r.uniform(0.5, 2.0, p), r.exponential(size=p) + 0.05,
+                           1e-4, 1.0, 3) for _ in range(K)]
+    out = {}
+    for sched in (pkg.SCHED_SINGLE, pkg.SCHED_TENSOR):
+        s = pkg.HSProbit(d["X"], d["y"], seed=9, num_chains=K, chol_sched=sched, beta_solve=pkg.BETA_SUBST)
+        try:
+            for m, st in enumerate(states):
+                s.set_state(st.beta, st.lam_inv2, st.nu_inv, st.tau_inv2, st.xi_inv, st.k, chain=m)
+            s.sweep(1)
+            out[sched] = [s.get_state(chain=m) for m in range(K)]
+        finally:
+            s.close()
+    for m in range(K):
+        a, b = out[pkg.SCHED_SINGLE][m], out[pkg.SCHED_TENSOR][m]
+        assert a["tau_inv2"] == b["tau_inv2"] and a["tau_inv2"] > 1e3 * states[m].tau_inv2
+        db = np.linalg.norm(a["beta"] - b["beta"]) / np.linalg.norm(a["beta"])
+        assert db <= 1e-11, (m, db)
+
+
 def test_eight_chains_on_fp8_correlated_design_at_p_4000(pkg):
     """The large correlated workload's shape with its K = 8 chains at a size
     the oracle runs in seconds: FP8 e4m3 X with column scales, AR(1) rows,
