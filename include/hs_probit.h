@@ -284,8 +284,10 @@ int hs_probit_xstream_noalloc(int x_dtype, const void* X, int64_t ld, const uint
  * one code per task, kind | k << 2 | i << 10 | j << 18 with kind 0 = C(i,k)
  * (L_ik = A_ik L_kk^{-T}), 1 = X(k,j) (X_kj = L_kk^{-1} B_kj), 2 = UA(i,j,k)
  * (A_ij -= L_ik L_jk^T), 3 = UB(i,j,k) (B_ij -= L_ik X_kj); inverse = 0 lists
- * the factor-only form (kinds 0 and 2).  The list is a topological order of
- * the task graph, found by a list schedule for `workers` concurrent tasks.
+ * the factor-only form (kinds 0 and 2).  A C entry carries j = k + 1: that
+ * task also applies UA(i,k+1,k) from the L_ik it holds, and the list leaves
+ * UA(i,k+1,k) out.  The list is a topological order of the task graph (with
+ * those updates merged), found by a list schedule for `workers` concurrent tasks.
  * Writes min(count, max_codes) codes to the caller's array and returns the
  * count, or HS_EINVAL (T outside 1..256, workers < 1, inverse not 0 or 1,
  * max_codes < 0, codes NULL with max_codes > 0). */
