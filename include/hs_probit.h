@@ -297,7 +297,8 @@ int64_t hs_chol_task_list(int32_t T, int32_t workers, int32_t inverse, int32_t* 
  * factorization (host only; no CUDA call): tile columns [k0, k1) of T tiles,
  * the tasks C(i, k) and UA(i, j, k) with j < k1 in the order the kernel hands
  * them out (a list schedule for `workers` concurrent tasks, like
- * hs_chol_task_list), as codes of hs_chol_task_list.  Writes
+ * hs_chol_task_list), as codes of hs_chol_task_list (C entries with j = k:
+ * nothing merged).  Writes
  * min(count, max_codes) codes and returns the count, or HS_EINVAL (T outside
  * 1..256, not 0 <= k0 < k1 <= T, workers < 1, max_codes < 0, codes NULL with
  * max_codes > 0). */
